@@ -1,0 +1,465 @@
+"""Benchmark of the GB300 triangle counter.  Prints ONE JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload rmat20|rmat26|er4096|batch]
+
+A step is one pass of the whole hot path over one synthetic graph: ingest (validate + pack the edge list), CSR
+build (sort, dedup, degree, orientation, offsets, bins) and the fused count.  `value` is GTEPS = m / t_step with the
+edge list already resident in HBM (m = distinct undirected edges); `e2e` repeats the step through the C ABI from
+pinned host buffers, the host->device copy of the edge list and the device->host read of the count included.
+Per-phase times, count-only GTEPS and the dominant kernel's roofline are reported beside it.
+
+Under torchrun (N > 1) every rank counts its own graph (same workload, seed + rank): independent problems, weak
+scaling, no collective on the data path; the barrier and the max over ranks are for timing only.
+
+--impl reference times the CPU oracle (test infrastructure, never tuned) on the host cores for the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+L2_BYTES = 129 * 1024 * 1024
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="rmat20", choices=["rmat20", "rmat26", "er4096", "batch"])
+    p.add_argument("--batch-graphs", type=int, default=4096)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------------------------------------------------
+# Distributed plumbing (timing only)
+# ------------------------------------------------------------------------------------------------------------
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+
+    def init(self, backend):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        return self._reduce(x, "max")
+
+    def sum(self, x: float) -> float:
+        return self._reduce(x, "sum")
+
+    def _reduce(self, x, op):
+        if not self.pg:
+            return x
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX if op == "max" else self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def aggregate(local_units: float, local_seconds: float, dist: Dist):
+    """Whole-job rate: units summed over ranks / the slowest rank's time."""
+    units = dist.sum(local_units)
+    secs = dist.max(local_seconds)
+    return units, secs
+
+
+# ------------------------------------------------------------------------------------------------------------
+# Clocks during the timed region
+# ------------------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------------------
+# Roofline helpers
+# ------------------------------------------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def count_kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("tc_count.cuh", "tc_count.cu", "tc_internal.cuh", "tc_prims.cuh"):
+        with open(os.path.join(ROOT, "paper_1909_02127_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch of the count kernel from the committed ncu summary, if it was taken on the current
+    kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"k_count_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_hash = re.search(r"source_sha:\s*([0-9a-f]+)", text)
+    m_tr = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_tr or m_hash.group(1) != count_kernel_source_hash():
+        return None
+    return float(m_tr.group(1))
+
+
+def algorithmic_bytes(info: dict, grid_ctas: int) -> float:
+    """Bytes the two-hop method must read once per use: offsets of every source (8(n+1)), its row N+(u) (4m), the
+    offset pair of every hop-1 target (16m), the row N+(v) of every hop-1 target (4W), one 8-byte atomic per CTA."""
+    n, m, W = info["num_vertices"], info["num_edges"], info["num_wedges"]
+    return 8.0 * (n + 1) + 4.0 * m + 16.0 * m + 4.0 * W + 8.0 * grid_ctas
+
+
+def count_grid(info: dict) -> int:
+    want = info["bin_block"] + info["bin_wide"] + (info["bin_warp"] + 15) // 16
+    return int(max(1, min(want, 2 * 152)))
+
+
+# ------------------------------------------------------------------------------------------------------------
+# Our arm
+# ------------------------------------------------------------------------------------------------------------
+def run_single(args, dist: Dist):
+    import numpy as np
+    import torch
+
+    import graphgen
+    import paper_1909_02127_gb300 as tc
+
+    dev = torch.device("cuda", dist.local)
+    torch.cuda.set_device(dev)
+    base = graphgen.config(args.workload)
+    spec = graphgen.GraphSpec(base.kind, base.n, base.num_edges, base.seed + dist.rank, base.scale, base.permute,
+                              base.name)
+    stream = torch.cuda.current_stream()
+    ds, dd = spec.edges(device=dev)
+    torch.cuda.synchronize()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+    d_total = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def step(events=None):
+        if events:
+            events[0].record(stream)
+        g = tc.tc_load_edges(ds, dd, spec.n, stream=stream)
+        tc.tc_build(g, stream)
+        if events:
+            events[1].record(stream)
+        tc.tc_count_device(g, d_total, stream)
+        if events:
+            events[2].record(stream)
+        return g
+
+    # warm-up (also fixes the graph's sizes)
+    info = None
+    T_ref = None
+    for _ in range(args.warmup):
+        g = step()
+        info = tc.tc_graph_get_info(g)
+        torch.cuda.synchronize()
+        T_now = int(d_total.item())
+        if T_ref is not None and T_now != T_ref:
+            raise RuntimeError("count changed between warm-up steps")
+        T_ref = T_now
+        tc.tc_free(g)
+    if info is None:
+        g = step()
+        info = tc.tc_graph_get_info(g)
+        torch.cuda.synchronize()
+        T_ref = int(d_total.item())
+        tc.tc_free(g)
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = ClockSampler(dist.local)
+    launches0 = tc.tc_kernel_launches()
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k)  # L2 flush between timed steps (outside the events)
+        g = step(evs[k])
+        tc.tc_free(g)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clock_info = clocks.stop()
+    dist.barrier()
+    launches = tc.tc_kernel_launches() - launches0
+    if int(d_total.item()) != T_ref:
+        raise RuntimeError("count changed in the timed region")
+    step_ms = [evs[k][0].elapsed_time(evs[k][2]) for k in range(args.steps)]
+    build_ms = [evs[k][0].elapsed_time(evs[k][1]) for k in range(args.steps)]
+    count_ms = [evs[k][1].elapsed_time(evs[k][2]) for k in range(args.steps)]
+    local_s = sum(step_ms) / 1e3
+    m = info["num_edges"]
+    units, secs = aggregate(m * args.steps, local_s, dist)
+    value = units / secs / 1e9
+
+    # end to end through the C ABI from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        hs = ds.cpu().pin_memory()
+        hd = dd.cpu().pin_memory()
+        for _ in range(max(1, min(args.warmup, 2))):
+            g = tc.tc_load_edges(hs, hd, spec.n, stream=stream)
+            tc.tc_build(g, stream)
+            tc.tc_count(g, stream)
+            tc.tc_free(g)
+        dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            g = tc.tc_load_edges(hs, hd, spec.n, stream=stream)
+            tc.tc_build(g, stream)
+            T_e2e = tc.tc_count(g, stream)
+            tc.tc_free(g)
+            if T_e2e != T_ref:
+                raise RuntimeError("end-to-end count differs")
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        u2, s2 = aggregate(m * args.steps, e2e_s, dist)
+        e2e = {"value": round(u2 / s2 / 1e9, 4), "unit": "GTEPS", "h2d_bytes_per_step": int(spec.num_edges * 8),
+               "d2h_bytes_per_step": 8}
+
+    peak, peak_kind = measured_peaks()
+    grid = count_grid(info)
+    b_alg = algorithmic_bytes(info, grid)
+    mean_count_s = statistics.mean(count_ms) / 1e3
+    achieved = b_alg / mean_count_s / 1e9
+    traffic = profiled_traffic(args.workload)
+    roofline = {"bound": "hbm", "kernel": "k_count", "achieved": round(achieved, 1), "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic, "algorithmic_bytes": b_alg}
+
+    cpu = None
+    if dist.rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(spec, ds, dd, T_ref)
+
+    out = {
+        "metric": "triangle-count GTEPS (R-MAT 20/26; ingest+build+count per step)",
+        "value": round(value, 4), "unit": "GTEPS", "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(statistics.mean(step_ms), 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32/uint64 (exact integer)", "data": "synthetic",
+        "config": {"workload": spec.name, "n": spec.n, "generated_pairs": spec.num_edges, "m": m,
+                   "wedges": info["num_wedges"], "triangles": T_ref, "seed": spec.seed,
+                   "l2": "2x L2 buffer written between timed steps; edge list (8 B/pair) exceeds L2",
+                   "parallelism": f"replicas x{dist.world}"},
+        "phases_ms": {"build": round(statistics.mean(build_ms), 4), "count": round(statistics.mean(count_ms), 4)},
+        "count_gteps": round(m / mean_count_s / 1e9, 4),
+        "triangles_per_s": round(T_ref / mean_count_s, 1),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clock_info,
+        "wall_s_timed": round(wall, 4),
+    }
+    return out
+
+
+def cpu_baseline(spec, ds, dd, T_expect):
+    """The oracle as it stands, on all host cores, on the same graph (whole graph: build + count)."""
+    import oracle
+    hs, hd = ds.cpu().numpy(), dd.cpu().numpy()
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    T, m = oracle.count(hs, hd, spec.n, threads=cores)
+    t = time.perf_counter() - t0
+    if T != T_expect:
+        raise RuntimeError(f"oracle {T} != GPU {T_expect}")
+    return {"value": round(m / t / 1e9, 5), "unit": "GTEPS", "cores": cores, "kind": "oracle",
+            "sample": f"whole {spec.name} graph (sort+CSR+merge count), {t:.2f} s"}
+
+
+def run_batch(args, dist: Dist):
+    import numpy as np
+    import torch
+
+    import graphgen
+    import paper_1909_02127_gb300 as tc
+
+    dev = torch.device("cuda", dist.local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    specs = graphgen.batch_mix(args.batch_graphs, graphgen.BASE_SEED + graphgen.BATCH_SEED_OFFSET
+                               + dist.rank * 1000003)
+    handles = []
+    for sp in specs:
+        s, d = sp.edges(device=dev)
+        h = tc.tc_load_edges(s, d, sp.n, stream=stream)
+        tc.tc_build(h, stream)
+        handles.append(h)
+    torch.cuda.synchronize()
+    solo = np.array([tc.tc_count(h, stream) for h in handles], dtype=np.uint64)
+    for _ in range(args.warmup):
+        got = tc.tc_count_batch(handles, stream)
+        if not np.array_equal(got, solo):
+            raise RuntimeError("batched counts differ from one-by-one counts")
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    l0 = tc.tc_kernel_launches()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        got = tc.tc_count_batch(handles, stream)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    launches = tc.tc_kernel_launches() - l0
+    clock_info = clocks.stop()
+    if not np.array_equal(got, solo):
+        raise RuntimeError("batched counts differ")
+    # one graph per launch, same graphs and counts
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.steps // 2)):
+        for h in handles:
+            tc.tc_count(h, stream)
+    t_solo = (time.perf_counter() - t0) / max(1, args.steps // 2)
+    units, secs = aggregate(len(handles) * args.steps, t_batch, dist)
+    u1, s1 = aggregate(len(handles), t_solo, dist)
+    for h in handles:
+        tc.tc_free(h)
+    return {
+        "metric": "batched graphs/s (4096-graph mix, one persistent launch) vs one graph per launch",
+        "value": round(units / secs, 2), "unit": "graphs/s", "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_batch / args.steps * 1e3, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32/uint64 (exact integer)", "data": "synthetic",
+        "config": {"workload": f"batch of {len(handles)} graphs (ER/R-MAT mix, n log-uniform [64, 65536])",
+                   "total_triangles": int(solo.sum()), "parallelism": f"replicas x{dist.world}"},
+        "one_by_one_graphs_per_s": round(u1 / s1, 2),
+        "speedup_vs_one_by_one": round((units / secs) / (u1 / s1), 3),
+        "e2e": None, "gpu_launches": int(launches), "clocks": clock_info,
+    }
+
+
+# ------------------------------------------------------------------------------------------------------------
+# Reference arm: the CPU oracle
+# ------------------------------------------------------------------------------------------------------------
+def run_reference(args, dist: Dist):
+    import graphgen
+    import oracle
+    if dist.rank != 0:
+        return None
+    if args.workload == "batch":
+        return {"impl": "reference", "unavailable": "the oracle arm is defined for the single-graph workloads"}
+    spec = graphgen.config(args.workload)
+    hs, hd = spec.edges()
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.count(hs, hd, spec.n, threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        T, m = oracle.count(hs, hd, spec.n, threads=cores)
+        times.append(time.perf_counter() - t0)
+    value = m * len(times) / sum(times) / 1e9
+    return {
+        "impl": "reference", "metric": "triangle-count GTEPS (R-MAT 20/26; ingest+build+count per step)",
+        "value": round(value, 5), "unit": "GTEPS", "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(statistics.mean(times) * 1e3, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32/uint64 (exact integer)", "data": "synthetic",
+        "config": {"workload": spec.name, "n": spec.n, "generated_pairs": spec.num_edges, "m": m, "triangles": T},
+        "cpu_baseline": {"value": round(value, 5), "unit": "GTEPS", "cores": cores, "kind": "oracle",
+                         "sample": f"whole {spec.name} graph per step (sort+CSR+merge count)"},
+        "e2e": {"value": round(value, 5), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    if args.impl == "reference":
+        dist.init("gloo")
+        out = run_reference(args, dist)
+        dist.close()
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    import paper_1909_02127_gb300 as tc
+    from paper_1909_02127_gb300 import build
+    build.build()
+    tc.load_library()
+    dist.init("nccl")
+    out = run_batch(args, dist) if args.workload == "batch" else run_single(args, dist)
+    dist.close()
+    if dist.rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

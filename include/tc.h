@@ -1,0 +1,165 @@
+/*
+ * tc.h — C ABI of the GB300 exact triangle counter (libtc.so).
+ *
+ * Method: Wang & Owens, "Fast BFS-Based Triangle Counting on GPUs" (HPEC Graph Challenge 2019).  Triangle counting
+ * is posed as matching the query graph Q = K3 in an undirected data graph G (Sec. II-A, Def. 1 and Def. 2) by an
+ * all-source breadth-first traversal (Sec. III, Algorithm 1): every source u advances to its neighbours v, every v
+ * advances to its neighbours w, and the 2-path u-v-w is kept only when the non-tree (closing) edge u-w exists.  A
+ * total order on the vertices — the unique mapping order of Sec. III-A and the duplicate avoidance of Sec. III-C —
+ * makes each triangle appear exactly once; this library orders vertices by (degree, id) and traverses only edges
+ * that go up in that order.  The answer is the number of matches |M|/|Q| (Algorithm 1, result line).
+ *
+ * Conventions for every entry point:
+ *  - Status: each call returns a tc_status; nothing aborts the process.  tc_last_error() gives a message for the
+ *    last failing call on the calling thread.
+ *  - Streams: `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.  All device work of
+ *    a call is ordered on that stream.
+ *  - Ids: vertex ids are int32 in [0, n).  Counts are exact uint64.
+ *  - Memory: every device buffer is obtained from the graph's allocator (tc_allocator, or cudaMallocAsync on the
+ *    call's stream when none is given) and returned to it; the graph owns its buffers until tc_free.
+ *  - Threads: a tc_graph may be used by one host thread at a time.
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define TC_API __attribute__((visibility("default")))
+#else
+#define TC_API
+#endif
+
+typedef enum tc_status {
+  TC_OK = 0,
+  TC_ERR_INVALID_ARG = 1,  /* null pointer, negative size, bad flag, size above a stated limit */
+  TC_ERR_OUT_OF_RANGE = 2, /* an edge endpoint outside [0, n) */
+  TC_ERR_NO_MEMORY = 3,    /* the allocator returned NULL */
+  TC_ERR_CUDA = 4,         /* a CUDA runtime call failed; see tc_last_error() */
+  TC_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
+  TC_ERR_INTERNAL = 6,     /* a device-side consistency check failed */
+  TC_ERR_STATE = 7         /* call out of order, e.g. counting before tc_build */
+} tc_status;
+
+/* Where a caller's array lives. */
+#define TC_PTR_HOST 0x1u
+#define TC_PTR_DEVICE 0x2u
+
+/* Device memory provider.  alloc returns a pointer aligned to at least 256 bytes that is usable in stream order
+ * on `stream`, or NULL on failure; free releases it in stream order.  ctx is passed back unchanged. */
+typedef struct tc_allocator {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, void* stream, void* ctx);
+  void* ctx;
+} tc_allocator;
+
+typedef struct tc_graph tc_graph; /* opaque */
+
+/* Sizes of a built graph, for reporting. */
+typedef struct tc_graph_info {
+  int64_t num_vertices;    /* n */
+  int64_t num_input_pairs; /* pairs given to tc_load_edges */
+  int64_t num_edges;       /* m: distinct undirected edges after dropping self-loops and repeats */
+  int64_t max_out_degree;  /* largest d+(u) in the (degree, id) orientation */
+  int64_t num_wedges;      /* W = sum over oriented edges u->v of d+(v): the candidate 2-paths u->v->w */
+  int64_t active_sources;  /* sources with d+(u) >= 2 and at least one candidate 2-path */
+  int64_t bin_warp;        /* sources handled one warp each */
+  int64_t bin_block;       /* sources handled one thread block each (hash of N+(u) in shared memory) */
+  int64_t bin_wide;        /* sources whose N+(u) exceeds shared memory (closing test by binary search) */
+  int32_t built;           /* 1 after tc_build */
+  int32_t closing_test;    /* 0: hash of N+(u) in shared memory, 1: bitmap of N+(u) in shared memory */
+} tc_graph_info;
+
+/*
+ * tc_load_edges — take the data graph G (Sec. II-A: "inputs ... one data graph G"; Def. 1).
+ *   src, dst     num_edges int32 endpoints; pair i is the undirected edge {src[i], dst[i]} ((u,v) and (v,u) are
+ *                the same edge, Def. 1).  Host or device memory as `flags` says (exactly one of TC_PTR_HOST,
+ *                TC_PTR_DEVICE).  Read during the call only: the caller keeps ownership and may free or reuse the
+ *                arrays once the call returns.
+ *   num_edges    >= 0 and < 2^32 - 1.
+ *   num_vertices n >= 0; every endpoint must lie in [0, n), else TC_ERR_OUT_OF_RANGE and no graph is returned.
+ *   alloc        device memory provider, or NULL for cudaMallocAsync/cudaFreeAsync on the call's stream.  The
+ *                struct is copied; its functions must stay valid until tc_free.
+ *   out          receives the new graph handle (set to NULL on failure).
+ * Self-loops and repeated pairs are accepted and removed by tc_build (the simple-graph reading of Def. 1).
+ * Synchronises `stream` once (to report out-of-range ids).
+ */
+TC_API tc_status tc_load_edges(const int32_t* src, const int32_t* dst, int64_t num_edges, int64_t num_vertices,
+                               uint32_t flags, const tc_allocator* alloc, void* stream, tc_graph** out);
+
+/*
+ * tc_build — the data structure and filtering steps before the traversal (Sec. III-B: CSR storage; Algorithm 1,
+ * filtering: NE = degree, Sec. III-A; k-look-ahead pruning, Sec. III-C).  On the device: sort and de-duplicate the
+ * edges, compute degrees, orient each edge from lower to higher (degree, id) (the unique mapping order of Sec.
+ * III-A), build the oriented CSR (int64 row offsets, int32 sorted column ids) and bin the sources u by their
+ * candidate-2-path work.  Sources with d+(u) < 2 are dropped (they cannot be the first vertex of a triangle).
+ * Frees the edge buffers.  Idempotent: a second call returns TC_OK.  Synchronises `stream`.
+ */
+TC_API tc_status tc_build(tc_graph* g, void* stream);
+
+/*
+ * tc_count — the verification loop of Algorithm 1 for Q = K3, fused: for every source u, every v in N+(u) and
+ * every w in N+(v), count the 2-path u->v->w when the closing edge u->w exists (Sec. III-A: the non-tree edge of
+ * the triangle's spanning path).  *out_total receives T, the number of triangles (|M|/|Q|).  Requires tc_build
+ * (else TC_ERR_STATE).  Blocks until *out_total (host memory) is valid.
+ */
+TC_API tc_status tc_count(tc_graph* g, uint64_t* out_total, void* stream);
+
+/*
+ * tc_count_device — tc_count without the host round trip: writes T to the device word *d_total (8-byte aligned
+ * device memory; overwritten, not accumulated) in stream order and returns at once.  No allocation, no
+ * synchronisation: the sequence can be captured in a CUDA graph.
+ */
+TC_API tc_status tc_count_device(tc_graph* g, uint64_t* d_total, void* stream);
+
+/*
+ * tc_count_per_vertex — as tc_count, and also t(x), the number of triangles containing x, for every x in [0, n)
+ * (the per-vertex view of the matches M of Algorithm 1).
+ *   per_vertex  n uint64 entries, host or device memory as `flags` says (TC_PTR_HOST or TC_PTR_DEVICE);
+ *               overwritten.
+ *   out_total   host pointer for T, or NULL.
+ * Blocks until both outputs are valid.
+ */
+TC_API tc_status tc_count_per_vertex(tc_graph* g, uint64_t* per_vertex, uint64_t* out_total, uint32_t flags,
+                                     void* stream);
+
+/*
+ * tc_count_batch — count many built graphs in one persistent launch fed by a device work queue (the traversal of
+ * tc_count applied to each graph independently; the batching itself has no counterpart in the paper).
+ *   gs          num_graphs built graph handles (host array); the same handle may appear more than once.
+ *   out_counts  host array of num_graphs uint64: out_counts[i] = T of gs[i].
+ * Blocks until the counts are valid.
+ */
+TC_API tc_status tc_count_batch(tc_graph* const* gs, int32_t num_graphs, uint64_t* out_counts, void* stream);
+
+/* tc_graph_get_info — sizes of g (valid fields depend on whether g is built). */
+TC_API tc_status tc_graph_get_info(const tc_graph* g, tc_graph_info* info);
+
+/*
+ * tc_copy_csr — copy the oriented CSR of a built graph to host memory, for inspection and tests.
+ *   offsets  n+1 int64 row offsets; row u holds N+(u), the out-neighbours of u in the (degree, id) order.
+ *   cols     m int32 column ids, ascending within each row.
+ * Synchronises `stream`.
+ */
+TC_API tc_status tc_copy_csr(const tc_graph* g, int64_t* offsets, int32_t* cols, void* stream);
+
+/* tc_free — release g and all its device memory (stream-ordered on the last stream g used).  NULL is a no-op. */
+TC_API void tc_free(tc_graph* g);
+
+/* tc_kernel_launches — number of CUDA kernels this library has launched in the process so far (all threads).
+ * A diagnostic with no counterpart in the paper: benchmarks difference it around a timed region. */
+TC_API uint64_t tc_kernel_launches(void);
+
+/* tc_last_error — message for the last failing call on this thread ("" if none).  Valid until the next call. */
+TC_API const char* tc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TC_H */

@@ -1,0 +1,299 @@
+"""Python binding of libtc, the GB300 exact triangle counter (Wang & Owens, "Fast BFS-Based Triangle Counting on
+GPUs", HPEC 2019).
+
+Argument marshalling only: every step of the computation runs in the CUDA kernels of ``csrc/`` behind the C ABI of
+``include/tc.h``.  The functions carry the C names.  PyTorch supplies device memory (through the allocator hook)
+and streams.  There is no CPU fallback: if ``libtc.so`` is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtc.so")
+
+TC_OK, TC_ERR_INVALID_ARG, TC_ERR_OUT_OF_RANGE, TC_ERR_NO_MEMORY, TC_ERR_CUDA, TC_ERR_TIMEOUT, TC_ERR_INTERNAL, \
+    TC_ERR_STATE = range(8)
+TC_PTR_HOST, TC_PTR_DEVICE = 1, 2
+STATUS_NAMES = ["TC_OK", "TC_ERR_INVALID_ARG", "TC_ERR_OUT_OF_RANGE", "TC_ERR_NO_MEMORY", "TC_ERR_CUDA",
+                "TC_ERR_TIMEOUT", "TC_ERR_INTERNAL", "TC_ERR_STATE"]
+
+
+class TCError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {message}")
+
+
+class tc_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)),
+                ("free", ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)),
+                ("ctx", ctypes.c_void_p)]
+
+
+class tc_graph_info(ctypes.Structure):
+    _fields_ = [("num_vertices", ctypes.c_int64), ("num_input_pairs", ctypes.c_int64), ("num_edges", ctypes.c_int64),
+                ("max_out_degree", ctypes.c_int64), ("num_wedges", ctypes.c_int64),
+                ("active_sources", ctypes.c_int64), ("bin_warp", ctypes.c_int64), ("bin_block", ctypes.c_int64),
+                ("bin_wide", ctypes.c_int64), ("built", ctypes.c_int32), ("closing_test", ctypes.c_int32)]
+
+
+EXPORTED = ["tc_load_edges", "tc_build", "tc_count", "tc_count_device", "tc_count_per_vertex", "tc_count_batch",
+            "tc_graph_get_info", "tc_copy_csr", "tc_free", "tc_last_error", "tc_kernel_launches"]
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libtc.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first (python -c 'import __graft_entry__ as g;"
+                           " g.build()')")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32, u32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32
+    st = ctypes.c_int
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    lib.tc_load_edges.argtypes = [vp, vp, i64, i64, u32, ctypes.POINTER(tc_allocator), vp, ctypes.POINTER(vp)]
+    lib.tc_load_edges.restype = st
+    lib.tc_build.argtypes = [vp, vp]
+    lib.tc_build.restype = st
+    lib.tc_count.argtypes = [vp, u64p, vp]
+    lib.tc_count.restype = st
+    lib.tc_count_device.argtypes = [vp, vp, vp]
+    lib.tc_count_device.restype = st
+    lib.tc_count_per_vertex.argtypes = [vp, vp, u64p, u32, vp]
+    lib.tc_count_per_vertex.restype = st
+    lib.tc_count_batch.argtypes = [ctypes.POINTER(vp), i32, u64p, vp]
+    lib.tc_count_batch.restype = st
+    lib.tc_graph_get_info.argtypes = [vp, ctypes.POINTER(tc_graph_info)]
+    lib.tc_graph_get_info.restype = st
+    lib.tc_copy_csr.argtypes = [vp, vp, vp, vp]
+    lib.tc_copy_csr.restype = st
+    lib.tc_free.argtypes = [vp]
+    lib.tc_free.restype = None
+    lib.tc_kernel_launches.argtypes = []
+    lib.tc_kernel_launches.restype = ctypes.c_uint64
+    lib.tc_last_error.argtypes = []
+    lib.tc_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != TC_OK:
+        raise TCError(status, load_library().tc_last_error().decode(errors="replace"))
+
+
+def tc_kernel_launches() -> int:
+    return int(load_library().tc_kernel_launches())
+
+
+def tc_last_error() -> str:
+    return load_library().tc_last_error().decode(errors="replace")
+
+
+# ---------------------------------------------------------------------------------------------------------------
+# Streams and the torch allocator hook
+# ---------------------------------------------------------------------------------------------------------------
+def _stream_ptr(stream) -> Optional[int]:
+    """A torch.cuda.Stream, a raw cudaStream_t (int) or None (torch's current stream)."""
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class _TorchAllocator:
+    """Device memory from torch's caching allocator, handed to libtc through tc_allocator."""
+
+    def __init__(self):
+        self.live = {}
+        self._alloc = tc_allocator._fields_[0][1](self._do_alloc)
+        self._free = tc_allocator._fields_[1][1](self._do_free)
+        self.struct = tc_allocator(self._alloc, self._free, None)
+
+    def _do_alloc(self, nbytes, stream, ctx):
+        try:
+            import torch
+            s = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream()
+            with torch.cuda.stream(s):
+                t = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
+            p = t.data_ptr()
+            self.live[p] = (t, stream)
+            return p
+        except Exception:
+            return None
+
+    def _do_free(self, ptr, stream, ctx):
+        entry = self.live.pop(ptr, None)
+        if entry is None:
+            return
+        t, s0 = entry
+        if stream and stream != s0:
+            import torch
+            t.record_stream(torch.cuda.ExternalStream(stream))
+        del t
+
+
+_torch_alloc = None
+
+
+def torch_allocator() -> _TorchAllocator:
+    global _torch_alloc
+    if _torch_alloc is None:
+        _torch_alloc = _TorchAllocator()
+    return _torch_alloc
+
+
+# ---------------------------------------------------------------------------------------------------------------
+# Entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------------------------------------------
+def _edge_ptrs(src, dst):
+    """Returns (src_ptr, dst_ptr, num_edges, flags, keepalive)."""
+    try:
+        import torch
+        is_t = isinstance(src, torch.Tensor)
+    except ImportError:
+        is_t = False
+    if is_t:
+        if src.dtype != torch.int32 or dst.dtype != torch.int32:
+            raise TypeError("edge tensors must be int32")
+        if src.shape != dst.shape or src.dim() != 1:
+            raise ValueError("src and dst must be 1-D and the same length")
+        src, dst = src.contiguous(), dst.contiguous()
+        flags = TC_PTR_DEVICE if src.is_cuda else TC_PTR_HOST
+        if src.is_cuda != dst.is_cuda:
+            raise ValueError("src and dst must both be on the host or both on the device")
+        return src.data_ptr(), dst.data_ptr(), src.numel(), flags, (src, dst)
+    s = np.ascontiguousarray(src, dtype=np.int32)
+    d = np.ascontiguousarray(dst, dtype=np.int32)
+    if s.shape != d.shape or s.ndim != 1:
+        raise ValueError("src and dst must be 1-D and the same length")
+    return s.ctypes.data, d.ctypes.data, s.size, TC_PTR_HOST, (s, d)
+
+
+def tc_load_edges(src, dst, num_vertices: int, stream=None, allocator="torch") -> int:
+    """Load the undirected pairs (src[i], dst[i]) of a graph on [0, num_vertices); returns a tc_graph handle.
+    allocator: "torch" (torch's caching allocator), None (cudaMallocAsync inside the library)."""
+    lib = load_library()
+    sp, dp, m, flags, keep = _edge_ptrs(src, dst)
+    alloc = ctypes.byref(torch_allocator().struct) if allocator == "torch" else None
+    out = ctypes.c_void_p()
+    _check(lib.tc_load_edges(sp, dp, m, num_vertices, flags, alloc, _stream_ptr(stream), ctypes.byref(out)))
+    del keep
+    return out.value
+
+
+def tc_build(g: int, stream=None) -> None:
+    _check(load_library().tc_build(g, _stream_ptr(stream)))
+
+
+def tc_count(g: int, stream=None) -> int:
+    out = ctypes.c_uint64(0)
+    _check(load_library().tc_count(g, ctypes.byref(out), _stream_ptr(stream)))
+    return int(out.value)
+
+
+def tc_count_device(g: int, d_total, stream=None) -> None:
+    """Asynchronous count into the device word d_total (a torch tensor with at least 8 bytes, or a pointer)."""
+    ptr = d_total if isinstance(d_total, int) else d_total.data_ptr()
+    _check(load_library().tc_count_device(g, ptr, _stream_ptr(stream)))
+
+
+def tc_count_per_vertex(g: int, out=None, stream=None):
+    """Returns (T, t): t is `out` if given (uint64/int64 numpy array or CUDA tensor of n entries) else a new numpy
+    uint64 array."""
+    lib = load_library()
+    n = tc_graph_get_info(g)["num_vertices"]
+    if out is None:
+        out = np.zeros(n, dtype=np.uint64)
+    total = ctypes.c_uint64(0)
+    if isinstance(out, np.ndarray):
+        if out.dtype not in (np.uint64, np.int64) or out.size < n or not out.flags.c_contiguous:
+            raise ValueError("out must be a contiguous 64-bit array of n entries")
+        _check(lib.tc_count_per_vertex(g, out.ctypes.data, ctypes.byref(total), TC_PTR_HOST, _stream_ptr(stream)))
+    else:
+        if out.element_size() != 8 or out.numel() < n or not out.is_contiguous():
+            raise ValueError("out must be a contiguous 64-bit tensor of n entries")
+        flags = TC_PTR_DEVICE if out.is_cuda else TC_PTR_HOST
+        _check(lib.tc_count_per_vertex(g, out.data_ptr(), ctypes.byref(total), flags, _stream_ptr(stream)))
+    return int(total.value), out
+
+
+def tc_count_batch(gs: Sequence[int], stream=None) -> np.ndarray:
+    lib = load_library()
+    arr = (ctypes.c_void_p * len(gs))(*gs)
+    out = np.zeros(len(gs), dtype=np.uint64)
+    _check(lib.tc_count_batch(arr, len(gs), out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                              _stream_ptr(stream)))
+    return out
+
+
+def tc_graph_get_info(g: int) -> dict:
+    info = tc_graph_info()
+    _check(load_library().tc_graph_get_info(g, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in tc_graph_info._fields_}
+
+
+def tc_copy_csr(g: int, stream=None):
+    info = tc_graph_get_info(g)
+    off = np.zeros(info["num_vertices"] + 1, dtype=np.int64)
+    col = np.zeros(max(info["num_edges"], 1), dtype=np.int32)
+    _check(load_library().tc_copy_csr(g, off.ctypes.data, col.ctypes.data, _stream_ptr(stream)))
+    return off, col[: info["num_edges"]]
+
+
+def tc_free(g: int) -> None:
+    if g:
+        load_library().tc_free(g)
+
+
+class Graph:
+    """Owning wrapper: Graph(src, dst, n) loads and builds; count() / count_per_vertex(); freed on close()."""
+
+    def __init__(self, src, dst, num_vertices: int, stream=None, allocator="torch", build: bool = True):
+        self.handle = tc_load_edges(src, dst, num_vertices, stream=stream, allocator=allocator)
+        self.stream = stream
+        if build:
+            tc_build(self.handle, stream)
+
+    def build(self):
+        tc_build(self.handle, self.stream)
+
+    def count(self) -> int:
+        return tc_count(self.handle, self.stream)
+
+    def count_per_vertex(self, out=None):
+        return tc_count_per_vertex(self.handle, out, self.stream)
+
+    def info(self) -> dict:
+        return tc_graph_get_info(self.handle)
+
+    def csr(self):
+        return tc_copy_csr(self.handle, self.stream)
+
+    def close(self):
+        if self.handle:
+            tc_free(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

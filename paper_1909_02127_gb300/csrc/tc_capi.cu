@@ -1,0 +1,322 @@
+// tc_capi.cu — the C entry points declared in include/tc.h: argument checks, handle lifetime, the allocator hook
+// and status reporting.  All arithmetic happens in the kernels of tc_build.cu / tc_count.cu / tc_batch.cu.
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <new>
+#include <string>
+
+#include "tc_internal.cuh"
+
+namespace tc {
+
+namespace {
+thread_local std::string g_last_error;
+std::atomic<unsigned long long> g_launches{0};
+}  // namespace
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+tc_status cuda_status(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return TC_OK;
+  set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+  return e == cudaErrorMemoryAllocation ? TC_ERR_NO_MEMORY : TC_ERR_CUDA;
+}
+
+void* Allocator::alloc(size_t bytes, cudaStream_t s) const {
+  if (bytes == 0) bytes = 16;
+  if (has_user) return user.alloc(bytes, (void*)s, user.ctx);
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void Allocator::free(void* p, cudaStream_t s) const {
+  if (!p) return;
+  if (has_user)
+    user.free(p, (void*)s, user.ctx);
+  else
+    (void)cudaFreeAsync(p, s);
+}
+
+tc_status buf_alloc(const Allocator& a, Buf& b, size_t bytes, cudaStream_t s) {
+  b.p = a.alloc(bytes, s);
+  b.bytes = bytes;
+  if (!b.p) {
+    b.bytes = 0;
+    char msg[96];
+    snprintf(msg, sizeof msg, "device allocation of %zu bytes failed", bytes);
+    set_error(msg);
+    return TC_ERR_NO_MEMORY;
+  }
+  return TC_OK;
+}
+
+void buf_release(const Allocator& a, Buf& b, cudaStream_t s) {
+  if (b.p) a.free(b.p, s);
+  b = Buf{};
+}
+
+}  // namespace tc
+
+using namespace tc;
+
+namespace {
+
+int bits_for(int64_t n) {
+  int b = 1;
+  while (b < 31 && (1ll << b) < n) ++b;
+  return b;
+}
+
+void release_all(tc_graph* g, cudaStream_t s) {
+  buf_release(g->alloc, g->keys, s);
+  buf_release(g->alloc, g->off, s);
+  buf_release(g->alloc, g->col, s);
+  buf_release(g->alloc, g->list, s);
+  buf_release(g->alloc, g->acc, s);
+  if (g->host_total) {
+    cudaFreeHost(g->host_total);
+    g->host_total = nullptr;
+  }
+}
+
+tc_status check_built(const tc_graph* g) {
+  if (!g) {
+    set_error("graph handle is NULL");
+    return TC_ERR_INVALID_ARG;
+  }
+  if (!g->built) {
+    set_error("graph is not built: call tc_build first");
+    return TC_ERR_STATE;
+  }
+  return TC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+TC_API const char* tc_last_error(void) { return g_last_error.c_str(); }
+
+TC_API uint64_t tc_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+TC_API tc_status tc_load_edges(const int32_t* src, const int32_t* dst, int64_t num_edges, int64_t num_vertices,
+                               uint32_t flags, const tc_allocator* alloc, void* stream, tc_graph** out) {
+  if (!out) {
+    set_error("tc_load_edges: out is NULL");
+    return TC_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (num_edges < 0 || num_vertices < 0) {
+    set_error("tc_load_edges: negative size");
+    return TC_ERR_INVALID_ARG;
+  }
+  if (num_vertices > 0x7fffffffLL) {
+    set_error("tc_load_edges: num_vertices exceeds the int32 id range");
+    return TC_ERR_INVALID_ARG;
+  }
+  if (num_edges >= 0xffffffffLL) {
+    set_error("tc_load_edges: num_edges must be below 2^32-1");
+    return TC_ERR_INVALID_ARG;
+  }
+  if (flags != TC_PTR_HOST && flags != TC_PTR_DEVICE) {
+    set_error("tc_load_edges: flags must be exactly one of TC_PTR_HOST, TC_PTR_DEVICE");
+    return TC_ERR_INVALID_ARG;
+  }
+  if (num_edges > 0 && (!src || !dst)) {
+    set_error("tc_load_edges: src/dst is NULL");
+    return TC_ERR_INVALID_ARG;
+  }
+  if (alloc && (!alloc->alloc || !alloc->free)) {
+    set_error("tc_load_edges: allocator has a NULL function");
+    return TC_ERR_INVALID_ARG;
+  }
+  if (num_edges > 0 && num_vertices == 0) {
+    set_error("tc_load_edges: edges given for an empty vertex set");
+    return TC_ERR_OUT_OF_RANGE;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  tc_graph* g = new (std::nothrow) tc_graph();
+  if (!g) {
+    set_error("tc_load_edges: host allocation failed");
+    return TC_ERR_NO_MEMORY;
+  }
+  if (alloc) {
+    g->alloc.user = *alloc;
+    g->alloc.has_user = true;
+  }
+  g->n = num_vertices;
+  g->num_pairs = num_edges;
+  g->key_bits = bits_for(num_vertices);
+  g->last_stream = s;
+  tc_status st = TC_OK;
+  Buf err, stage;
+  uint32_t h_err = 0;
+  do {
+    if ((st = buf_alloc(g->alloc, g->acc, 64, s))) break;
+    if (cudaMallocHost((void**)&g->host_total, 64) != cudaSuccess) {
+      (void)cudaGetLastError();
+      g->host_total = nullptr;
+      set_error("tc_load_edges: pinned host allocation failed");
+      st = TC_ERR_NO_MEMORY;
+      break;
+    }
+    if (num_edges == 0) break;
+    if ((st = buf_alloc(g->alloc, g->keys, (size_t)num_edges * 8, s))) break;
+    if ((st = buf_alloc(g->alloc, err, 16, s))) break;
+    if ((st = cuda_status(cudaMemsetAsync(err.p, 0, 4, s), "memset err"))) break;
+    if (flags == TC_PTR_DEVICE) {
+      if ((st = pack_edges(g, src, dst, num_edges, 0, err.as<uint32_t>(), s))) break;
+    } else {
+      // host arrays: stream them through a device staging buffer in chunks
+      const int64_t chunk = num_edges < (int64_t)(1 << 24) ? num_edges : (int64_t)(1 << 24);
+      if ((st = buf_alloc(g->alloc, stage, (size_t)chunk * 8, s))) break;
+      int32_t* ds = stage.as<int32_t>();
+      int32_t* dd = ds + chunk;
+      for (int64_t o = 0; o < num_edges && st == TC_OK; o += chunk) {
+        const int64_t len = num_edges - o < chunk ? num_edges - o : chunk;
+        st = cuda_status(cudaMemcpyAsync(ds, src + o, (size_t)len * 4, cudaMemcpyHostToDevice, s), "H2D src");
+        if (st == TC_OK)
+          st = cuda_status(cudaMemcpyAsync(dd, dst + o, (size_t)len * 4, cudaMemcpyHostToDevice, s), "H2D dst");
+        if (st == TC_OK) st = pack_edges(g, ds, dd, len, o, err.as<uint32_t>(), s);
+      }
+      if (st) break;
+    }
+    if ((st = cuda_status(cudaMemcpyAsync(&h_err, err.p, 4, cudaMemcpyDeviceToHost, s), "copy err"))) break;
+    if ((st = cuda_status(cudaStreamSynchronize(s), "tc_load_edges sync"))) break;
+    if (h_err) {
+      set_error("tc_load_edges: an edge endpoint lies outside [0, num_vertices)");
+      st = TC_ERR_OUT_OF_RANGE;
+    }
+  } while (0);
+  buf_release(g->alloc, stage, s);
+  buf_release(g->alloc, err, s);
+  if (st != TC_OK) {
+    release_all(g, s);
+    delete g;
+    return st;
+  }
+  *out = g;
+  return TC_OK;
+}
+
+TC_API tc_status tc_build(tc_graph* g, void* stream) {
+  if (!g) {
+    set_error("tc_build: graph handle is NULL");
+    return TC_ERR_INVALID_ARG;
+  }
+  if (g->built) return TC_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  g->last_stream = s;
+  tc_status st = build_graph(g, s);
+  if (st != TC_OK) return st;
+  g->built = true;
+  return TC_OK;
+}
+
+TC_API tc_status tc_count_device(tc_graph* g, uint64_t* d_total, void* stream) {
+  TC_TRY(check_built(g));
+  if (!d_total) {
+    set_error("tc_count_device: d_total is NULL");
+    return TC_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  g->last_stream = s;
+  return launch_count(g, d_total, nullptr, reinterpret_cast<uint32_t*>(g->acc.as<uint64_t>() + 1), s);
+}
+
+TC_API tc_status tc_count(tc_graph* g, uint64_t* out_total, void* stream) {
+  TC_TRY(check_built(g));
+  if (!out_total) {
+    set_error("tc_count: out_total is NULL");
+    return TC_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  g->last_stream = s;
+  uint64_t* d_total = g->acc.as<uint64_t>();
+  TC_TRY(launch_count(g, d_total, nullptr, reinterpret_cast<uint32_t*>(d_total + 1), s));
+  TC_CUDA(cudaMemcpyAsync(g->host_total, d_total, 8, cudaMemcpyDeviceToHost, s));
+  TC_CUDA(cudaStreamSynchronize(s));
+  *out_total = *g->host_total;
+  return TC_OK;
+}
+
+TC_API tc_status tc_count_per_vertex(tc_graph* g, uint64_t* per_vertex, uint64_t* out_total, uint32_t flags,
+                                     void* stream) {
+  TC_TRY(check_built(g));
+  if (flags != TC_PTR_HOST && flags != TC_PTR_DEVICE) {
+    set_error("tc_count_per_vertex: flags must be exactly one of TC_PTR_HOST, TC_PTR_DEVICE");
+    return TC_ERR_INVALID_ARG;
+  }
+  if (!per_vertex && g->n > 0) {
+    set_error("tc_count_per_vertex: per_vertex is NULL");
+    return TC_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  g->last_stream = s;
+  uint64_t* d_total = g->acc.as<uint64_t>();
+  Buf tmp;
+  uint64_t* d_pv = per_vertex;
+  if (flags == TC_PTR_HOST && g->n > 0) {
+    TC_TRY(buf_alloc(g->alloc, tmp, (size_t)g->n * 8, s));
+    d_pv = tmp.as<uint64_t>();
+  }
+  tc_status st = launch_count(g, d_total, g->n > 0 ? d_pv : nullptr, reinterpret_cast<uint32_t*>(d_total + 1), s);
+  if (st == TC_OK && flags == TC_PTR_HOST && g->n > 0)
+    st = cuda_status(cudaMemcpyAsync(per_vertex, d_pv, (size_t)g->n * 8, cudaMemcpyDeviceToHost, s), "D2H t");
+  if (st == TC_OK) st = cuda_status(cudaMemcpyAsync(g->host_total, d_total, 8, cudaMemcpyDeviceToHost, s), "D2H T");
+  if (st == TC_OK) st = cuda_status(cudaStreamSynchronize(s), "tc_count_per_vertex sync");
+  buf_release(g->alloc, tmp, s);
+  if (st == TC_OK && out_total) *out_total = *g->host_total;
+  return st;
+}
+
+TC_API tc_status tc_graph_get_info(const tc_graph* g, tc_graph_info* info) {
+  if (!g || !info) {
+    set_error("tc_graph_get_info: NULL argument");
+    return TC_ERR_INVALID_ARG;
+  }
+  memset(info, 0, sizeof *info);
+  info->num_vertices = g->n;
+  info->num_input_pairs = g->num_pairs;
+  info->built = g->built ? 1 : 0;
+  if (g->built) {
+    info->num_edges = g->m;
+    info->max_out_degree = g->max_out_degree;
+    info->num_wedges = g->wedges;
+    info->active_sources = g->active;
+    info->bin_warp = g->nw;
+    info->bin_block = g->nb - g->nwide;
+    info->bin_wide = g->nwide;
+    info->closing_test = g->n <= kBitmapMaxN ? 1 : 0;
+  }
+  return TC_OK;
+}
+
+TC_API tc_status tc_copy_csr(const tc_graph* g, int64_t* offsets, int32_t* cols, void* stream) {
+  TC_TRY(check_built(g));
+  if (!offsets || (g->m > 0 && !cols)) {
+    set_error("tc_copy_csr: NULL output");
+    return TC_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  TC_CUDA(cudaMemcpyAsync(offsets, g->off.p, (size_t)(g->n + 1) * 8, cudaMemcpyDeviceToHost, s));
+  if (g->m > 0) TC_CUDA(cudaMemcpyAsync(cols, g->col.p, (size_t)g->m * 4, cudaMemcpyDeviceToHost, s));
+  TC_CUDA(cudaStreamSynchronize(s));
+  return TC_OK;
+}
+
+TC_API void tc_free(tc_graph* g) {
+  if (!g) return;
+  release_all(g, g->last_stream);
+  delete g;
+}
+
+}  // extern "C"

@@ -1,0 +1,143 @@
+// tc_internal.cuh — internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "tc.h"
+
+namespace tc {
+
+constexpr int kNumSMs = 152;
+
+// ------------------------------------------------------------------------------------------------------------
+// Errors
+// ------------------------------------------------------------------------------------------------------------
+void set_error(const std::string& msg);
+// Counts kernel launches made by this library (reported by tc_kernel_launches).
+void note_launch();
+tc_status cuda_status(cudaError_t e, const char* what);
+
+#define TC_CUDA(call)                                              \
+  do {                                                             \
+    cudaError_t tc_e_ = (call);                                    \
+    if (tc_e_ != cudaSuccess) return ::tc::cuda_status(tc_e_, #call); \
+  } while (0)
+
+#define TC_TRY(call)                         \
+  do {                                       \
+    tc_status tc_s_ = (call);                \
+    if (tc_s_ != TC_OK) return tc_s_;        \
+  } while (0)
+
+// ------------------------------------------------------------------------------------------------------------
+// Device memory through the graph's allocator
+// ------------------------------------------------------------------------------------------------------------
+struct Allocator {
+  tc_allocator user{};
+  bool has_user = false;
+  void* alloc(size_t bytes, cudaStream_t s) const;
+  void free(void* p, cudaStream_t s) const;
+};
+
+// A buffer owned by the code that allocated it (freed in stream order by release()).
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+tc_status buf_alloc(const Allocator& a, Buf& b, size_t bytes, cudaStream_t s);
+void buf_release(const Allocator& a, Buf& b, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------------------------
+// Count-kernel parameters (shared by tc_count and tc_count_batch)
+// ------------------------------------------------------------------------------------------------------------
+constexpr int kCountThreads = 512;                 // threads per CTA of the counting kernel
+constexpr int kWarpsPerCTA = kCountThreads / 32;
+constexpr int kWarpHashSlots = 256;                // per-warp hash of N+(u): d+(u) <= kWarpMaxDeg
+constexpr int kWarpMaxDeg = 64;
+constexpr int kBlockHashSlotsMax = 8192;           // per-CTA hash of N+(u): d+(u) <= kBlockMaxDeg
+constexpr int kBlockMaxDeg = kBlockHashSlotsMax / 2;
+constexpr int kBlockRows = 512;                    // rows (v in N+(u)) staged per CTA pass
+constexpr int64_t kBlockMinWork = 1 << 15;         // w(u) above this goes to a whole CTA
+constexpr int kBitmapMaxN = kWarpHashSlots * 32;   // n <= this: per-warp bitmap of N+(u) instead of a hash
+
+// Per-graph view used by the counting kernels.
+struct CsrView {
+  const int64_t* off;   // n+1 row offsets
+  const int32_t* col;   // m column ids (+ padding to a multiple of 4, 16-byte aligned)
+  const int32_t* list;  // active sources: [0, nb) block bin, [nb, nb+nw) warp bin
+  int64_t n;
+  int32_t nb;           // block-bin sources (includes wide ones)
+  int32_t nw;           // warp-bin sources
+  int32_t bitmap;       // 1: closing test by per-warp bitmap over [0, n)
+  int32_t pad;
+};
+
+// ------------------------------------------------------------------------------------------------------------
+// Primitives (tc_prims.cu)
+// ------------------------------------------------------------------------------------------------------------
+// LSD radix sort of uint64 keys on bits [bit_lo, bit_hi), stable.  keys/alt: n elements each; the sorted result
+// is in *result (either keys or alt).
+tc_status radix_sort_u64(const Allocator& a, uint64_t* keys, uint64_t* alt, int64_t n, int bit_lo, int bit_hi,
+                         uint64_t** result, cudaStream_t s);
+// Exclusive scan of n int32 values into n+1 int64 values (out[n] = total).
+tc_status exclusive_scan_i32_to_i64(const Allocator& a, const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
+// Exclusive scan of n uint32 values in place; *total (device, may be null) receives the sum.
+tc_status exclusive_scan_u32(const Allocator& a, uint32_t* data, int64_t n, cudaStream_t s);
+
+int grid_for(int64_t items, int threads, int max_blocks = kNumSMs * 16);
+
+}  // namespace tc
+
+// ------------------------------------------------------------------------------------------------------------
+// The graph handle
+// ------------------------------------------------------------------------------------------------------------
+struct tc_graph {
+  tc::Allocator alloc;
+  cudaStream_t last_stream = nullptr;
+  int64_t n = 0;
+  int64_t num_pairs = 0;
+  int key_bits = 1;          // B: bits per vertex id in packed keys
+  tc::Buf keys;              // packed (lo << B) | hi keys, until tc_build
+  bool built = false;
+  // built state
+  int64_t m = 0;
+  int64_t max_out_degree = 0;
+  int64_t wedges = 0;
+  int64_t active = 0;
+  int64_t nb = 0, nw = 0, nwide = 0;
+  tc::Buf off;               // int64[n+1]
+  tc::Buf col;               // int32[round_up(m,4)+4]
+  tc::Buf list;              // int32[nb + nw]
+  tc::Buf acc;               // uint64 scratch word(s) for counting: [0] total, [1..2] work cursors
+  uint64_t* host_total = nullptr;  // pinned 8-byte landing slot
+  tc::CsrView view() const {
+    tc::CsrView v;
+    v.off = off.as<int64_t>();
+    v.col = col.as<int32_t>();
+    v.list = list.as<int32_t>();
+    v.n = n;
+    v.nb = (int32_t)nb;
+    v.nw = (int32_t)nw;
+    v.bitmap = n <= tc::kBitmapMaxN ? 1 : 0;
+    v.pad = 0;
+    return v;
+  }
+};
+
+namespace tc {
+// tc_build.cu
+tc_status pack_edges(tc_graph* g, const int32_t* src, const int32_t* dst, int64_t len, int64_t offset,
+                     uint32_t* d_err, cudaStream_t s);
+tc_status build_graph(tc_graph* g, cudaStream_t s);
+// tc_count.cu
+tc_status launch_count(const tc_graph* g, uint64_t* d_total, uint64_t* d_per_vertex, uint32_t* d_cursors,
+                       cudaStream_t s);
+}  // namespace tc

@@ -21,7 +21,8 @@ def _pack(edges, n, T, t):
 
 def complete(n):
     """K_n: every 3-set is a triangle, T = C(n,3); each vertex in C(n-1,2)."""
-    return _pack(itertools.combinations(range(n), 2), n, math.comb(n, 3), [math.comb(n - 1, 2)] * n)
+    a, b = np.triu_indices(n, 1)
+    return a.astype(np.int32), b.astype(np.int32), n, math.comb(n, 3), np.full(n, math.comb(n - 1, 2), np.uint64)
 
 
 def wheel(k):

@@ -1,0 +1,91 @@
+"""The C-ABI library loads and exports every symbol include/tc.h declares; host-side argument checks (no GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    with open(os.path.join(ROOT, "include", "tc.h")) as f:
+        text = f.read()
+    for m in re.finditer(r"TC_API\s+[\w\s\*]+?\b(tc_\w+)\s*\(", text):
+        names.append(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1909_02127_gb300 import build
+    build.build()
+    import paper_1909_02127_gb300 as tc
+    return tc.load_library()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("tc_load_edges", "tc_build", "tc_count", "tc_count_per_vertex", "tc_count_batch", "tc_free"):
+        assert required in names
+
+
+def test_exports_every_declared_symbol(lib):
+    import paper_1909_02127_gb300 as tc
+    for name in _declared_functions():
+        assert hasattr(lib, name), f"libtc.so does not export {name}"
+    assert set(_declared_functions()) <= set(tc.EXPORTED)
+
+
+def test_library_is_built_for_sm103a():
+    # the build flags name exactly one target: sm_103a
+    from paper_1909_02127_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_argument_errors_without_gpu(lib):
+    import paper_1909_02127_gb300 as tc
+    out = ctypes.c_void_p()
+    # NULL out
+    assert lib.tc_load_edges(None, None, 0, 0, tc.TC_PTR_HOST, None, None, None) == tc.TC_ERR_INVALID_ARG
+    assert "out is NULL" in tc.tc_last_error()
+    # negative sizes
+    assert lib.tc_load_edges(None, None, -1, 3, tc.TC_PTR_HOST, None, None, ctypes.byref(out)) == tc.TC_ERR_INVALID_ARG
+    assert lib.tc_load_edges(None, None, 0, -3, tc.TC_PTR_HOST, None, None, ctypes.byref(out)) == tc.TC_ERR_INVALID_ARG
+    # too many vertices / edges
+    assert lib.tc_load_edges(None, None, 0, 1 << 31, tc.TC_PTR_HOST, None, None,
+                             ctypes.byref(out)) == tc.TC_ERR_INVALID_ARG
+    assert lib.tc_load_edges(None, None, (1 << 32) - 1, 5, tc.TC_PTR_HOST, None, None,
+                             ctypes.byref(out)) == tc.TC_ERR_INVALID_ARG
+    # bad flags
+    assert lib.tc_load_edges(None, None, 0, 3, 0, None, None, ctypes.byref(out)) == tc.TC_ERR_INVALID_ARG
+    assert lib.tc_load_edges(None, None, 0, 3, 3, None, None, ctypes.byref(out)) == tc.TC_ERR_INVALID_ARG
+    # NULL edge arrays with edges
+    assert lib.tc_load_edges(None, None, 5, 3, tc.TC_PTR_HOST, None, None, ctypes.byref(out)) == tc.TC_ERR_INVALID_ARG
+    # edges on an empty vertex set are out of range
+    a = (ctypes.c_int32 * 1)(0)
+    assert lib.tc_load_edges(a, a, 1, 0, tc.TC_PTR_HOST, None, None, ctypes.byref(out)) == tc.TC_ERR_OUT_OF_RANGE
+    assert out.value is None
+    # NULL handles
+    assert lib.tc_build(None, None) == tc.TC_ERR_INVALID_ARG
+    v = ctypes.c_uint64()
+    assert lib.tc_count(None, ctypes.byref(v), None) == tc.TC_ERR_INVALID_ARG
+    assert lib.tc_count_device(None, None, None) == tc.TC_ERR_INVALID_ARG
+    assert lib.tc_count_per_vertex(None, None, None, tc.TC_PTR_HOST, None) == tc.TC_ERR_INVALID_ARG
+    assert lib.tc_graph_get_info(None, None) == tc.TC_ERR_INVALID_ARG
+    assert lib.tc_copy_csr(None, None, None, None) == tc.TC_ERR_INVALID_ARG
+    assert lib.tc_count_batch(None, -1, None, None) == tc.TC_ERR_INVALID_ARG
+    assert lib.tc_count_batch(None, 0, None, None) == tc.TC_OK
+    lib.tc_free(None)  # no-op
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    import paper_1909_02127_gb300 as tc
+    saved = tc._lib
+    try:
+        tc._lib = None
+        with pytest.raises(RuntimeError, match="missing"):
+            tc.load_library(str(tmp_path / "nope.so"))
+    finally:
+        tc._lib = saved

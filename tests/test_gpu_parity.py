@@ -1,0 +1,269 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle (and closed forms), bit-exact.
+
+Counts are integers with a unique value, so every comparison here is equality (tolerance 0).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from tests import graphs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tc():
+    import torch
+    import paper_1909_02127_gb300 as tc
+    from paper_1909_02127_gb300 import build
+    build.build()
+    torch.cuda.init()
+    return tc
+
+
+def gpu_counts(tc, src, dst, n, device=True, per_vertex=True, allocator="torch"):
+    import torch
+    if device:
+        s = torch.as_tensor(np.asarray(src, dtype=np.int32)).cuda()
+        d = torch.as_tensor(np.asarray(dst, dtype=np.int32)).cuda()
+    else:
+        s, d = np.asarray(src, dtype=np.int32), np.asarray(dst, dtype=np.int32)
+    g = tc.tc_load_edges(s, d, n, allocator=allocator)
+    try:
+        tc.tc_build(g)
+        T = tc.tc_count(g)
+        t = None
+        if per_vertex:
+            T2, t = tc.tc_count_per_vertex(g)
+            assert T2 == T
+        info = tc.tc_graph_get_info(g)
+    finally:
+        tc.tc_free(g)
+    return T, t, info
+
+
+@pytest.mark.parametrize("name,g", graphs.closed_form_cases(), ids=lambda x: x if isinstance(x, str) else "")
+def test_closed_forms(tc, name, g):
+    src, dst, n, T, t = g
+    got, gt, info = gpu_counts(tc, src, dst, n)
+    assert got == T
+    if t is not None:
+        np.testing.assert_array_equal(gt, t)
+
+
+@pytest.mark.parametrize("n", [200, 1500, 4300])
+def test_complete_graph_block_and_wide_bins(tc, n):
+    """K_n: d+(u) runs from 0 to n-1, so sources land in the warp, block (d+ > 64) and wide (d+ > 4096) bins."""
+    src, dst, n, T, t = graphs.complete(n)
+    got, gt, info = gpu_counts(tc, src, dst, n)
+    assert got == math.comb(n, 3)
+    np.testing.assert_array_equal(gt, t)
+    assert info["bin_block"] > 0
+    if n > 4097:
+        assert info["bin_wide"] > 0
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_random_small_graphs(tc, seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.choice([1, 2, 3, 31, 33, 97, 1000, 5000, 9000, 20000]))
+    m = int(rng.integers(0, 8 * n + 1))
+    src, dst = graphs.random_simple_pairs(rng, n, m)
+    T, mm, t = oracle.count(src, dst, n, per_vertex=True)
+    got, gt, info = gpu_counts(tc, src, dst, n, device=bool(seed % 2))
+    assert got == T and info["num_edges"] == mm
+    np.testing.assert_array_equal(gt, t)
+
+
+def test_hub_heavy_graph(tc):
+    """One hub joined to everything plus a dense core: long N+(v) rows re-read by many sources."""
+    rng = np.random.default_rng(7)
+    n = 30000
+    hub_s = np.zeros(n - 1, dtype=np.int32)
+    hub_d = np.arange(1, n, dtype=np.int32)
+    core = rng.integers(1, 400, size=(60000, 2)).astype(np.int32)
+    rest = rng.integers(0, n, size=(100000, 2)).astype(np.int32)
+    src = np.concatenate([hub_s, core[:, 0], rest[:, 0]])
+    dst = np.concatenate([hub_d, core[:, 1], rest[:, 1]])
+    T, _, t = oracle.count(src, dst, n, per_vertex=True)
+    got, gt, _ = gpu_counts(tc, src, dst, n)
+    assert got == T
+    np.testing.assert_array_equal(gt, t)
+
+
+def test_ids_at_the_top_of_the_range(tc):
+    n = 100003
+    rng = np.random.default_rng(3)
+    src = (n - 1 - rng.integers(0, 300, size=20000)).astype(np.int32)
+    dst = (n - 1 - rng.integers(0, 300, size=20000)).astype(np.int32)
+    T, _, t = oracle.count(src, dst, n, per_vertex=True)
+    got, gt, _ = gpu_counts(tc, src, dst, n)
+    assert got == T
+    np.testing.assert_array_equal(gt, t)
+
+
+def test_duplicate_heavy_input(tc):
+    src, dst, n, T, t = graphs.complete(30)
+    src, dst = np.tile(np.concatenate([src, dst]), 50), np.tile(np.concatenate([dst, src]), 50)
+    T_ref, m_ref, t_ref = oracle.count(src, dst, n, per_vertex=True)
+    got, gt, info = gpu_counts(tc, src, dst, n)
+    assert got == T_ref and info["num_edges"] == m_ref
+    np.testing.assert_array_equal(gt, t_ref)
+
+
+def test_empty_and_degenerate(tc):
+    e = np.zeros(0, dtype=np.int32)
+    assert gpu_counts(tc, e, e, 0)[0] == 0
+    got, gt, info = gpu_counts(tc, e, e, 9)
+    assert got == 0 and not gt.any() and info["num_edges"] == 0
+    loops = np.arange(50, dtype=np.int32)
+    got, gt, info = gpu_counts(tc, loops, loops, 50)
+    assert got == 0 and info["num_edges"] == 0
+    one = np.array([0], dtype=np.int32)
+    assert gpu_counts(tc, one, one + 1, 2)[0] == 0
+
+
+@pytest.mark.parametrize("cfg", ["er4096"])
+def test_er4096_full(tc, cfg):
+    spec = graphgen.config(cfg)
+    hs, hd = spec.edges()
+    T, m, t = oracle.count(hs, hd, spec.n, per_vertex=True)
+    ds, dd = spec.edges(device="cuda")
+    g = tc.tc_load_edges(ds, dd, spec.n)
+    try:
+        tc.tc_build(g)
+        info = tc.tc_graph_get_info(g)
+        assert info["closing_test"] == 1 and info["num_edges"] == m
+        assert tc.tc_count(g) == T
+        T2, gt = tc.tc_count_per_vertex(g)
+        assert T2 == T
+        np.testing.assert_array_equal(gt, t)
+    finally:
+        tc.tc_free(g)
+
+
+@pytest.mark.parametrize("spec", [graphgen.rmat(16, 16, 11), graphgen.rmat(17, 8, 12, n=100000, permute=True),
+                                  graphgen.er(200000, 3000000, 13)], ids=["rmat16", "rmat17p", "er200k"])
+def test_medium_graphs(tc, spec):
+    hs, hd = spec.edges()
+    T, m, t = oracle.count(hs, hd, spec.n, per_vertex=True)
+    got, gt, info = gpu_counts(tc, hs, hd, spec.n)
+    assert got == T and info["num_edges"] == m
+    np.testing.assert_array_equal(gt, t)
+
+
+def test_rmat20_full(tc):
+    """R-MAT scale 20, edge factor 16: the benchmark workload, counted in the benchmark's launch configuration
+    (device-resident edges, one tc_count), every per-vertex count compared."""
+    import torch
+    spec = graphgen.config("rmat20")
+    hs, hd = spec.edges()
+    T, m, t = oracle.count(hs, hd, spec.n, per_vertex=True)
+    ds, dd = spec.edges(device="cuda")
+    g = tc.tc_load_edges(ds, dd, spec.n)
+    try:
+        tc.tc_build(g)
+        info = tc.tc_graph_get_info(g)
+        assert info["num_edges"] == m
+        assert tc.tc_count(g) == T
+        d_total = torch.zeros(1, dtype=torch.int64, device="cuda")
+        tc.tc_count_device(g, d_total)
+        assert int(d_total.item()) == T
+        T2, gt = tc.tc_count_per_vertex(g)
+        assert T2 == T
+        np.testing.assert_array_equal(gt, t)
+    finally:
+        tc.tc_free(g)
+
+
+def test_csr_structure(tc):
+    """The oriented CSR: m entries, rows ascending, each undirected edge once, oriented up the (deg, id) order."""
+    spec = graphgen.rmat(13, 12, 21)
+    hs, hd = spec.edges()
+    g = tc.tc_load_edges(hs, hd, spec.n)
+    try:
+        tc.tc_build(g)
+        off, col = tc.tc_copy_csr(g)
+        info = tc.tc_graph_get_info(g)
+    finally:
+        tc.tc_free(g)
+    n = spec.n
+    lo = np.minimum(hs, hd)
+    hi = np.maximum(hs, hd)
+    keep = lo != hi
+    und = np.unique(lo[keep].astype(np.int64) * n + hi[keep])
+    deg = np.bincount(np.concatenate([und // n, und % n]), minlength=n)
+    assert off[0] == 0 and off[-1] == und.size == col.size == info["num_edges"]
+    rows = np.repeat(np.arange(n), np.diff(off))
+    for r in np.unique(rows)[:2000]:
+        seg = col[off[r]:off[r + 1]]
+        assert np.all(np.diff(seg) > 0)
+    rank_r = deg[rows].astype(np.int64) * n + rows
+    rank_c = deg[col].astype(np.int64) * n + col
+    assert np.all(rank_r < rank_c)
+    got = np.sort(np.minimum(rows, col).astype(np.int64) * n + np.maximum(rows, col))
+    np.testing.assert_array_equal(got, und)
+    assert info["max_out_degree"] == np.diff(off).max()
+    # W = sum over oriented edges u->v of d+(v)
+    assert info["num_wedges"] == int(np.diff(off)[col].sum())
+
+
+def test_host_and_device_inputs_and_allocators_agree(tc):
+    spec = graphgen.rmat(14, 10, 31)
+    hs, hd = spec.edges()
+    ref = oracle.count(hs, hd, spec.n)[0]
+    for device in (False, True):
+        for allocator in ("torch", None):
+            assert gpu_counts(tc, hs, hd, spec.n, device=device, per_vertex=False, allocator=allocator)[0] == ref
+
+
+def test_errors(tc):
+    import torch
+    s = torch.tensor([0, 1, 5], dtype=torch.int32, device="cuda")
+    d = torch.tensor([1, 2, 0], dtype=torch.int32, device="cuda")
+    with pytest.raises(tc.TCError) as e:
+        tc.tc_load_edges(s, d, 5)
+    assert e.value.status == tc.TC_ERR_OUT_OF_RANGE
+    with pytest.raises(tc.TCError) as e:
+        tc.tc_load_edges(s - 1, d, 6)
+    assert e.value.status == tc.TC_ERR_OUT_OF_RANGE
+    g = tc.tc_load_edges(s, d, 6)
+    try:
+        with pytest.raises(tc.TCError) as e:
+            tc.tc_count(g)
+        assert e.value.status == tc.TC_ERR_STATE
+        tc.tc_build(g)
+        tc.tc_build(g)  # idempotent
+        assert tc.tc_count(g) == 0
+    finally:
+        tc.tc_free(g)
+
+
+def test_batch_equals_solo(tc):
+    specs = graphgen.batch_mix(48)
+    extra = [graphs.complete(150), graphs.wheel(40), graphs.complete(5000)]
+    handles, expect = [], []
+    try:
+        for sp in specs:
+            hs, hd = sp.edges()
+            handles.append(tc.tc_load_edges(hs, hd, sp.n))
+            tc.tc_build(handles[-1])
+            expect.append(oracle.count(hs, hd, sp.n)[0])
+        for src, dst, n, T, _ in extra:
+            handles.append(tc.tc_load_edges(src, dst, n))
+            tc.tc_build(handles[-1])
+            expect.append(T)
+        solo = [tc.tc_count(h) for h in handles]
+        assert solo == expect
+        got = tc.tc_count_batch(handles)
+        assert got.tolist() == expect
+        # repeated handles and reversed order
+        rev = handles[::-1] + handles[:5]
+        got = tc.tc_count_batch(rev)
+        assert got.tolist() == expect[::-1] + expect[:5]
+    finally:
+        for h in handles:
+            tc.tc_free(h)
