@@ -40,7 +40,8 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="rmat20", choices=["rmat20", "rmat26", "er4096", "batch"])
+    p.add_argument("--workload", default="rmat20",
+                   help="rmat20 | rmat26 | er4096 | batch | rmat<scale> (other R-MAT scales, edge factor 16)")
     p.add_argument("--batch-graphs", type=int, default=4096)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -188,7 +189,7 @@ def algorithmic_bytes(info: dict, grid_ctas: int) -> float:
 
 
 def count_grid(info: dict) -> int:
-    want = info["bin_block"] + info["bin_wide"] + (info["bin_warp"] + 15) // 16
+    want = info["bin_block"] + (info["bin_warp"] + 15) // 16
     return int(max(1, min(want, 2 * 152)))
 
 

@@ -228,6 +228,9 @@ def config(name: str) -> GraphSpec:
         return rmat(20, 16, BASE_SEED + 1, name="R-MAT scale 20 ef 16")
     if name == "rmat26":
         return rmat(26, 16, BASE_SEED + 2, permute=True, name="R-MAT scale 26 ef 16 (permuted ids)")
+    if name.startswith("rmat") and name[4:].isdigit():  # other scales, for profiling and sweeps
+        scale = int(name[4:])
+        return rmat(scale, 16, BASE_SEED + 100 + scale, name=f"R-MAT scale {scale} ef 16")
     raise KeyError(name)
 
 

@@ -65,14 +65,14 @@ typedef struct tc_graph_info {
   int64_t num_vertices;    /* n */
   int64_t num_input_pairs; /* pairs given to tc_load_edges */
   int64_t num_edges;       /* m: distinct undirected edges after dropping self-loops and repeats */
+  int64_t csr_entries;     /* column entries of the oriented CSR, rows padded to a multiple of 4 */
   int64_t max_out_degree;  /* largest d+(u) in the (degree, id) orientation */
   int64_t num_wedges;      /* W = sum over oriented edges u->v of d+(v): the candidate 2-paths u->v->w */
   int64_t active_sources;  /* sources with d+(u) >= 2 and at least one candidate 2-path */
   int64_t bin_warp;        /* sources handled one warp each */
-  int64_t bin_block;       /* sources handled one thread block each (hash of N+(u) in shared memory) */
-  int64_t bin_wide;        /* sources whose N+(u) exceeds shared memory (closing test by binary search) */
+  int64_t bin_block;       /* sources handled one thread block each */
   int32_t built;           /* 1 after tc_build */
-  int32_t closing_test;    /* 0: hash of N+(u) in shared memory, 1: bitmap of N+(u) in shared memory */
+  int32_t reserved;
 } tc_graph_info;
 
 /*
@@ -141,12 +141,16 @@ TC_API tc_status tc_count_batch(tc_graph* const* gs, int32_t num_graphs, uint64_
 TC_API tc_status tc_graph_get_info(const tc_graph* g, tc_graph_info* info);
 
 /*
- * tc_copy_csr — copy the oriented CSR of a built graph to host memory, for inspection and tests.
- *   offsets  n+1 int64 row offsets; row u holds N+(u), the out-neighbours of u in the (degree, id) order.
- *   cols     m int32 column ids, ascending within each row.
+ * tc_copy_csr — copy the oriented CSR of a built graph to host memory, for inspection and tests (Sec. III-B: the
+ * graph is stored in CSR).  The CSR is in rank space: vertex r is the r-th vertex in the (degree, id) order, and
+ * row r holds N+(r), the ranks above r adjacent to it, ascending.  Each row starts at a multiple of 4 entries and
+ * is padded to a multiple of 4 with the value n.
+ *   offsets  n+1 int64 row offsets (host).
+ *   cols     csr_entries int32 column entries (host; see tc_graph_info.csr_entries), or NULL.
+ *   perm     n int32 (host), or NULL: perm[r] = the original id of rank r.
  * Synchronises `stream`.
  */
-TC_API tc_status tc_copy_csr(const tc_graph* g, int64_t* offsets, int32_t* cols, void* stream);
+TC_API tc_status tc_copy_csr(const tc_graph* g, int64_t* offsets, int32_t* cols, int32_t* perm, void* stream);
 
 /* tc_free — release g and all its device memory (stream-ordered on the last stream g used).  NULL is a no-op. */
 TC_API void tc_free(tc_graph* g);

@@ -37,9 +37,9 @@ class tc_allocator(ctypes.Structure):
 
 class tc_graph_info(ctypes.Structure):
     _fields_ = [("num_vertices", ctypes.c_int64), ("num_input_pairs", ctypes.c_int64), ("num_edges", ctypes.c_int64),
-                ("max_out_degree", ctypes.c_int64), ("num_wedges", ctypes.c_int64),
+                ("csr_entries", ctypes.c_int64), ("max_out_degree", ctypes.c_int64), ("num_wedges", ctypes.c_int64),
                 ("active_sources", ctypes.c_int64), ("bin_warp", ctypes.c_int64), ("bin_block", ctypes.c_int64),
-                ("bin_wide", ctypes.c_int64), ("built", ctypes.c_int32), ("closing_test", ctypes.c_int32)]
+                ("built", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 EXPORTED = ["tc_load_edges", "tc_build", "tc_count", "tc_count_device", "tc_count_per_vertex", "tc_count_batch",
@@ -74,7 +74,7 @@ def load_library(path: str = LIB_PATH):
     lib.tc_count_batch.restype = st
     lib.tc_graph_get_info.argtypes = [vp, ctypes.POINTER(tc_graph_info)]
     lib.tc_graph_get_info.restype = st
-    lib.tc_copy_csr.argtypes = [vp, vp, vp, vp]
+    lib.tc_copy_csr.argtypes = [vp, vp, vp, vp, vp]
     lib.tc_copy_csr.restype = st
     lib.tc_free.argtypes = [vp]
     lib.tc_free.restype = None
@@ -245,11 +245,15 @@ def tc_graph_get_info(g: int) -> dict:
 
 
 def tc_copy_csr(g: int, stream=None):
+    """Returns (offsets, cols, perm): the oriented CSR in rank space (rows padded to multiples of 4 with n) and
+    perm[r] = original id of rank r."""
     info = tc_graph_get_info(g)
-    off = np.zeros(info["num_vertices"] + 1, dtype=np.int64)
-    col = np.zeros(max(info["num_edges"], 1), dtype=np.int32)
-    _check(load_library().tc_copy_csr(g, off.ctypes.data, col.ctypes.data, _stream_ptr(stream)))
-    return off, col[: info["num_edges"]]
+    n = info["num_vertices"]
+    off = np.zeros(n + 1, dtype=np.int64)
+    col = np.zeros(max(info["csr_entries"], 1), dtype=np.int32)
+    perm = np.zeros(max(n, 1), dtype=np.int32)
+    _check(load_library().tc_copy_csr(g, off.ctypes.data, col.ctypes.data, perm.ctypes.data, _stream_ptr(stream)))
+    return off, col[: info["csr_entries"]], perm[:n]
 
 
 def tc_free(g: int) -> None:

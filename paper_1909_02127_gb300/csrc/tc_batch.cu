@@ -34,7 +34,7 @@ __device__ __forceinline__ int find_graph(const int64_t* p, int G, int64_t i) {
 
 __global__ void __launch_bounds__(kCountThreads, 2)
     k_count_batch(BatchTable t, unsigned long long* __restrict__ counts, unsigned long long* __restrict__ cursors) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint32_t ws[32];
   __shared__ unsigned long long red[kWarpsPerCTA];
   __shared__ long long s_idx;
@@ -43,9 +43,8 @@ __global__ void __launch_bounds__(kCountThreads, 2)
   const int64_t NB = __ldg(&t.pb[G]), NW = __ldg(&t.pw[G]);
 
   if (NB > 0) {
-    int32_t* tab = reinterpret_cast<int32_t*>(smem);
-    const dev::Rows r = dev::rows_at(smem + kBlockHashSlotsMax * 4, kBlockRows);
-    for (int i = tid; i < kBlockHashSlotsMax; i += kCountThreads) tab[i] = -1;
+    const dev::BlockRows br = dev::block_rows(smem);
+    dev::zero_words(smem, dev::kBlockBitmapWords, tid, kCountThreads);
     __syncthreads();
     while (true) {
       if (tid == 0) s_idx = (long long)atomicAdd(&cursors[0], 1ull);
@@ -55,7 +54,7 @@ __global__ void __launch_bounds__(kCountThreads, 2)
       if (i >= NB) break;
       const int g = find_graph(t.pb, G, i);
       const CsrView v = t.views[g];
-      unsigned long long h = dev::block_source<false>(v.list[i - __ldg(&t.pb[g])], v, tab, r, ws, nullptr);
+      unsigned long long h = dev::block_source<false>(v.list[i - __ldg(&t.pb[g])], v, smem, br, ws, nullptr);
       h = warp_sum(h);
       if (lane == 0) red[warp] = h;
       __syncthreads();
@@ -68,13 +67,9 @@ __global__ void __launch_bounds__(kCountThreads, 2)
     }
   }
   if (NW > 0) {
-    unsigned char* region = smem + warp * dev::kWarpRegion;
-    const dev::Rows r = dev::rows_at(region + kWarpHashSlots * 4, 32);
-    uint32_t* words = reinterpret_cast<uint32_t*>(region);
-    // the set region must start empty for whichever kind (bitmap 0 / hash -1) the first source uses; sources
-    // always leave it in their own empty state, so reset it whenever the kind changes
-    int kind = 0;  // 0: hash (-1 words), 1: bitmap (0 words)
-    for (int i = lane; i < kWarpHashSlots; i += 32) words[i] = 0xffffffffu;
+    uint32_t* region = smem + warp * dev::kWarpRegionWords;
+    const dev::Rows r = dev::warp_rows(region);
+    dev::zero_words(region, dev::kWarpBitmapWords, lane, 32);
     __syncwarp();
     int cur_g = -1;
     unsigned long long acc = 0;
@@ -95,17 +90,7 @@ __global__ void __launch_bounds__(kCountThreads, 2)
         }
         const CsrView v = t.views[g];
         const int32_t u = v.list[v.n - v.nw + (i - __ldg(&t.pw[g]))];
-        if (v.bitmap != kind) {
-          kind = v.bitmap;
-          const uint32_t empty = kind ? 0u : 0xffffffffu;
-          for (int k = lane; k < kWarpHashSlots; k += 32) words[k] = empty;
-          __syncwarp();
-        }
-        if (kind)
-          acc += dev::warp_source<false>(u, v, dev::BitSet{words}, words, kWarpHashSlots, 0u, r, nullptr);
-        else
-          acc += dev::warp_source<false>(u, v, dev::HashSet{reinterpret_cast<int32_t*>(words), kWarpHashSlots - 1, 24},
-                                         words, kWarpHashSlots, 0xffffffffu, r, nullptr);
+        acc += dev::warp_source<false>(u, v, region, r, nullptr);
       }
     }
     acc = warp_sum(acc);
@@ -169,14 +154,10 @@ extern "C" TC_API tc_status tc_count_batch(tc_graph* const* gs, int32_t num_grap
     t.pw = reinterpret_cast<const int64_t*>(base + views_bytes + pre_bytes);
     t.num_graphs = num_graphs;
     if (hpb[G] + hpw[G] > 0) {
-      static bool attr = false;
-      if (!attr) {
-        if ((st = cuda_status(cudaFuncSetAttribute(k_count_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   dev::kCountSmem),
-                              "smem attr")))
-          break;
-        attr = true;
-      }
+      if ((st = cuda_status(cudaFuncSetAttribute(k_count_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 dev::kCountSmem),
+                            "smem attr")))
+        break;
       const int64_t want = hpb[G] + (hpw[G] + kWarpsPerCTA - 1) / kWarpsPerCTA;
       const int grid = (int)(want < 2 * kNumSMs ? want : 2 * kNumSMs);
       k_count_batch<<<grid, kCountThreads, dev::kCountSmem, s>>>(t, counts, cursors); note_launch();

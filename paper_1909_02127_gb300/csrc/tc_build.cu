@@ -1,21 +1,20 @@
-// tc_build.cu — from an edge list to the oriented CSR and the source bins.
+// tc_build.cu — from an edge list to the oriented, relabelled CSR and the source bins.
 //
 // Steps (all on the caller's stream):
-//   pack      validate ids, drop self-loops, key = (min << B) | max                       (Def. 1: undirected)
+//   pack      validate ids, drop self-loops, key = (min << B) | max                     (Def. 1: undirected)
 //   sort      LSD radix sort on bits [0, 2B)
-//   unique    keep the first of each run of equal keys                                     (simple graph)
-//   degree    deg(x) = number of distinct edges at x                                       (NE, Sec. III-A)
-//   orient    edge {a,b} goes from the lower to the higher (deg, id): key (s << B) | d     (UMO, Sec. III-A/C)
-//   sort      stable radix sort on the s bits only; each row is then already ascending in d (see below)
-//   csr       int64 offsets by an exclusive scan of d+(s); int32 columns (padded to whole 16-byte quads)
-//   bins      w(u) = sum of d+(v) over v in N+(u); sources with d+(u) >= 2 and w(u) > 0 are kept (the
-//             2-look-ahead of Sec. III-C: a source needs two out-neighbours to close a triangle) and binned by
-//             d+(u) and w(u) into warp-per-source and block-per-source lists.
+//   unique    keep the first of each run of equal keys                                   (simple graph)
+//   degree    deg(x) = number of distinct edges at x                                     (NE = degree, Sec. III-A)
+//   rank      sort (deg, id) -> rank(x); perm[rank] = x                                   (the visiting order)
+//   relabel   edge {a,b} -> (min(rank a, rank b), max(...)): it now points up the order   (UMO, Sec. III-A/III-C)
+//   sort      full radix sort of the relabelled keys: rows by source, ascending targets
+//   csr       row lengths padded to a multiple of 4 (pad id n), int64 offsets by a scan, int32 columns
+//   bins      w(u) = padded work of u's second hops; sources with d+(u) >= 2 and a candidate 2-path are kept
+//             (the 2-look-ahead of Sec. III-C: a source needs two out-neighbours to close a triangle) and put in
+//             the warp bin, or in the block bin when w(u) is large.
 //
-// Why one stable pass on s suffices: the unique keys are sorted by (lo, hi).  Row s receives d < s from edges
-// (d, s), which appear in increasing d, all before the block lo = s; and d > s from edges (s, d), which appear
-// in increasing d inside that block.  The input order of row s's entries is therefore ascending in d, and a
-// stable sort on s keeps it.
+// Relabelling by rank gives the kernel two things: hubs get the highest ids, so a bitmap over the top ids answers
+// most closing-edge tests; and hub rows, which are re-read by many sources, sit together in memory.
 #include "tc_internal.cuh"
 #include "tc_prims.cuh"
 
@@ -24,7 +23,7 @@ namespace {
 
 __global__ void k_pack(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t len, int64_t n,
                        int B, uint64_t* __restrict__ keys, uint32_t* __restrict__ err) {
-  const uint64_t sentinel = (2 * B >= 64) ? ~0ull : ((1ull << (2 * B)) - 1ull);
+  const uint64_t sentinel = (1ull << (2 * B)) - 1ull;
   bool bad = false;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t a = src[i], b = dst[i];
@@ -86,7 +85,7 @@ __global__ void __launch_bounds__(kUThreads) k_unique_scatter(const uint64_t* __
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *m = (int64_t)part[blockIdx.x] + tot;
 }
 
-// ---- degree / orientation -------------------------------------------------------------------------------------
+// ---- degree, rank, relabel ---------------------------------------------------------------------------------
 // Warp-aggregated increment: lanes with the same target add once.
 __device__ __forceinline__ void agg_inc(int32_t* cnt, uint32_t idx, bool active) {
   const uint32_t key = active ? idx : 0xffffffffu;
@@ -106,8 +105,24 @@ __global__ void k_degree(const uint64_t* __restrict__ ukeys, int64_t m, int B, i
   }
 }
 
-__global__ void k_orient(const uint64_t* __restrict__ ukeys, int64_t m, int B, const int32_t* __restrict__ deg,
-                         uint64_t* __restrict__ okeys, int32_t* __restrict__ odeg) {
+// (deg << B) | id: ascending order of these keys is the (degree, id) order.
+__global__ void k_rank_keys(const int32_t* __restrict__ deg, int64_t n, int B, uint64_t* __restrict__ rkeys) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    rkeys[i] = ((uint64_t)(uint32_t)deg[i] << B) | (uint64_t)i;
+}
+
+__global__ void k_rank(const uint64_t* __restrict__ sorted, int64_t n, int B, int32_t* __restrict__ rank,
+                       int32_t* __restrict__ perm) {
+  const uint64_t mask = (1ull << B) - 1ull;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t id = (int32_t)(sorted[r] & mask);
+    rank[id] = (int32_t)r;
+    perm[r] = id;
+  }
+}
+
+__global__ void k_relabel(const uint64_t* __restrict__ ukeys, int64_t m, int B, const int32_t* __restrict__ rank,
+                          uint64_t* __restrict__ okeys, int32_t* __restrict__ odeg) {
   const uint64_t mask = (1ull << B) - 1ull;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < m; base += stride) {
@@ -116,23 +131,34 @@ __global__ void k_orient(const uint64_t* __restrict__ ukeys, int64_t m, int B, c
     uint32_t s = 0;
     if (ok) {
       const uint64_t k = ukeys[i];
-      const uint32_t lo = (uint32_t)(k >> B), hi = (uint32_t)(k & mask);
-      const int32_t dl = deg[lo], dh = deg[hi];
-      // (deg, id) order; lo < hi breaks ties
-      const bool lo_first = dl < dh || (dl == dh);
-      s = lo_first ? lo : hi;
-      const uint32_t d = lo_first ? hi : lo;
+      const uint32_t ra = (uint32_t)rank[k >> B], rb = (uint32_t)rank[k & mask];
+      s = ra < rb ? ra : rb;
+      const uint32_t d = ra < rb ? rb : ra;
       okeys[i] = ((uint64_t)s << B) | d;
     }
     agg_inc(odeg, s, ok);
   }
 }
 
-__global__ void k_columns(const uint64_t* __restrict__ okeys, int64_t m, int64_t padded, int B,
-                          int32_t* __restrict__ col) {
+__global__ void k_padded_len(const int32_t* __restrict__ odeg, int64_t n, int32_t* __restrict__ plen) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    plen[i] = (odeg[i] + 3) & ~3;
+}
+
+__global__ void k_fill(int32_t* __restrict__ p, int64_t len, int32_t value) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = value;
+}
+
+// Entry i of the sorted relabelled keys is the (i - ustart[s])-th out-neighbour of its source s.
+__global__ void k_columns(const uint64_t* __restrict__ okeys, int64_t m, int B, const int64_t* __restrict__ ustart,
+                          const int64_t* __restrict__ off, int32_t* __restrict__ col) {
   const uint64_t mask = (1ull << B) - 1ull;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < padded; i += (int64_t)gridDim.x * blockDim.x)
-    col[i] = i < m ? (int32_t)(okeys[i] & mask) : 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = okeys[i];
+    const int64_t s = (int64_t)(k >> B);
+    col[off[s] + (i - ustart[s])] = (int32_t)(k & mask);
+  }
 }
 
 // ---- work estimate and binning ----------------------------------------------------------------------------------
@@ -141,12 +167,13 @@ struct BinCounters {
   unsigned long long active;
   unsigned int nb;
   unsigned int nw;
-  unsigned int nwide;
   int max_out;
+  int pad;
 };
 
-__global__ void k_bins(const int64_t* __restrict__ off, const int32_t* __restrict__ col, int64_t n,
-                       int32_t* __restrict__ list, BinCounters* __restrict__ bc) {
+__global__ void k_bins(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                       const int64_t* __restrict__ ustart, int64_t n, int32_t* __restrict__ list,
+                       BinCounters* __restrict__ bc) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -154,33 +181,31 @@ __global__ void k_bins(const int64_t* __restrict__ off, const int32_t* __restric
   int dmax = 0;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
     const int64_t u = base + threadIdx.x;
-    int64_t d = 0, w = 0;
+    int64_t d = 0, wpad = 0, wtrue = 0;
     if (u < n) {
-      const int64_t b = off[u], e = off[u + 1];
-      d = e - b;
-      for (int64_t j = b; j < e; ++j) {
+      d = ustart[u + 1] - ustart[u];
+      const int64_t b = off[u];
+      for (int64_t j = b; j < b + d; ++j) {
         const int32_t v = col[j];
-        w += off[v + 1] - off[v];
+        wpad += off[v + 1] - off[v];
+        wtrue += ustart[v + 1] - ustart[v];
       }
     }
-    wsum += (unsigned long long)w;
+    wsum += (unsigned long long)wtrue;
     if (d > dmax) dmax = (int)d;
-    const bool keep = d >= 2 && w > 0;
-    const bool blk = keep && (d > kWarpMaxDeg || w > kBlockMinWork);
+    const bool keep = d >= 2 && wtrue > 0;
+    const bool blk = keep && wpad > kBlockMinWork;
     const bool wrp = keep && !blk;
     act += keep ? 1 : 0;
     const unsigned mb = __ballot_sync(kFull, blk);
     const unsigned mw = __ballot_sync(kFull, wrp);
-    const unsigned mx = __ballot_sync(kFull, keep && d > kBlockMaxDeg);
     unsigned pb = 0, pw = 0;
     if (lane == 0) {
       if (mb) pb = atomicAdd(&bc->nb, (unsigned)__popc(mb));
       if (mw) pw = atomicAdd(&bc->nw, (unsigned)__popc(mw));
-      if (mx) atomicAdd(&bc->nwide, (unsigned)__popc(mx));
     }
     pb = __shfl_sync(kFull, pb, 0);
     pw = __shfl_sync(kFull, pw, 0);
-    // block bin from the front of `list`, warp bin from the back
     if (blk) list[pb + __popc(mb & lt)] = (int32_t)u;
     if (wrp) list[n - 1 - (pw + __popc(mw & lt))] = (int32_t)u;
   }
@@ -194,13 +219,30 @@ __global__ void k_bins(const int64_t* __restrict__ off, const int32_t* __restric
   }
 }
 
+// Scatter of counts from rank space back to original ids.
+__global__ void k_unpermute(const unsigned long long* __restrict__ by_rank, const int32_t* __restrict__ perm,
+                            int64_t n, unsigned long long* __restrict__ by_id) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+    by_id[perm[r]] = by_rank[r];
+}
+
 }  // namespace
 
 tc_status pack_edges(tc_graph* g, const int32_t* src, const int32_t* dst, int64_t len, int64_t offset,
                      uint32_t* d_err, cudaStream_t s) {
   if (len <= 0) return TC_OK;
   k_pack<<<grid_for(len, 256), 256, 0, s>>>(src, dst, len, g->n, g->key_bits, g->keys.as<uint64_t>() + offset,
-                                            d_err); note_launch();
+                                            d_err);
+  note_launch();
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+tc_status unpermute_counts(const tc_graph* g, const uint64_t* by_rank, uint64_t* by_id, cudaStream_t s) {
+  if (g->n <= 0) return TC_OK;
+  k_unpermute<<<grid_for(g->n, 256), 256, 0, s>>>((const unsigned long long*)by_rank, g->perm.as<int32_t>(), g->n,
+                                                  (unsigned long long*)by_id);
+  note_launch();
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }
@@ -210,102 +252,127 @@ tc_status build_graph(tc_graph* g, cudaStream_t s) {
   const int B = g->key_bits;
   const int64_t M = g->num_pairs;
   const int64_t n = g->n;
-  const uint64_t sentinel = (2 * B >= 64) ? ~0ull : ((1ull << (2 * B)) - 1ull);
+  const int64_t n1 = n > 0 ? n : 1;
+  const uint64_t sentinel = (1ull << (2 * B)) - 1ull;
   tc_status st = TC_OK;
-  Buf alt, part, counters, deg, odeg, ukeys;
-  uint64_t* sorted = nullptr;
+  Buf alt, part, counters, deg, odeg, ukeys, okeys, rkeys, rkeys_alt, rank, ustart, plen;
   int64_t m = 0;
   BinCounters hb{};
+  int64_t total_padded = 0;
+  auto launched = [&](const char* what) {
+    note_launch();
+    return cuda_status(cudaGetLastError(), what);
+  };
 
-  // The pipeline below frees what it allocated on every path.
   do {
+    if ((st = buf_alloc(a, counters, 64, s))) break;
+    // ---- sort + unique: g->keys -> ukeys (m distinct undirected edges, sorted by (lo, hi)) ----
     if (M > 0) {
+      uint64_t* sorted = nullptr;
       if ((st = buf_alloc(a, alt, (size_t)M * 8, s))) break;
       if ((st = radix_sort_u64(a, g->keys.as<uint64_t>(), alt.as<uint64_t>(), M, 0, 2 * B, &sorted, s))) break;
-      // unique -> the other buffer
-      uint64_t* uout = sorted == g->keys.as<uint64_t>() ? alt.as<uint64_t>() : g->keys.as<uint64_t>();
+      const bool in_keys = sorted == g->keys.as<uint64_t>();
       const int64_t tiles = (M + kUTile - 1) / kUTile;
       if ((st = buf_alloc(a, part, (size_t)tiles * 4, s))) break;
-      if ((st = buf_alloc(a, counters, 64, s))) break;
-      k_unique_count<<<(unsigned)tiles, kUThreads, 0, s>>>(sorted, M, sentinel, part.as<uint32_t>()); note_launch();
-      if ((st = cuda_status(cudaGetLastError(), "k_unique_count"))) break;
+      k_unique_count<<<(unsigned)tiles, kUThreads, 0, s>>>(sorted, M, sentinel, part.as<uint32_t>());
+      if ((st = launched("k_unique_count"))) break;
       if ((st = exclusive_scan_u32(a, part.as<uint32_t>(), tiles, s))) break;
+      uint64_t* uout = in_keys ? alt.as<uint64_t>() : g->keys.as<uint64_t>();
       k_unique_scatter<<<(unsigned)tiles, kUThreads, 0, s>>>(sorted, M, sentinel, part.as<uint32_t>(), uout,
-                                                              counters.as<int64_t>()); note_launch();
-      if ((st = cuda_status(cudaGetLastError(), "k_unique_scatter"))) break;
+                                                              counters.as<int64_t>());
+      if ((st = launched("k_unique_scatter"))) break;
       if ((st = cuda_status(cudaMemcpyAsync(&m, counters.p, 8, cudaMemcpyDeviceToHost, s), "copy m"))) break;
       if ((st = cuda_status(cudaStreamSynchronize(s), "sync m"))) break;
-      // keep the unique keys in `ukeys`, drop the other buffer
-      if (uout == alt.as<uint64_t>()) {
+      buf_release(a, part, s);
+      // ukeys takes the buffer holding the unique keys; okeys the other one (free now)
+      if (in_keys) {
         ukeys = alt;
-        alt = Buf{};
+        okeys = g->keys;
       } else {
         ukeys = g->keys;
-        g->keys = Buf{};
+        okeys = alt;
       }
-      buf_release(a, part, s);
+      alt = Buf{};
+      g->keys = Buf{};
     }
     g->m = m;
-    // degrees and orientation
-    if ((st = buf_alloc(a, deg, (size_t)(n > 0 ? n : 1) * 4, s))) break;
-    if ((st = buf_alloc(a, odeg, (size_t)(n > 0 ? n : 1) * 4, s))) break;
-    if (n > 0) {
-      if ((st = cuda_status(cudaMemsetAsync(deg.p, 0, (size_t)n * 4, s), "memset deg"))) break;
-      if ((st = cuda_status(cudaMemsetAsync(odeg.p, 0, (size_t)n * 4, s), "memset odeg"))) break;
-    }
-    Buf okeys_buf;
+
+    // ---- degree and rank ----
+    if ((st = buf_alloc(a, deg, (size_t)n1 * 4, s))) break;
+    if ((st = buf_alloc(a, rank, (size_t)n1 * 4, s))) break;
+    if ((st = buf_alloc(a, g->perm, (size_t)n1 * 4, s))) break;
+    if ((st = cuda_status(cudaMemsetAsync(deg.p, 0, (size_t)n1 * 4, s), "memset deg"))) break;
     if (m > 0) {
-      k_degree<<<grid_for(m, 256), 256, 0, s>>>(ukeys.as<uint64_t>(), m, B, deg.as<int32_t>()); note_launch();
-      if ((st = cuda_status(cudaGetLastError(), "k_degree"))) break;
-      // orient into whichever of the two key buffers is free
-      Buf& free_buf = g->keys.p ? g->keys : alt;
-      okeys_buf = free_buf;
-      free_buf = Buf{};
-      k_orient<<<grid_for(m, 256), 256, 0, s>>>(ukeys.as<uint64_t>(), m, B, deg.as<int32_t>(),
-                                                okeys_buf.as<uint64_t>(), odeg.as<int32_t>()); note_launch();
-      if ((st = cuda_status(cudaGetLastError(), "k_orient"))) {
-        buf_release(a, okeys_buf, s);
-        break;
-      }
-      uint64_t* osorted = nullptr;
-      st = radix_sort_u64(a, okeys_buf.as<uint64_t>(), ukeys.as<uint64_t>(), m, B, 2 * B, &osorted, s);
-      if (st) {
-        buf_release(a, okeys_buf, s);
-        break;
-      }
-      const int64_t padded = ((m + 3) / 4) * 4 + 4;
-      if ((st = buf_alloc(a, g->col, (size_t)padded * 4, s))) {
-        buf_release(a, okeys_buf, s);
-        break;
-      }
-      k_columns<<<grid_for(padded, 256), 256, 0, s>>>(osorted, m, padded, B, g->col.as<int32_t>()); note_launch();
-      st = cuda_status(cudaGetLastError(), "k_columns");
-      buf_release(a, okeys_buf, s);
-      if (st) break;
+      k_degree<<<grid_for(m, 256), 256, 0, s>>>(ukeys.as<uint64_t>(), m, B, deg.as<int32_t>());
+      if ((st = launched("k_degree"))) break;
+    }
+    if (n > 0) {
+      if ((st = buf_alloc(a, rkeys, (size_t)n * 8, s))) break;
+      if ((st = buf_alloc(a, rkeys_alt, (size_t)n * 8, s))) break;
+      k_rank_keys<<<grid_for(n, 256), 256, 0, s>>>(deg.as<int32_t>(), n, B, rkeys.as<uint64_t>());
+      if ((st = launched("k_rank_keys"))) break;
+      uint64_t* rs = nullptr;
+      if ((st = radix_sort_u64(a, rkeys.as<uint64_t>(), rkeys_alt.as<uint64_t>(), n, 0, 2 * B, &rs, s))) break;
+      k_rank<<<grid_for(n, 256), 256, 0, s>>>(rs, n, B, rank.as<int32_t>(), g->perm.as<int32_t>());
+      if ((st = launched("k_rank"))) break;
+      buf_release(a, rkeys, s);
+      buf_release(a, rkeys_alt, s);
+    }
+    buf_release(a, deg, s);
+
+    // ---- relabel + sort: okeys = (rank s << B) | rank d with s < d, sorted ----
+    if ((st = buf_alloc(a, odeg, (size_t)n1 * 4, s))) break;
+    if ((st = cuda_status(cudaMemsetAsync(odeg.p, 0, (size_t)n1 * 4, s), "memset odeg"))) break;
+    uint64_t* osorted = nullptr;
+    if (m > 0) {
+      k_relabel<<<grid_for(m, 256), 256, 0, s>>>(ukeys.as<uint64_t>(), m, B, rank.as<int32_t>(),
+                                                 okeys.as<uint64_t>(), odeg.as<int32_t>());
+      if ((st = launched("k_relabel"))) break;
+      if ((st = radix_sort_u64(a, okeys.as<uint64_t>(), ukeys.as<uint64_t>(), m, 0, 2 * B, &osorted, s))) break;
+    }
+    buf_release(a, rank, s);
+
+    // ---- offsets: unpadded starts (ustart) and padded offsets (off) ----
+    if ((st = buf_alloc(a, ustart, (size_t)(n + 1) * 8, s))) break;
+    if ((st = buf_alloc(a, g->off, (size_t)(n + 1) * 8, s))) break;
+    if ((st = buf_alloc(a, plen, (size_t)n1 * 4, s))) break;
+    if (n > 0) {
+      if ((st = exclusive_scan_i32_to_i64(a, odeg.as<int32_t>(), ustart.as<int64_t>(), n, s))) break;
+      k_padded_len<<<grid_for(n, 256), 256, 0, s>>>(odeg.as<int32_t>(), n, plen.as<int32_t>());
+      if ((st = launched("k_padded_len"))) break;
+      if ((st = exclusive_scan_i32_to_i64(a, plen.as<int32_t>(), g->off.as<int64_t>(), n, s))) break;
     } else {
-      if ((st = buf_alloc(a, g->col, 16, s))) break;
-      if ((st = cuda_status(cudaMemsetAsync(g->col.p, 0, 16, s), "memset col"))) break;
+      if ((st = cuda_status(cudaMemsetAsync(ustart.p, 0, 8, s), "memset ustart"))) break;
+      if ((st = cuda_status(cudaMemsetAsync(g->off.p, 0, 8, s), "memset off"))) break;
+    }
+    buf_release(a, plen, s);
+    buf_release(a, odeg, s);
+    if ((st = cuda_status(cudaMemcpyAsync(&total_padded, g->off.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, s),
+                          "copy entries")))
+      break;
+    if ((st = cuda_status(cudaStreamSynchronize(s), "sync entries"))) break;
+    g->csr_entries = total_padded;
+
+    // ---- columns: fill with the pad id n, then scatter ----
+    const int64_t ncol = total_padded + 4;
+    if ((st = buf_alloc(a, g->col, (size_t)ncol * 4, s))) break;
+    k_fill<<<grid_for(ncol, 256), 256, 0, s>>>(g->col.as<int32_t>(), ncol, (int32_t)n);
+    if ((st = launched("k_fill"))) break;
+    if (m > 0) {
+      k_columns<<<grid_for(m, 256), 256, 0, s>>>(osorted, m, B, ustart.as<int64_t>(), g->off.as<int64_t>(),
+                                                 g->col.as<int32_t>());
+      if ((st = launched("k_columns"))) break;
     }
     buf_release(a, ukeys, s);
-    buf_release(a, alt, s);
-    buf_release(a, g->keys, s);
-    buf_release(a, deg, s);
-    // offsets
-    if ((st = buf_alloc(a, g->off, (size_t)(n + 1) * 8, s))) break;
-    if (n > 0) {
-      if ((st = exclusive_scan_i32_to_i64(a, odeg.as<int32_t>(), g->off.as<int64_t>(), n, s))) break;
-    } else if ((st = cuda_status(cudaMemsetAsync(g->off.p, 0, 8, s), "memset off"))) {
-      break;
-    }
-    buf_release(a, odeg, s);
-    // bins
-    if ((st = buf_alloc(a, g->list, (size_t)(n > 0 ? n : 1) * 4, s))) break;
-    if (!counters.p && (st = buf_alloc(a, counters, 64, s))) break;
+    buf_release(a, okeys, s);
+
+    // ---- bins ----
+    if ((st = buf_alloc(a, g->list, (size_t)n1 * 4, s))) break;
     if ((st = cuda_status(cudaMemsetAsync(counters.p, 0, sizeof(BinCounters), s), "memset bins"))) break;
     if (n > 0) {
-      k_bins<<<grid_for(n, 256), 256, 0, s>>>(g->off.as<int64_t>(), g->col.as<int32_t>(), n,
-                                              g->list.as<int32_t>(), counters.as<BinCounters>()); note_launch();
-      if ((st = cuda_status(cudaGetLastError(), "k_bins"))) break;
+      k_bins<<<grid_for(n, 256), 256, 0, s>>>(g->off.as<int64_t>(), g->col.as<int32_t>(), ustart.as<int64_t>(), n,
+                                              g->list.as<int32_t>(), counters.as<BinCounters>());
+      if ((st = launched("k_bins"))) break;
     }
     if ((st = cuda_status(cudaMemcpyAsync(&hb, counters.p, sizeof(BinCounters), cudaMemcpyDeviceToHost, s),
                           "copy bins")))
@@ -313,19 +380,14 @@ tc_status build_graph(tc_graph* g, cudaStream_t s) {
     if ((st = cuda_status(cudaStreamSynchronize(s), "sync bins"))) break;
   } while (0);
 
-  buf_release(a, alt, s);
-  buf_release(a, part, s);
-  buf_release(a, counters, s);
-  buf_release(a, deg, s);
-  buf_release(a, odeg, s);
-  buf_release(a, ukeys, s);
+  for (Buf* b : {&alt, &part, &counters, &deg, &odeg, &ukeys, &okeys, &rkeys, &rkeys_alt, &rank, &ustart, &plen})
+    buf_release(a, *b, s);
   buf_release(a, g->keys, s);
   if (st != TC_OK) return st;
   g->wedges = (int64_t)hb.wedges;
   g->active = (int64_t)hb.active;
   g->nb = hb.nb;
   g->nw = hb.nw;
-  g->nwide = hb.nwide;
   g->max_out_degree = hb.max_out;
   return TC_OK;
 }

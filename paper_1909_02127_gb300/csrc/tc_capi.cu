@@ -80,6 +80,7 @@ void release_all(tc_graph* g, cudaStream_t s) {
   buf_release(g->alloc, g->off, s);
   buf_release(g->alloc, g->col, s);
   buf_release(g->alloc, g->list, s);
+  buf_release(g->alloc, g->perm, s);
   buf_release(g->alloc, g->acc, s);
   if (g->host_total) {
     cudaFreeHost(g->host_total);
@@ -262,15 +263,23 @@ TC_API tc_status tc_count_per_vertex(tc_graph* g, uint64_t* per_vertex, uint64_t
   cudaStream_t s = (cudaStream_t)stream;
   g->last_stream = s;
   uint64_t* d_total = g->acc.as<uint64_t>();
-  Buf tmp;
-  uint64_t* d_pv = per_vertex;
-  if (flags == TC_PTR_HOST && g->n > 0) {
-    TC_TRY(buf_alloc(g->alloc, tmp, (size_t)g->n * 8, s));
-    d_pv = tmp.as<uint64_t>();
+  if (g->n == 0) {
+    TC_TRY(launch_count(g, d_total, nullptr, reinterpret_cast<uint32_t*>(d_total + 1), s));
+    TC_CUDA(cudaMemcpyAsync(g->host_total, d_total, 8, cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaStreamSynchronize(s));
+    if (out_total) *out_total = *g->host_total;
+    return TC_OK;
   }
-  tc_status st = launch_count(g, d_total, g->n > 0 ? d_pv : nullptr, reinterpret_cast<uint32_t*>(d_total + 1), s);
-  if (st == TC_OK && flags == TC_PTR_HOST && g->n > 0)
-    st = cuda_status(cudaMemcpyAsync(per_vertex, d_pv, (size_t)g->n * 8, cudaMemcpyDeviceToHost, s), "D2H t");
+  // counts are produced in rank space, then scattered to original ids
+  Buf tmp;
+  const bool host = flags == TC_PTR_HOST;
+  TC_TRY(buf_alloc(g->alloc, tmp, (size_t)g->n * 8 * (host ? 2 : 1), s));
+  uint64_t* by_rank = tmp.as<uint64_t>();
+  uint64_t* by_id = host ? by_rank + g->n : per_vertex;
+  tc_status st = launch_count(g, d_total, by_rank, reinterpret_cast<uint32_t*>(d_total + 1), s);
+  if (st == TC_OK) st = unpermute_counts(g, by_rank, by_id, s);
+  if (st == TC_OK && host)
+    st = cuda_status(cudaMemcpyAsync(per_vertex, by_id, (size_t)g->n * 8, cudaMemcpyDeviceToHost, s), "D2H t");
   if (st == TC_OK) st = cuda_status(cudaMemcpyAsync(g->host_total, d_total, 8, cudaMemcpyDeviceToHost, s), "D2H T");
   if (st == TC_OK) st = cuda_status(cudaStreamSynchronize(s), "tc_count_per_vertex sync");
   buf_release(g->alloc, tmp, s);
@@ -289,26 +298,27 @@ TC_API tc_status tc_graph_get_info(const tc_graph* g, tc_graph_info* info) {
   info->built = g->built ? 1 : 0;
   if (g->built) {
     info->num_edges = g->m;
+    info->csr_entries = g->csr_entries;
     info->max_out_degree = g->max_out_degree;
     info->num_wedges = g->wedges;
     info->active_sources = g->active;
     info->bin_warp = g->nw;
-    info->bin_block = g->nb - g->nwide;
-    info->bin_wide = g->nwide;
-    info->closing_test = g->n <= kBitmapMaxN ? 1 : 0;
+    info->bin_block = g->nb;
   }
   return TC_OK;
 }
 
-TC_API tc_status tc_copy_csr(const tc_graph* g, int64_t* offsets, int32_t* cols, void* stream) {
+TC_API tc_status tc_copy_csr(const tc_graph* g, int64_t* offsets, int32_t* cols, int32_t* perm, void* stream) {
   TC_TRY(check_built(g));
-  if (!offsets || (g->m > 0 && !cols)) {
-    set_error("tc_copy_csr: NULL output");
+  if (!offsets) {
+    set_error("tc_copy_csr: offsets is NULL");
     return TC_ERR_INVALID_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;
   TC_CUDA(cudaMemcpyAsync(offsets, g->off.p, (size_t)(g->n + 1) * 8, cudaMemcpyDeviceToHost, s));
-  if (g->m > 0) TC_CUDA(cudaMemcpyAsync(cols, g->col.p, (size_t)g->m * 4, cudaMemcpyDeviceToHost, s));
+  if (cols && g->csr_entries > 0)
+    TC_CUDA(cudaMemcpyAsync(cols, g->col.p, (size_t)g->csr_entries * 4, cudaMemcpyDeviceToHost, s));
+  if (perm && g->n > 0) TC_CUDA(cudaMemcpyAsync(perm, g->perm.p, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
   TC_CUDA(cudaStreamSynchronize(s));
   return TC_OK;
 }

@@ -7,15 +7,17 @@
 // Nothing is materialised: the 2-paths live in registers only, so Algorithm 1's Compute / Write_to_Partial /
 // Mask steps, which exist to store and compact intermediate matches, have no counterpart here.
 //
-// N+(u) is put in shared memory as a set (a hash table with linear probing, or a bitmap over [0, n) when n is
-// small; for very large N+(u), binary search in the sorted global row) and every w is tested against it.
+// Closing test.  Vertices are numbered by rank in the (degree, id) order, so the ids that occur most often as w
+// (targets of hub rows) are the highest ones.  N+(u) is marked in a shared-memory bitmap over the top ids
+// [base, n] (4 KB per warp, or 64 KB per CTA for heavy sources); a test is one shared load and a bit extract.
+// The rare w below base is looked up by binary search in the part of N+(u) below base, which is a prefix of the
+// sorted row.  Pad entries (id n) fall on bit n - base, which is never set.
 //
-// Load balance inside a source: the rows N+(v), v in N+(u), are concatenated and cut into 16-byte quads of the
-// column array (a row [rs, re) covers quads rs/4 .. (re-1)/4; elements outside the row are masked).  A warp walks
-// this quad stream 32 quads at a time, one int4 load per lane, so short rows do not leave lanes idle.  The row
-// that owns a lane's quad is found without a search: with the rows' quad prefix P (strictly increasing, empty
-// rows removed), the lanes that hold the next 32 rows OR together one bit per row start inside the window, and a
-// lane's owner is the current row plus the number of starts below it (a popcount).
+// Traversal.  Rows are 16-byte aligned and padded to whole quads, so every load is one aligned int4.  Rows of
+// >= kLongQuads quads are walked by a whole warp, 32 quads per step.  Shorter rows are concatenated and cut into
+// quads; a warp walks this stream 32 quads at a time, and the row owning a lane's quad is found without a
+// search: the lanes holding the next 32 rows OR together one bit per row start inside the window, and a lane's
+// owner is the current row plus the number of starts below it (a popcount).
 #pragma once
 
 #include "tc_internal.cuh"
@@ -24,88 +26,71 @@
 namespace tc {
 namespace dev {
 
-// Row descriptors in shared memory (structure of arrays).  Row k covers quads [q0, q0 + P[k+1] - P[k]) of the
-// column array and, inside that span, elements [lo, hi) (relative to 4*q0).
+// The closing-edge test against N+(u).
+template <bool LOW>
+struct Closing {
+  const uint32_t* bm;    // bit (x - base) set iff x in N+(u), for x in [base, n]
+  int32_t base;
+  const int32_t* low;    // N+(u) entries below base (sorted), LOW only
+  int32_t nlow;
+  __device__ __forceinline__ uint32_t operator()(int32_t w) const {
+    const int32_t t = w - base;
+    if (t >= 0) return (bm[t >> 5] >> (t & 31)) & 1u;
+    if (!LOW) return 0u;
+    int a = 0, b = nlow;
+    while (a < b) {
+      const int mid = (a + b) >> 1;
+      if (__ldg(&low[mid]) < w)
+        a = mid + 1;
+      else
+        b = mid;
+    }
+    return (a < nlow && __ldg(&low[a]) == w) ? 1u : 0u;
+  }
+};
+
+template <bool PV, class C>
+__device__ __forceinline__ uint32_t test_quad(const int4 q, const C& c, unsigned long long* pv, int32_t v) {
+  const uint32_t h0 = c(q.x), h1 = c(q.y), h2 = c(q.z), h3 = c(q.w);
+  if (PV) {
+    if (h0) atomicAdd(&pv[q.x], 1ull);
+    if (h1) atomicAdd(&pv[q.y], 1ull);
+    if (h2) atomicAdd(&pv[q.z], 1ull);
+    if (h3) atomicAdd(&pv[q.w], 1ull);
+    const uint32_t s = h0 + h1 + h2 + h3;
+    if (s) atomicAdd(&pv[v], (unsigned long long)s);
+    return s;
+  }
+  return h0 + h1 + h2 + h3;
+}
+
+// One long row (quads [q0, q0 + nq)) walked by the calling warp.
+template <bool PV, class C>
+__device__ __forceinline__ uint32_t long_row(const int4* __restrict__ col4, uint32_t q0, uint32_t nq, const C& c,
+                                             unsigned long long* pv, int32_t v) {
+  uint32_t hits = 0;
+  const int lane = threadIdx.x & 31;
+#pragma unroll 2
+  for (uint32_t q = lane; q < nq; q += 32) hits += test_quad<PV>(__ldg(&col4[q0 + q]), c, pv, v);
+  return hits;
+}
+
+// Short rows in shared memory: row k covers quads [q0[k], q0[k] + P[k+1] - P[k]); P is strictly increasing.
 struct Rows {
   uint32_t* q0;
   uint32_t* P;
-  uint32_t* lo;
-  uint32_t* hi;
   int32_t* v;
 };
 
-// Fibonacci hashing of a vertex id into 2^bits slots.
-struct HashSet {
-  int32_t* tab;
-  uint32_t mask;
-  int shift;
-  __device__ __forceinline__ uint32_t slot(int32_t k) const { return ((uint32_t)k * 2654435761u) >> shift; }
-  // The table always has more than twice as many slots as keys, so the probe sequences below end.
-  __device__ __forceinline__ void insert(int32_t k) const {
-    uint32_t s = slot(k);
-    while (true) {
-      const int32_t old = atomicCAS(&tab[s], -1, k);
-      if (old == -1) return;
-      s = (s + 1) & mask;
-    }
-  }
-  __device__ __forceinline__ bool contains(int32_t k) const {
-    uint32_t s = slot(k);
-    while (true) {
-      const int32_t x = tab[s];
-      if (x == k) return true;
-      if (x < 0) return false;
-      s = (s + 1) & mask;
-    }
-  }
-};
-
-struct BitSet {
-  uint32_t* bm;
-  __device__ __forceinline__ void insert(int32_t k) const { atomicOr(&bm[k >> 5], 1u << (k & 31)); }
-  __device__ __forceinline__ bool contains(int32_t k) const { return (bm[k >> 5] >> (k & 31)) & 1u; }
-};
-
-// Closing test by binary search in the sorted global row N+(u) (rows too long for shared memory).
-struct SortedGlobal {
-  const int32_t* a;
-  int32_t len;
-  __device__ __forceinline__ bool contains(int32_t k) const {
-    int lo = 0, hi = len;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (__ldg(&a[mid]) < k)
-        lo = mid + 1;
-      else
-        hi = mid;
-    }
-    return lo < len && __ldg(&a[lo]) == k;
-  }
-};
-
-template <bool PV, class Set>
-__device__ __forceinline__ void test_one(int32_t w, int e, uint32_t lo, uint32_t hi, const Set& set,
-                                         uint32_t& hits, unsigned long long* pv, int32_t v) {
-  if ((uint32_t)e >= lo && (uint32_t)e < hi && set.contains(w)) {
-    ++hits;
-    if (PV) {
-      atomicAdd(&pv[w], 1ull);
-      atomicAdd(&pv[v], 1ull);
-    }
-  }
-}
-
-// Walk quads [x0, x1) of the concatenated rows 0..R-1 with one warp.  Returns this lane's number of closed
-// 2-paths.
-template <bool PV, class Set>
+// Walk quads [x0, x1) of the concatenated short rows 0..R-1 with one warp.
+template <bool PV, class C>
 __device__ __forceinline__ uint32_t walk(const Rows& r, int R, uint32_t x0, uint32_t x1,
-                                         const int4* __restrict__ col4, const Set& set, unsigned long long* pv) {
+                                         const int4* __restrict__ col4, const C& c, unsigned long long* pv) {
   uint32_t hits = 0;
   if (x0 >= x1) return 0;
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
-  // cur = last row with P <= x0
-  int a = 0, b = R;
+  int a = 0, b = R;  // cur = last row with P <= x0
   while (a < b) {
     const int mid = (a + b) >> 1;
     if (r.P[mid] <= x0)
@@ -126,74 +111,106 @@ __device__ __forceinline__ uint32_t walk(const Rows& r, int R, uint32_t x0, uint
     const uint32_t x = base + lane;
     if (x < x1) {
       const int own = cur + __popc(starts & lt);
-      const uint32_t rel = x - r.P[own];
-      const int4 q = __ldg(&col4[r.q0[own] + rel]);
-      const uint32_t lo = r.lo[own], hi = r.hi[own];
-      const int32_t v = PV ? r.v[own] : 0;
-      const int e = 4 * (int)rel;
-      test_one<PV>(q.x, e + 0, lo, hi, set, hits, pv, v);
-      test_one<PV>(q.y, e + 1, lo, hi, set, hits, pv, v);
-      test_one<PV>(q.z, e + 2, lo, hi, set, hits, pv, v);
-      test_one<PV>(q.w, e + 3, lo, hi, set, hits, pv, v);
+      const int4 q = __ldg(&col4[r.q0[own] + (x - r.P[own])]);
+      hits += test_quad<PV>(q, c, pv, PV ? r.v[own] : 0);
     }
     cur += __popc(starts);
   }
   return hits;
 }
 
-// Row descriptor of v (or an empty row for v < 0).
+// Descriptor of row v (v = n is the pad id: no row).
 struct RowOf {
-  uint32_t q0, nq, lo, hi;
-  bool nonempty;
+  uint32_t q0, nq;
 };
-__device__ __forceinline__ RowOf row_of(const int64_t* __restrict__ off, int32_t v) {
-  RowOf r{0, 0, 0, 0, false};
-  if (v >= 0) {
+__device__ __forceinline__ RowOf row_of(const int64_t* __restrict__ off, int32_t v, int64_t n) {
+  RowOf r{0, 0};
+  if (v >= 0 && v < n) {
     const int64_t rs = __ldg(&off[v]), re = __ldg(&off[v + 1]);
-    if (re > rs) {
-      r.nonempty = true;
-      r.q0 = (uint32_t)(rs >> 2);
-      r.nq = (uint32_t)(((re + 3) >> 2) - (rs >> 2));
-      r.lo = (uint32_t)(rs - 4 * (rs >> 2));
-      r.hi = (uint32_t)(re - 4 * (rs >> 2));
-    }
+    r.q0 = (uint32_t)(rs >> 2);
+    r.nq = (uint32_t)((re - rs) >> 2);
   }
   return r;
 }
 
-// One source u, one warp.  `set` is the warp's private, empty set; it is emptied again before returning.
-template <bool PV, class Set>
-__device__ __forceinline__ uint32_t warp_source(int32_t u, const CsrView& g, const Set& set, uint32_t* words,
-                                                int nwords, uint32_t empty_word, const Rows& r,
-                                                unsigned long long* pv) {
+// Mark (set = true) or clear N+(u) ∩ [base, n) in a bitmap, with `stride` cooperating threads at index `t`;
+// returns this thread's count of entries below base.
+__device__ __forceinline__ uint32_t mark_row(const int32_t* __restrict__ row, int64_t len, int64_t n, int32_t base,
+                                             uint32_t* bm, bool set, int t, int stride) {
+  uint32_t low = 0;
+  for (int64_t i = t; i < len; i += stride) {
+    const int32_t x = __ldg(&row[i]);
+    if (x >= n) continue;
+    if (x >= base) {
+      const int32_t b = x - base;
+      if (set)
+        atomicOr(&bm[b >> 5], 1u << (b & 31));
+      else
+        bm[b >> 5] = 0u;
+    } else {
+      ++low;
+    }
+  }
+  return low;
+}
+
+// All second hops of source u for the calling warp, given its closing test.
+template <bool PV, class C>
+__device__ __forceinline__ uint32_t warp_hops(const CsrView& g, int64_t beg, int64_t len, const C& c, const Rows& r,
+                                              unsigned long long* pv) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
-  const int64_t beg = __ldg(&g.off[u]), end = __ldg(&g.off[u + 1]);
-  const int d = (int)(end - beg);
-  for (int i = lane; i < d; i += 32) set.insert(__ldg(&g.col[beg + i]));
-  __syncwarp();
-  uint32_t hits = 0;
   const int4* col4 = reinterpret_cast<const int4*>(g.col);
-  for (int vb = 0; vb < d; vb += 32) {
-    const int j = vb + lane;
-    const int32_t v = j < d ? __ldg(&g.col[beg + j]) : -1;
-    const RowOf ro = row_of(g.off, v);
-    const unsigned ne = __ballot_sync(kFull, ro.nonempty);
-    const uint32_t incl = warp_inclusive_scan(ro.nq);
-    const uint32_t Q = __shfl_sync(kFull, incl, 31);
-    if (ro.nonempty) {
-      const int k = __popc(ne & lt);
-      r.q0[k] = ro.q0;
-      r.P[k] = incl - ro.nq;
-      r.lo[k] = ro.lo;
-      r.hi[k] = ro.hi;
-      if (PV) r.v[k] = v;
+  uint32_t hits = 0;
+  for (int64_t vb = 0; vb < len; vb += 32) {
+    const int64_t j = vb + lane;
+    const int32_t v = j < len ? __ldg(&g.col[beg + j]) : (int32_t)g.n;
+    const RowOf ro = row_of(g.off, v, g.n);
+    const bool is_long = ro.nq >= (uint32_t)kLongQuads;
+    unsigned longs = __ballot_sync(kFull, is_long);
+    while (longs) {
+      const int k = __ffs(longs) - 1;
+      longs &= longs - 1;
+      const uint32_t q0 = __shfl_sync(kFull, ro.q0, k), nq = __shfl_sync(kFull, ro.nq, k);
+      const int32_t vk = PV ? __shfl_sync(kFull, v, k) : 0;
+      hits += long_row<PV>(col4, q0, nq, c, pv, vk);
     }
-    __syncwarp();
-    hits += walk<PV>(r, __popc(ne), 0, Q, col4, set, pv);
-    __syncwarp();
+    const bool is_short = ro.nq > 0 && !is_long;
+    const unsigned shorts = __ballot_sync(kFull, is_short);
+    if (shorts) {
+      const uint32_t nq = is_short ? ro.nq : 0u;
+      const uint32_t incl = warp_inclusive_scan(nq);
+      const uint32_t Q = __shfl_sync(kFull, incl, 31);
+      if (is_short) {
+        const int k = __popc(shorts & lt);
+        r.q0[k] = ro.q0;
+        r.P[k] = incl - nq;
+        if (PV) r.v[k] = v;
+      }
+      __syncwarp();
+      hits += walk<PV>(r, __popc(shorts), 0, Q, col4, c, pv);
+      __syncwarp();
+    }
   }
-  for (int i = lane; i < nwords; i += 32) words[i] = empty_word;
+  return hits;
+}
+
+// One source u, one warp.  bm is the warp's bitmap over [base_w, n] (all zero on entry and on return).
+template <bool PV>
+__device__ __forceinline__ uint32_t warp_source(int32_t u, const CsrView& g, uint32_t* bm, const Rows& r,
+                                                unsigned long long* pv) {
+  const int lane = threadIdx.x & 31;
+  const int64_t beg = __ldg(&g.off[u]), len = __ldg(&g.off[u + 1]) - beg;
+  const int32_t* row = g.col + beg;
+  const uint32_t nlow = warp_sum(mark_row(row, len, g.n, g.base_w, bm, true, lane, 32));
+  __syncwarp();
+  uint32_t hits;
+  if (nlow == 0)
+    hits = warp_hops<PV>(g, beg, len, Closing<false>{bm, g.base_w, row, 0}, r, pv);
+  else
+    hits = warp_hops<PV>(g, beg, len, Closing<true>{bm, g.base_w, row, (int32_t)nlow}, r, pv);
+  __syncwarp();
+  mark_row(row, len, g.n, g.base_w, bm, false, lane, 32);
   __syncwarp();
   if (PV) {
     const uint32_t s = warp_sum(hits);
@@ -202,52 +219,67 @@ __device__ __forceinline__ uint32_t warp_source(int32_t u, const CsrView& g, con
   return hits;
 }
 
-// One source u, the whole block.  `tab` is the block's hash region (kBlockHashSlotsMax slots, all -1 on entry and
-// on return); `ws` is shared scratch for block scans (32 entries).
-template <bool PV>
-__device__ __forceinline__ uint32_t block_source(int32_t u, const CsrView& g, int32_t* tab, const Rows& r,
-                                                 uint32_t* ws, unsigned long long* pv) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t beg = __ldg(&g.off[u]), end = __ldg(&g.off[u + 1]);
-  const int d = (int)(end - beg);
-  const bool wide = d > kBlockMaxDeg;
-  int slots = 256, bits = 8;
-  while (slots < 2 * d && slots < kBlockHashSlotsMax) {
-    slots <<= 1;
-    ++bits;
-  }
-  const HashSet hs{tab, (uint32_t)(slots - 1), 32 - bits};
-  const SortedGlobal gs{g.col + beg, d};
-  if (!wide)
-    for (int i = tid; i < d; i += kCountThreads) hs.insert(__ldg(&g.col[beg + i]));
-  __syncthreads();
-  uint32_t hits = 0;
+// Block-mode staging of one chunk of rows: long rows (q0, nq, v) and short rows (q0, P, v).
+struct BlockRows {
+  uint32_t* lq0;
+  uint32_t* lnq;
+  int32_t* lv;
+  Rows sr;
+};
+
+template <bool PV, class C>
+__device__ __forceinline__ uint32_t block_hops(const CsrView& g, int64_t beg, int64_t len, const C& c,
+                                               const BlockRows& br, uint32_t* ws, unsigned long long* pv) {
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int4* col4 = reinterpret_cast<const int4*>(g.col);
-  for (int cb = 0; cb < d; cb += kBlockRows) {
-    const int j = cb + tid;
-    const int32_t v = j < d ? __ldg(&g.col[beg + j]) : -1;
-    const RowOf ro = row_of(g.off, v);
-    uint32_t R, Q;
-    const uint32_t rank = block_exclusive_scan<uint32_t>(ro.nonempty ? 1u : 0u, ws, &R);
-    const uint32_t pre = block_exclusive_scan<uint32_t>(ro.nq, ws, &Q);
-    if (ro.nonempty) {
-      r.q0[rank] = ro.q0;
-      r.P[rank] = pre;
-      r.lo[rank] = ro.lo;
-      r.hi[rank] = ro.hi;
-      if (PV) r.v[rank] = v;
+  uint32_t hits = 0;
+  for (int64_t cb = 0; cb < len; cb += kBlockRows) {
+    const int64_t j = cb + tid;
+    const int32_t v = j < len ? __ldg(&g.col[beg + j]) : (int32_t)g.n;
+    const RowOf ro = row_of(g.off, v, g.n);
+    const bool is_long = ro.nq >= (uint32_t)kLongQuads;
+    const bool is_short = ro.nq > 0 && !is_long;
+    uint32_t NL, R, Q;
+    const uint32_t lrank = block_exclusive_scan<uint32_t>(is_long ? 1u : 0u, ws, &NL);
+    const uint32_t srank = block_exclusive_scan<uint32_t>(is_short ? 1u : 0u, ws, &R);
+    const uint32_t pre = block_exclusive_scan<uint32_t>(is_short ? ro.nq : 0u, ws, &Q);
+    if (is_long) {
+      br.lq0[lrank] = ro.q0;
+      br.lnq[lrank] = ro.nq;
+      if (PV) br.lv[lrank] = v;
+    }
+    if (is_short) {
+      br.sr.q0[srank] = ro.q0;
+      br.sr.P[srank] = pre;
+      if (PV) br.sr.v[srank] = v;
     }
     __syncthreads();
+    for (uint32_t k = warp; k < NL; k += kWarpsPerCTA)
+      hits += long_row<PV>(col4, br.lq0[k], br.lnq[k], c, pv, PV ? br.lv[k] : 0);
     const uint32_t per = (Q + kWarpsPerCTA - 1) / kWarpsPerCTA;
     const uint32_t x0 = min(Q, (uint32_t)warp * per), x1 = min(Q, x0 + per);
-    if (wide)
-      hits += walk<PV>(r, (int)R, x0, x1, col4, gs, pv);
-    else
-      hits += walk<PV>(r, (int)R, x0, x1, col4, hs, pv);
+    hits += walk<PV>(br.sr, (int)R, x0, x1, col4, c, pv);
     __syncthreads();
   }
-  if (!wide)
-    for (int i = tid; i < slots; i += kCountThreads) tab[i] = -1;
+  return hits;
+}
+
+// One source u, the whole block.  bm is the block's bitmap over [base_b, n] (all zero on entry and on return).
+template <bool PV>
+__device__ __forceinline__ uint32_t block_source(int32_t u, const CsrView& g, uint32_t* bm, const BlockRows& br,
+                                                 uint32_t* ws, unsigned long long* pv) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int64_t beg = __ldg(&g.off[u]), len = __ldg(&g.off[u + 1]) - beg;
+  const int32_t* row = g.col + beg;
+  uint32_t nlow;
+  block_exclusive_scan<uint32_t>(mark_row(row, len, g.n, g.base_b, bm, true, tid, kCountThreads), ws, &nlow);
+  // (the scan's barriers also publish the bitmap)
+  uint32_t hits;
+  if (nlow == 0)
+    hits = block_hops<PV>(g, beg, len, Closing<false>{bm, g.base_b, row, 0}, br, ws, pv);
+  else
+    hits = block_hops<PV>(g, beg, len, Closing<true>{bm, g.base_b, row, (int32_t)nlow}, br, ws, pv);
+  mark_row(row, len, g.n, g.base_b, bm, false, tid, kCountThreads);
   if (PV) {
     const uint32_t s = warp_sum(hits);
     if (lane == 0 && s) atomicAdd(&pv[u], (unsigned long long)s);
@@ -256,36 +288,51 @@ __device__ __forceinline__ uint32_t block_source(int32_t u, const CsrView& g, in
   return hits;
 }
 
-// Shared-memory layout of the counting kernel.
-constexpr int kBlockRowBytes = kBlockRows * 4 * 4 + (kBlockRows + 1) * 4;
-constexpr int kBlockSmem = kBlockHashSlotsMax * 4 + kBlockRowBytes;
-constexpr int kWarpRowBytes = 32 * 4 * 4 + 33 * 4;
-constexpr int kWarpRegion = kWarpHashSlots * 4 + kWarpRowBytes;
-constexpr int kWarpSmem = kWarpsPerCTA * kWarpRegion;
+// Shared-memory layout of the counting kernels.
+constexpr int kWarpBitmapWords = kWarpBitmapBits / 32 + kBitmapSlackWords;
+constexpr int kBlockBitmapWords = kBlockBitmapBits / 32 + kBitmapSlackWords;
+constexpr int kWarpRowWords = 32 + 33 + 32;                        // q0, P, v
+constexpr int kWarpRegionWords = kWarpBitmapWords + kWarpRowWords;
+constexpr int kWarpSmem = kWarpsPerCTA * kWarpRegionWords * 4;
+constexpr int kBlockRowWords = 3 * kBlockRows + (2 * kBlockRows + kBlockRows + 1);
+constexpr int kBlockSmem = (kBlockBitmapWords + kBlockRowWords) * 4;
 constexpr int kCountSmem = kBlockSmem > kWarpSmem ? kBlockSmem : kWarpSmem;
 
-__device__ __forceinline__ Rows rows_at(unsigned char* p, int cap) {
+__device__ __forceinline__ Rows warp_rows(uint32_t* region) {
   Rows r;
-  r.q0 = reinterpret_cast<uint32_t*>(p);
-  r.lo = r.q0 + cap;
-  r.hi = r.lo + cap;
-  r.v = reinterpret_cast<int32_t*>(r.hi + cap);
-  r.P = reinterpret_cast<uint32_t*>(r.v + cap);
+  r.q0 = region + kWarpBitmapWords;
+  r.P = r.q0 + 32;
+  r.v = reinterpret_cast<int32_t*>(r.P + 33);
   return r;
 }
 
-// Count the triangles of one graph, processing its block-bin sources first, then its warp-bin sources.
+__device__ __forceinline__ BlockRows block_rows(uint32_t* smem) {
+  BlockRows b;
+  uint32_t* p = smem + kBlockBitmapWords;
+  b.lq0 = p;
+  b.lnq = p + kBlockRows;
+  b.lv = reinterpret_cast<int32_t*>(p + 2 * kBlockRows);
+  b.sr.q0 = p + 3 * kBlockRows;
+  b.sr.v = reinterpret_cast<int32_t*>(p + 4 * kBlockRows);
+  b.sr.P = p + 5 * kBlockRows;
+  return b;
+}
+
+__device__ __forceinline__ void zero_words(uint32_t* p, int nwords, int t, int stride) {
+  for (int i = t; i < nwords; i += stride) p[i] = 0u;
+}
+
+// Count the triangles of one graph: block-bin sources first (one CTA each), then warp-bin sources.
 // cursors[0], cursors[1]: zeroed work counters of this graph.  Returns this thread's count.
 template <bool PV>
 __device__ __forceinline__ unsigned long long count_graph(const CsrView& g, unsigned long long* pv,
-                                                          uint32_t* cursors, unsigned char* smem, uint32_t* ws,
+                                                          uint32_t* cursors, uint32_t* smem, uint32_t* ws,
                                                           int* s_idx) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   unsigned long long acc = 0;
   if (g.nb > 0) {
-    int32_t* tab = reinterpret_cast<int32_t*>(smem);
-    const Rows r = rows_at(smem + kBlockHashSlotsMax * 4, kBlockRows);
-    for (int i = tid; i < kBlockHashSlotsMax; i += kCountThreads) tab[i] = -1;
+    const BlockRows br = block_rows(smem);
+    zero_words(smem, kBlockBitmapWords, tid, kCountThreads);
     __syncthreads();
     while (true) {
       if (tid == 0) *s_idx = (int)atomicAdd(&cursors[0], 1u);
@@ -293,15 +340,13 @@ __device__ __forceinline__ unsigned long long count_graph(const CsrView& g, unsi
       const int idx = *s_idx;
       __syncthreads();
       if (idx >= g.nb) break;
-      acc += block_source<PV>(g.list[idx], g, tab, r, ws, pv);
+      acc += block_source<PV>(g.list[idx], g, smem, br, ws, pv);
     }
   }
   if (g.nw > 0) {
-    unsigned char* region = smem + warp * kWarpRegion;
-    const Rows r = rows_at(region + kWarpHashSlots * 4, 32);
-    uint32_t* words = reinterpret_cast<uint32_t*>(region);
-    const uint32_t empty = g.bitmap ? 0u : 0xffffffffu;
-    for (int i = lane; i < kWarpHashSlots; i += 32) words[i] = empty;
+    uint32_t* region = smem + warp * kWarpRegionWords;
+    const Rows r = warp_rows(region);
+    zero_words(region, kWarpBitmapWords, lane, 32);
     __syncwarp();
     const int32_t* wlist = g.list + (g.n - g.nw);
     constexpr int kChunk = 4;
@@ -311,14 +356,7 @@ __device__ __forceinline__ unsigned long long count_graph(const CsrView& g, unsi
       idx = __shfl_sync(kFull, idx, 0);
       if (idx >= g.nw) break;
       const int e = min(idx + kChunk, g.nw);
-      for (int k = idx; k < e; ++k) {
-        const int32_t u = wlist[k];
-        if (g.bitmap)
-          acc += warp_source<PV>(u, g, BitSet{words}, words, kWarpHashSlots, empty, r, pv);
-        else
-          acc += warp_source<PV>(u, g, HashSet{reinterpret_cast<int32_t*>(words), kWarpHashSlots - 1, 24}, words,
-                                 kWarpHashSlots, empty, r, pv);
-      }
+      for (int k = idx; k < e; ++k) acc += warp_source<PV>(wlist[k], g, region, r, pv);
     }
   }
   return acc;

@@ -60,24 +60,25 @@ void buf_release(const Allocator& a, Buf& b, cudaStream_t s);
 // ------------------------------------------------------------------------------------------------------------
 constexpr int kCountThreads = 512;                 // threads per CTA of the counting kernel
 constexpr int kWarpsPerCTA = kCountThreads / 32;
-constexpr int kWarpHashSlots = 256;                // per-warp hash of N+(u): d+(u) <= kWarpMaxDeg
-constexpr int kWarpMaxDeg = 64;
-constexpr int kBlockHashSlotsMax = 8192;           // per-CTA hash of N+(u): d+(u) <= kBlockMaxDeg
-constexpr int kBlockMaxDeg = kBlockHashSlotsMax / 2;
-constexpr int kBlockRows = 512;                    // rows (v in N+(u)) staged per CTA pass
-constexpr int64_t kBlockMinWork = 1 << 15;         // w(u) above this goes to a whole CTA
-constexpr int kBitmapMaxN = kWarpHashSlots * 32;   // n <= this: per-warp bitmap of N+(u) instead of a hash
+constexpr int kWarpBitmapBits = 1 << 15;           // per-warp bitmap of N+(u) over the top 32768 ranks (4 KB)
+constexpr int kBlockBitmapBits = 1 << 19;          // per-CTA bitmap of N+(u) over the top 524288 ranks (64 KB)
+constexpr int kBitmapSlackWords = 32;              // room for the padding id n (its bit is never set)
+constexpr int kBlockRows = kCountThreads;          // rows (v in N+(u)) staged per CTA pass
+constexpr int kLongQuads = 16;                     // rows of >= 16 quads (64 ids) are walked by a whole warp
+constexpr int64_t kBlockMinWork = 1 << 15;         // sources with more candidate 2-paths go to a whole CTA
 
-// Per-graph view used by the counting kernels.
+// Per-graph view used by the counting kernels.  Vertices are relabelled by rank in the (degree, id) order, so
+// every oriented edge goes from a lower to a higher id and rows hold ascending ids.  Rows start on 16-byte
+// boundaries and are padded to a multiple of 4 entries with the id n, which no bitmap ever marks.
 struct CsrView {
-  const int64_t* off;   // n+1 row offsets
-  const int32_t* col;   // m column ids (+ padding to a multiple of 4, 16-byte aligned)
-  const int32_t* list;  // active sources: [0, nb) block bin, [nb, nb+nw) warp bin
+  const int64_t* off;   // n+1 padded row offsets (multiples of 4)
+  const int32_t* col;   // off[n] column ids (+ one spare quad)
+  const int32_t* list;  // sources: [0, nb) block bin, [n - nw, n) warp bin
   int64_t n;
-  int32_t nb;           // block-bin sources (includes wide ones)
+  int32_t nb;           // block-bin sources
   int32_t nw;           // warp-bin sources
-  int32_t bitmap;       // 1: closing test by per-warp bitmap over [0, n)
-  int32_t pad;
+  int32_t base_w;       // per-warp bitmap covers ids [base_w, n]
+  int32_t base_b;       // per-CTA bitmap covers ids [base_b, n]
 };
 
 // ------------------------------------------------------------------------------------------------------------
@@ -112,10 +113,12 @@ struct tc_graph {
   int64_t max_out_degree = 0;
   int64_t wedges = 0;
   int64_t active = 0;
-  int64_t nb = 0, nw = 0, nwide = 0;
-  tc::Buf off;               // int64[n+1]
-  tc::Buf col;               // int32[round_up(m,4)+4]
-  tc::Buf list;              // int32[nb + nw]
+  int64_t nb = 0, nw = 0;
+  int64_t csr_entries = 0;   // off[n]: column entries including padding
+  tc::Buf off;               // int64[n+1], padded row offsets
+  tc::Buf col;               // int32[csr_entries + 4]
+  tc::Buf list;              // int32[n]: block bin at the front, warp bin at the back
+  tc::Buf perm;              // int32[n]: perm[r] = original id of the vertex of rank r
   tc::Buf acc;               // uint64 scratch word(s) for counting: [0] total, [1..2] work cursors
   uint64_t* host_total = nullptr;  // pinned 8-byte landing slot
   tc::CsrView view() const {
@@ -126,8 +129,8 @@ struct tc_graph {
     v.n = n;
     v.nb = (int32_t)nb;
     v.nw = (int32_t)nw;
-    v.bitmap = n <= tc::kBitmapMaxN ? 1 : 0;
-    v.pad = 0;
+    v.base_w = (int32_t)(n > tc::kWarpBitmapBits ? n - tc::kWarpBitmapBits : 0);
+    v.base_b = (int32_t)(n > tc::kBlockBitmapBits ? n - tc::kBlockBitmapBits : 0);
     return v;
   }
 };
@@ -137,7 +140,11 @@ namespace tc {
 tc_status pack_edges(tc_graph* g, const int32_t* src, const int32_t* dst, int64_t len, int64_t offset,
                      uint32_t* d_err, cudaStream_t s);
 tc_status build_graph(tc_graph* g, cudaStream_t s);
+// by_id[perm[r]] = by_rank[r] for the n vertices (device arrays)
+tc_status unpermute_counts(const tc_graph* g, const uint64_t* by_rank, uint64_t* by_id, cudaStream_t s);
 // tc_count.cu
+// d_per_vertex (if not null) receives counts in rank space.
 tc_status launch_count(const tc_graph* g, uint64_t* d_total, uint64_t* d_per_vertex, uint32_t* d_cursors,
                        cudaStream_t s);
+int count_grid(const tc_graph* g);
 }  // namespace tc

@@ -74,7 +74,7 @@ def test_argument_errors_without_gpu(lib):
     assert lib.tc_count_device(None, None, None) == tc.TC_ERR_INVALID_ARG
     assert lib.tc_count_per_vertex(None, None, None, tc.TC_PTR_HOST, None) == tc.TC_ERR_INVALID_ARG
     assert lib.tc_graph_get_info(None, None) == tc.TC_ERR_INVALID_ARG
-    assert lib.tc_copy_csr(None, None, None, None) == tc.TC_ERR_INVALID_ARG
+    assert lib.tc_copy_csr(None, None, None, None, None) == tc.TC_ERR_INVALID_ARG
     assert lib.tc_count_batch(None, -1, None, None) == tc.TC_ERR_INVALID_ARG
     assert lib.tc_count_batch(None, 0, None, None) == tc.TC_OK
     lib.tc_free(None)  # no-op
