@@ -45,6 +45,7 @@ __global__ void __launch_bounds__(kCountThreads, 2)
   if (NB > 0) {
     const dev::BlockRows br = dev::block_rows(smem);
     dev::zero_words(smem, dev::kBlockBitmapWords, tid, kCountThreads);
+    for (int k = tid; k < kBlockLowSlots; k += kCountThreads) br.ltab[k] = -1;
     __syncthreads();
     while (true) {
       if (tid == 0) s_idx = (long long)atomicAdd(&cursors[0], 1ull);
@@ -69,7 +70,9 @@ __global__ void __launch_bounds__(kCountThreads, 2)
   if (NW > 0) {
     uint32_t* region = smem + warp * dev::kWarpRegionWords;
     const dev::Rows r = dev::warp_rows(region);
+    int32_t* ltab = dev::warp_low(region);
     dev::zero_words(region, dev::kWarpBitmapWords, lane, 32);
+    for (int k = lane; k < kWarpLowSlots; k += 32) ltab[k] = -1;
     __syncwarp();
     int cur_g = -1;
     unsigned long long acc = 0;
@@ -90,7 +93,7 @@ __global__ void __launch_bounds__(kCountThreads, 2)
         }
         const CsrView v = t.views[g];
         const int32_t u = v.list[v.n - v.nw + (i - __ldg(&t.pw[g]))];
-        acc += dev::warp_source<false>(u, v, region, r, nullptr);
+        acc += dev::warp_source<false>(u, v, region, ltab, r, nullptr);
       }
     }
     acc = warp_sum(acc);

@@ -10,14 +10,17 @@
 // Closing test.  Vertices are numbered by rank in the (degree, id) order, so the ids that occur most often as w
 // (targets of hub rows) are the highest ones.  N+(u) is marked in a shared-memory bitmap over the top ids
 // [base, n] (4 KB per warp, or 64 KB per CTA for heavy sources); a test is one shared load and a bit extract.
-// The rare w below base is looked up by binary search in the part of N+(u) below base, which is a prefix of the
-// sorted row.  Pad entries (id n) fall on bit n - base, which is never set.
+// The entries of N+(u) below base (a prefix of the sorted row) go into a small shared-memory hash (128 slots per
+// warp, 2048 per CTA), or, if they do not fit, are found by binary search in the row.  Pad entries (id n) fall
+// on bit n - base, which is never set.
 //
-// Traversal.  Rows are 16-byte aligned and padded to whole quads, so every load is one aligned int4.  Rows of
-// >= kLongQuads quads are walked by a whole warp, 32 quads per step.  Shorter rows are concatenated and cut into
-// quads; a warp walks this stream 32 quads at a time, and the row owning a lane's quad is found without a
-// search: the lanes holding the next 32 rows OR together one bit per row start inside the window, and a lane's
-// owner is the current row plus the number of starts below it (a popcount).
+// Traversal.  Rows are 16-byte aligned and padded to whole quads, so every load is one aligned int4.  In warp mode
+// rows of >= kLongQuads quads are walked by the whole warp, four 32-quad steps in flight; shorter rows are
+// concatenated and cut into quads, and a warp walks this stream 32 quads at a time.  The row owning a lane's quad
+// is found without a search: the lanes holding the next 32 rows OR together one bit per row start inside the
+// window, and a lane's owner is the current row plus the number of starts below it (a popcount).  In block mode
+// the long rows of a 512-row chunk are handed to warps one at a time from a shared-memory counter, so no warp
+// waits at the chunk barrier behind another's long rows, and the short rows' stream is cut into equal shares.
 #pragma once
 
 #include "tc_internal.cuh"
@@ -26,17 +29,39 @@
 namespace tc {
 namespace dev {
 
+// Hash of a vertex id into 2^bits slots (Fibonacci hashing).
+__device__ __forceinline__ uint32_t low_slot(int32_t k, uint32_t mask) {
+  return (((uint32_t)k * 2654435761u) >> 16) & mask;
+}
+
+// How the entries of N+(u) below the bitmap window are looked up.
+enum LowMode { kLowNone = 0, kLowHash = 1, kLowSearch = 2 };
+
 // The closing-edge test against N+(u).
-template <bool LOW>
+template <int LOW>
 struct Closing {
   const uint32_t* bm;    // bit (x - base) set iff x in N+(u), for x in [base, n]
   int32_t base;
-  const int32_t* low;    // N+(u) entries below base (sorted), LOW only
-  int32_t nlow;
+  const int32_t* low;    // kLowSearch: N+(u) entries below base (sorted, global); kLowHash: open-addressing table
+  int32_t nlow;          // kLowSearch: number of entries; kLowHash: table mask
+  uint32_t cap;          // bitmap size in bits: bit `cap` exists and is never set
+  __device__ __forceinline__ uint32_t bit(uint32_t t) const {
+    return __funnelshift_r(bm[t >> 5], 0u, t) & 1u;  // shift amount taken mod 32
+  }
   __device__ __forceinline__ uint32_t operator()(int32_t w) const {
+    // w <= n always, so w - base <= cap; an id below base wraps to a huge value and is clamped to bit `cap`
+    if (LOW == kLowNone) return bit(min((uint32_t)(w - base), cap));
     const int32_t t = w - base;
-    if (t >= 0) return (bm[t >> 5] >> (t & 31)) & 1u;
-    if (!LOW) return 0u;
+    if (t >= 0) return bit((uint32_t)t);
+    if (LOW == kLowHash) {  // linear probing; the table is at most half full, so an empty slot ends the probe
+      uint32_t s = low_slot(w, (uint32_t)nlow);
+      while (true) {
+        const int32_t x = low[s];
+        if (x == w) return 1u;
+        if (x < 0) return 0u;
+        s = (s + 1) & (uint32_t)nlow;
+      }
+    }
     int a = 0, b = nlow;
     while (a < b) {
       const int mid = (a + b) >> 1;
@@ -48,6 +73,16 @@ struct Closing {
     return (a < nlow && __ldg(&low[a]) == w) ? 1u : 0u;
   }
 };
+
+// Insert the low entries row[0..nlow) (distinct ids) into an empty table of mask+1 slots, mask+1 >= 2*nlow.
+__device__ __forceinline__ void low_insert(const int32_t* __restrict__ row, int nlow, int32_t* tab, uint32_t mask,
+                                           int t, int stride) {
+  for (int i = t; i < nlow; i += stride) {
+    const int32_t k = __ldg(&row[i]);
+    uint32_t s = low_slot(k, mask);
+    while (atomicCAS(&tab[s], -1, k) != -1) s = (s + 1) & mask;
+  }
+}
 
 template <bool PV, class C>
 __device__ __forceinline__ uint32_t test_quad(const int4 q, const C& c, unsigned long long* pv, int32_t v) {
@@ -61,7 +96,7 @@ __device__ __forceinline__ uint32_t test_quad(const int4 q, const C& c, unsigned
     if (s) atomicAdd(&pv[v], (unsigned long long)s);
     return s;
   }
-  return h0 + h1 + h2 + h3;
+  return (h0 + h1) + (h2 + h3);
 }
 
 // One long row (quads [q0, q0 + nq)) walked by the calling warp.
@@ -70,8 +105,14 @@ __device__ __forceinline__ uint32_t long_row(const int4* __restrict__ col4, uint
                                              unsigned long long* pv, int32_t v) {
   uint32_t hits = 0;
   const int lane = threadIdx.x & 31;
-#pragma unroll 2
-  for (uint32_t q = lane; q < nq; q += 32) hits += test_quad<PV>(__ldg(&col4[q0 + q]), c, pv, v);
+  uint32_t q = lane;
+  for (; q + 96 < nq; q += 128) {  // four independent loads in flight per lane
+    const int4 a = __ldg(&col4[q0 + q]), b = __ldg(&col4[q0 + q + 32]);
+    const int4 e = __ldg(&col4[q0 + q + 64]), f = __ldg(&col4[q0 + q + 96]);
+    hits += (test_quad<PV>(a, c, pv, v) + test_quad<PV>(b, c, pv, v)) +
+            (test_quad<PV>(e, c, pv, v) + test_quad<PV>(f, c, pv, v));
+  }
+  for (; q < nq; q += 32) hits += test_quad<PV>(__ldg(&col4[q0 + q]), c, pv, v);
   return hits;
 }
 
@@ -195,20 +236,29 @@ __device__ __forceinline__ uint32_t warp_hops(const CsrView& g, int64_t beg, int
   return hits;
 }
 
-// One source u, one warp.  bm is the warp's bitmap over [base_w, n] (all zero on entry and on return).
+// One source u, one warp.  bm is the warp's bitmap over [base_w, n] (all zero on entry and on return); ltab its
+// low-entry hash (all -1 on entry and on return).
 template <bool PV>
-__device__ __forceinline__ uint32_t warp_source(int32_t u, const CsrView& g, uint32_t* bm, const Rows& r,
-                                                unsigned long long* pv) {
+__device__ __forceinline__ uint32_t warp_source(int32_t u, const CsrView& g, uint32_t* bm, int32_t* ltab,
+                                                const Rows& r, unsigned long long* pv) {
   const int lane = threadIdx.x & 31;
   const int64_t beg = __ldg(&g.off[u]), len = __ldg(&g.off[u + 1]) - beg;
   const int32_t* row = g.col + beg;
   const uint32_t nlow = warp_sum(mark_row(row, len, g.n, g.base_w, bm, true, lane, 32));
   __syncwarp();
+  constexpr uint32_t cap = (uint32_t)kWarpBitmapBits, lmask = (uint32_t)kWarpLowSlots - 1;
   uint32_t hits;
-  if (nlow == 0)
-    hits = warp_hops<PV>(g, beg, len, Closing<false>{bm, g.base_w, row, 0}, r, pv);
-  else
-    hits = warp_hops<PV>(g, beg, len, Closing<true>{bm, g.base_w, row, (int32_t)nlow}, r, pv);
+  if (nlow == 0) {
+    hits = warp_hops<PV>(g, beg, len, Closing<kLowNone>{bm, g.base_w, row, 0, cap}, r, pv);
+  } else if (nlow <= (uint32_t)kWarpLowSlots / 2) {
+    low_insert(row, (int)nlow, ltab, lmask, lane, 32);
+    __syncwarp();
+    hits = warp_hops<PV>(g, beg, len, Closing<kLowHash>{bm, g.base_w, ltab, (int32_t)lmask, cap}, r, pv);
+    __syncwarp();
+    for (int i = lane; i < kWarpLowSlots; i += 32) ltab[i] = -1;
+  } else {
+    hits = warp_hops<PV>(g, beg, len, Closing<kLowSearch>{bm, g.base_w, row, (int32_t)nlow, cap}, r, pv);
+  }
   __syncwarp();
   mark_row(row, len, g.n, g.base_w, bm, false, lane, 32);
   __syncwarp();
@@ -219,18 +269,20 @@ __device__ __forceinline__ uint32_t warp_source(int32_t u, const CsrView& g, uin
   return hits;
 }
 
-// Block-mode staging of one chunk of rows: long rows (q0, nq, v) and short rows (q0, P, v).
+// Block-mode staging of one chunk of rows: long rows (q0, nq, v), short rows as a quad stream, a work counter.
 struct BlockRows {
   uint32_t* lq0;
   uint32_t* lnq;
   int32_t* lv;
   Rows sr;
+  uint32_t* next;
+  int32_t* ltab;
 };
 
 template <bool PV, class C>
 __device__ __forceinline__ uint32_t block_hops(const CsrView& g, int64_t beg, int64_t len, const C& c,
                                                const BlockRows& br, uint32_t* ws, unsigned long long* pv) {
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int4* col4 = reinterpret_cast<const int4*>(g.col);
   uint32_t hits = 0;
   for (int64_t cb = 0; cb < len; cb += kBlockRows) {
@@ -253,9 +305,17 @@ __device__ __forceinline__ uint32_t block_hops(const CsrView& g, int64_t beg, in
       br.sr.P[srank] = pre;
       if (PV) br.sr.v[srank] = v;
     }
+    if (tid == 0) *br.next = 0;
     __syncthreads();
-    for (uint32_t k = warp; k < NL; k += kWarpsPerCTA)
+    // long rows: each warp takes the next untaken row (bounded by NL), so no warp idles behind a long tail
+    while (true) {
+      uint32_t k = 0;
+      if (lane == 0) k = atomicAdd(br.next, 1u);
+      k = __shfl_sync(kFull, k, 0);
+      if (k >= NL) break;
       hits += long_row<PV>(col4, br.lq0[k], br.lnq[k], c, pv, PV ? br.lv[k] : 0);
+    }
+    // short rows: equal contiguous shares of the quad stream
     const uint32_t per = (Q + kWarpsPerCTA - 1) / kWarpsPerCTA;
     const uint32_t x0 = min(Q, (uint32_t)warp * per), x1 = min(Q, x0 + per);
     hits += walk<PV>(br.sr, (int)R, x0, x1, col4, c, pv);
@@ -264,7 +324,8 @@ __device__ __forceinline__ uint32_t block_hops(const CsrView& g, int64_t beg, in
   return hits;
 }
 
-// One source u, the whole block.  bm is the block's bitmap over [base_b, n] (all zero on entry and on return).
+// One source u, the whole block.  bm is the block's bitmap over [base_b, n] (all zero on entry and on return);
+// br.ltab its low-entry hash (all -1 on entry and on return).
 template <bool PV>
 __device__ __forceinline__ uint32_t block_source(int32_t u, const CsrView& g, uint32_t* bm, const BlockRows& br,
                                                  uint32_t* ws, unsigned long long* pv) {
@@ -274,11 +335,18 @@ __device__ __forceinline__ uint32_t block_source(int32_t u, const CsrView& g, ui
   uint32_t nlow;
   block_exclusive_scan<uint32_t>(mark_row(row, len, g.n, g.base_b, bm, true, tid, kCountThreads), ws, &nlow);
   // (the scan's barriers also publish the bitmap)
+  constexpr uint32_t cap = (uint32_t)kBlockBitmapBits, lmask = (uint32_t)kBlockLowSlots - 1;
   uint32_t hits;
-  if (nlow == 0)
-    hits = block_hops<PV>(g, beg, len, Closing<false>{bm, g.base_b, row, 0}, br, ws, pv);
-  else
-    hits = block_hops<PV>(g, beg, len, Closing<true>{bm, g.base_b, row, (int32_t)nlow}, br, ws, pv);
+  if (nlow == 0) {
+    hits = block_hops<PV>(g, beg, len, Closing<kLowNone>{bm, g.base_b, row, 0, cap}, br, ws, pv);
+  } else if (nlow <= (uint32_t)kBlockLowSlots / 2) {
+    low_insert(row, (int)nlow, br.ltab, lmask, tid, kCountThreads);
+    __syncthreads();
+    hits = block_hops<PV>(g, beg, len, Closing<kLowHash>{bm, g.base_b, br.ltab, (int32_t)lmask, cap}, br, ws, pv);
+    for (int i = tid; i < kBlockLowSlots; i += kCountThreads) br.ltab[i] = -1;  // block_hops ended with a barrier
+  } else {
+    hits = block_hops<PV>(g, beg, len, Closing<kLowSearch>{bm, g.base_b, row, (int32_t)nlow, cap}, br, ws, pv);
+  }
   mark_row(row, len, g.n, g.base_b, bm, false, tid, kCountThreads);
   if (PV) {
     const uint32_t s = warp_sum(hits);
@@ -292,10 +360,10 @@ __device__ __forceinline__ uint32_t block_source(int32_t u, const CsrView& g, ui
 constexpr int kWarpBitmapWords = kWarpBitmapBits / 32 + kBitmapSlackWords;
 constexpr int kBlockBitmapWords = kBlockBitmapBits / 32 + kBitmapSlackWords;
 constexpr int kWarpRowWords = 32 + 33 + 32;                        // q0, P, v
-constexpr int kWarpRegionWords = kWarpBitmapWords + kWarpRowWords;
+constexpr int kWarpRegionWords = kWarpBitmapWords + kWarpRowWords + kWarpLowSlots;
 constexpr int kWarpSmem = kWarpsPerCTA * kWarpRegionWords * 4;
-constexpr int kBlockRowWords = 3 * kBlockRows + (2 * kBlockRows + kBlockRows + 1);
-constexpr int kBlockSmem = (kBlockBitmapWords + kBlockRowWords) * 4;
+constexpr int kBlockRowWords = 3 * kBlockRows + 2 * kBlockRows + (kBlockRows + 1) + 1;  // long, short, counter
+constexpr int kBlockSmem = (kBlockBitmapWords + kBlockRowWords + kBlockLowSlots) * 4;
 constexpr int kCountSmem = kBlockSmem > kWarpSmem ? kBlockSmem : kWarpSmem;
 
 __device__ __forceinline__ Rows warp_rows(uint32_t* region) {
@@ -304,6 +372,10 @@ __device__ __forceinline__ Rows warp_rows(uint32_t* region) {
   r.P = r.q0 + 32;
   r.v = reinterpret_cast<int32_t*>(r.P + 33);
   return r;
+}
+
+__device__ __forceinline__ int32_t* warp_low(uint32_t* region) {
+  return reinterpret_cast<int32_t*>(region + kWarpBitmapWords + kWarpRowWords);
 }
 
 __device__ __forceinline__ BlockRows block_rows(uint32_t* smem) {
@@ -315,6 +387,8 @@ __device__ __forceinline__ BlockRows block_rows(uint32_t* smem) {
   b.sr.q0 = p + 3 * kBlockRows;
   b.sr.v = reinterpret_cast<int32_t*>(p + 4 * kBlockRows);
   b.sr.P = p + 5 * kBlockRows;
+  b.next = p + 6 * kBlockRows + 1;
+  b.ltab = reinterpret_cast<int32_t*>(p + kBlockRowWords);
   return b;
 }
 
@@ -333,6 +407,7 @@ __device__ __forceinline__ unsigned long long count_graph(const CsrView& g, unsi
   if (g.nb > 0) {
     const BlockRows br = block_rows(smem);
     zero_words(smem, kBlockBitmapWords, tid, kCountThreads);
+    for (int i = tid; i < kBlockLowSlots; i += kCountThreads) br.ltab[i] = -1;
     __syncthreads();
     while (true) {
       if (tid == 0) *s_idx = (int)atomicAdd(&cursors[0], 1u);
@@ -346,7 +421,9 @@ __device__ __forceinline__ unsigned long long count_graph(const CsrView& g, unsi
   if (g.nw > 0) {
     uint32_t* region = smem + warp * kWarpRegionWords;
     const Rows r = warp_rows(region);
+    int32_t* ltab = warp_low(region);
     zero_words(region, kWarpBitmapWords, lane, 32);
+    for (int i = lane; i < kWarpLowSlots; i += 32) ltab[i] = -1;
     __syncwarp();
     const int32_t* wlist = g.list + (g.n - g.nw);
     constexpr int kChunk = 4;
@@ -356,7 +433,7 @@ __device__ __forceinline__ unsigned long long count_graph(const CsrView& g, unsi
       idx = __shfl_sync(kFull, idx, 0);
       if (idx >= g.nw) break;
       const int e = min(idx + kChunk, g.nw);
-      for (int k = idx; k < e; ++k) acc += warp_source<PV>(wlist[k], g, region, r, pv);
+      for (int k = idx; k < e; ++k) acc += warp_source<PV>(wlist[k], g, region, ltab, r, pv);
     }
   }
   return acc;

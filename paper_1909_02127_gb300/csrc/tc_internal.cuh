@@ -63,6 +63,8 @@ constexpr int kWarpsPerCTA = kCountThreads / 32;
 constexpr int kWarpBitmapBits = 1 << 15;           // per-warp bitmap of N+(u) over the top 32768 ranks (4 KB)
 constexpr int kBlockBitmapBits = 1 << 19;          // per-CTA bitmap of N+(u) over the top 524288 ranks (64 KB)
 constexpr int kBitmapSlackWords = 32;              // room for the padding id n (its bit is never set)
+constexpr int kWarpLowSlots = 128;                 // per-warp hash of N+(u) entries below the bitmap window
+constexpr int kBlockLowSlots = 2048;               // per-CTA hash of the same
 constexpr int kBlockRows = kCountThreads;          // rows (v in N+(u)) staged per CTA pass
 constexpr int kLongQuads = 16;                     // rows of >= 16 quads (64 ids) are walked by a whole warp
 constexpr int64_t kBlockMinWork = 1 << 15;         // sources with more candidate 2-paths go to a whole CTA

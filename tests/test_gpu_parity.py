@@ -93,6 +93,24 @@ def test_hub_heavy_graph(tc):
     np.testing.assert_array_equal(gt, t)
 
 
+def test_sources_with_many_entries_below_the_bitmap_window(tc):
+    """A clique K_101 of degree-100 vertices beside 32768 vertices of higher degree: the clique's ranks fall below
+    the per-warp bitmap window (the top 32768 ranks), so their sources have up to 100 out-neighbours below it and
+    take the binary-search closing test.  The clique adds exactly C(101, 3) triangles to those of the rest."""
+    rng = np.random.default_rng(17)
+    top = 32768
+    m_top = top * 110
+    ts = rng.integers(0, top, size=m_top).astype(np.int32)
+    td = rng.integers(0, top, size=m_top).astype(np.int32)
+    a, b = np.triu_indices(101, 1)
+    src = np.concatenate([ts, (a + top).astype(np.int32)])
+    dst = np.concatenate([td, (b + top).astype(np.int32)])
+    n = top + 101
+    T_top, _ = oracle.count(ts, td, top)
+    got, gt, info = gpu_counts(tc, src, dst, n, per_vertex=False)
+    assert got == T_top + math.comb(101, 3)
+
+
 def test_ids_at_the_top_of_the_range(tc):
     n = 100003
     rng = np.random.default_rng(3)
