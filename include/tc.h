@@ -129,6 +129,22 @@ TC_API tc_status tc_count_per_vertex(tc_graph* g, uint64_t* per_vertex, uint64_t
                                      void* stream);
 
 /*
+ * tc_count_per_vertex_noalloc — tc_count_per_vertex for callers that may not allocate device memory while they
+ * run (for example a serving loop that reserves all its memory at start-up, or a host whose device memory belongs
+ * to another framework's allocator).  The paper has no counterpart; this is an interface variant only.
+ * It allocates nothing: its scratch (the counts in rank space) is a file-scope device array of 2^20 uint64 entries
+ * (8 MiB) that every GPU which loads the library holds until the process exits.
+ *   d_per_vertex  n uint64 entries of DEVICE memory, overwritten with t(x).
+ *   d_total       one uint64 of DEVICE memory, overwritten with T.
+ * Graphs with more than 2^20 vertices are rejected with TC_ERR_INVALID_ARG (use tc_count_per_vertex).  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress) with that device current.  All calls
+ * on a device share the one array, and each call clears the part it uses before counting: calls whose GPU work
+ * overlaps (different streams, no ordering between them) race on it and give wrong results.  Asynchronous: the
+ * outputs are valid in stream order.
+ */
+TC_API tc_status tc_count_per_vertex_noalloc(tc_graph* g, uint64_t* d_per_vertex, uint64_t* d_total, void* stream);
+
+/*
  * tc_count_batch — count many built graphs in one persistent launch fed by a device work queue (the traversal of
  * tc_count applied to each graph independently; the batching itself has no counterpart in the paper).
  *   gs          num_graphs built graph handles (host array); the same handle may appear more than once.

@@ -42,7 +42,8 @@ class tc_graph_info(ctypes.Structure):
                 ("built", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
-EXPORTED = ["tc_load_edges", "tc_build", "tc_count", "tc_count_device", "tc_count_per_vertex", "tc_count_batch",
+EXPORTED = ["tc_load_edges", "tc_build", "tc_count", "tc_count_device", "tc_count_per_vertex",
+            "tc_count_per_vertex_noalloc", "tc_count_batch",
             "tc_graph_get_info", "tc_copy_csr", "tc_free", "tc_last_error", "tc_kernel_launches"]
 
 _lib = None
@@ -70,6 +71,8 @@ def load_library(path: str = LIB_PATH):
     lib.tc_count_device.restype = st
     lib.tc_count_per_vertex.argtypes = [vp, vp, u64p, u32, vp]
     lib.tc_count_per_vertex.restype = st
+    lib.tc_count_per_vertex_noalloc.argtypes = [vp, vp, vp, vp]
+    lib.tc_count_per_vertex_noalloc.restype = st
     lib.tc_count_batch.argtypes = [ctypes.POINTER(vp), i32, u64p, vp]
     lib.tc_count_batch.restype = st
     lib.tc_graph_get_info.argtypes = [vp, ctypes.POINTER(tc_graph_info)]
@@ -117,6 +120,7 @@ class _TorchAllocator:
 
     def __init__(self):
         self.live = {}
+        self.allocations = 0  # number of alloc callbacks served (diagnostic)
         self._alloc = tc_allocator._fields_[0][1](self._do_alloc)
         self._free = tc_allocator._fields_[1][1](self._do_free)
         self.struct = tc_allocator(self._alloc, self._free, None)
@@ -129,6 +133,7 @@ class _TorchAllocator:
                 t = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
             p = t.data_ptr()
             self.live[p] = (t, stream)
+            self.allocations += 1
             return p
         except Exception:
             return None
@@ -227,6 +232,15 @@ def tc_count_per_vertex(g: int, out=None, stream=None):
         flags = TC_PTR_DEVICE if out.is_cuda else TC_PTR_HOST
         _check(lib.tc_count_per_vertex(g, out.data_ptr(), ctypes.byref(total), flags, _stream_ptr(stream)))
     return int(total.value), out
+
+
+def tc_count_per_vertex_noalloc(g: int, d_per_vertex, d_total, stream=None) -> None:
+    """Per-vertex counts into caller-provided DEVICE memory, allocating nothing (scratch is a static device array
+    of 2^20 entries; larger graphs are rejected).  d_per_vertex: n 64-bit entries; d_total: one 64-bit entry.
+    Asynchronous on `stream`."""
+    pv = d_per_vertex if isinstance(d_per_vertex, int) else d_per_vertex.data_ptr()
+    tot = d_total if isinstance(d_total, int) else d_total.data_ptr()
+    _check(load_library().tc_count_per_vertex_noalloc(g, pv, tot, _stream_ptr(stream)))
 
 
 def tc_count_batch(gs: Sequence[int], stream=None) -> np.ndarray:
