@@ -43,6 +43,10 @@ def parse():
     p.add_argument("--workload", default="rmat20",
                    help="rmat20 | rmat26 | er4096 | batch | rmat<scale> (other R-MAT scales, edge factor 16)")
     p.add_argument("--batch-graphs", type=int, default=4096)
+    p.add_argument("--rate", type=float, default=2000.0, help="serve: mean request arrivals per second")
+    p.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
+    p.add_argument("--serve-pool", type=int, default=1024, help="serve: distinct request graphs")
+    p.add_argument("--build-workers", type=int, default=6, help="serve: concurrent CSR builders")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -408,6 +412,106 @@ def run_batch(args, dist: Dist):
     }
 
 
+def run_serve(args, dist: Dist):
+    """Replay one Poisson arrival trace against the serving loop twice: continuous batching, then one graph per
+    launch.  Every result is checked against the graph's solo count."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import graphgen
+    import paper_1909_02127_gb300 as tc
+
+    dev = torch.device("cuda", dist.local)
+    torch.cuda.set_device(dev)
+    pool = graphgen.serve_pool(args.serve_pool, graphgen.BASE_SEED + graphgen.SERVE_SEED_OFFSET + dist.rank * 7919)
+    sizes = np.array([sp.num_edges for sp in pool], dtype=np.int64)
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    total = int(offs[-1])
+    host = torch.empty(2 * total, dtype=torch.int32).pin_memory()
+    for i, sp in enumerate(pool):
+        s, d = sp.edges(device=dev)
+        host[offs[i]:offs[i + 1]].copy_(s)
+        host[total + offs[i]:total + offs[i + 1]].copy_(d)
+    torch.cuda.synchronize()
+    base = host.data_ptr()
+    src_ptr = [base + 4 * int(offs[i]) for i in range(len(pool))]
+    dst_ptr = [base + 4 * (total + int(offs[i])) for i in range(len(pool))]
+    solo = []
+    for i, sp in enumerate(pool):
+        g = tc.tc_load_edges(host[offs[i]:offs[i + 1]], host[total + offs[i]:total + offs[i + 1]], sp.n)
+        tc.tc_build(g)
+        solo.append(tc.tc_count(g))
+        tc.tc_free(g)
+    arrivals = graphgen.poisson_arrivals(args.rate, args.duration)
+    key = graphgen.stream_key(graphgen.BASE_SEED + graphgen.SERVE_SEED_OFFSET - 2, graphgen.STREAM_PARAMS)
+    half = len(pool) // 2
+    pick = [2 * (graphgen.draw(key, j) % half) + (j % 2) for j in range(len(arrivals))]
+
+    def replay(batching: bool):
+        srv = tc.tc_server_create(batching=batching, build_workers=args.build_workers)
+        results = []
+        done = threading.Event()
+        expected = len(arrivals)
+
+        def poller():
+            while len(results) < expected and not done.is_set():
+                results.extend(tc.tc_server_poll(srv, 8192, 20))
+
+        th = threading.Thread(target=poller)
+        th.start()
+        owner = {}
+        t0 = time.perf_counter()
+        for j, ta in enumerate(arrivals):
+            wait = t0 + ta - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            k = pick[j]
+            owner[tc.tc_server_submit(srv, src_ptr[k], dst_ptr[k], int(sizes[k]), pool[k].n)] = k
+        th.join(timeout=args.duration * 20 + 600)
+        done.set()
+        stats = tc.tc_server_get_stats(srv)
+        tc.tc_server_destroy(srv)
+        if len(results) != expected:
+            raise RuntimeError(f"serve: {len(results)} of {expected} requests finished")
+        bad = [r for r in results if r["status"] != 0 or r["triangles"] != solo[owner[r["id"]]]]
+        if bad:
+            raise RuntimeError(f"serve: {len(bad)} results differ from their solo counts")
+        lat = np.array([(r["t_done_ns"] - r["t_submit_ns"]) / 1e6 for r in results])
+        span = (max(r["t_done_ns"] for r in results) - min(r["t_submit_ns"] for r in results)) / 1e9
+        return {"graphs_per_s": round(expected / span, 2), "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                "p99_ms": round(float(np.percentile(lat, 99)), 3), "mean_ms": round(float(lat.mean()), 3),
+                "launches": stats["launches"], "max_batch": stats["max_batch_seen"],
+                "mean_batch": round(stats["completed"] / max(1, stats["launches"]), 2),
+                "peak_held_gb": round(stats["peak_held_bytes"] / 1e9, 3), "requests": expected,
+                "span_s": round(span, 3)}
+
+    clocks = ClockSampler(dist.local)
+    dist.barrier()
+    clocks.start()
+    l0 = tc.tc_kernel_launches()
+    batched = replay(True)
+    launches = tc.tc_kernel_launches() - l0
+    clock_info = clocks.stop()
+    single = replay(False)
+    units, secs = aggregate(batched["requests"], batched["span_s"], dist)
+    return {
+        "metric": "served graphs/s with p50/p99 latency (Poisson arrivals, continuous batching) vs one graph per launch",
+        "value": round(units / secs, 2), "unit": "graphs/s", "n_gpus": dist.world, "steps": 1, "warmup": 0,
+        "ms_per_step": round(batched["span_s"] * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32/uint64 (exact integer)", "data": "synthetic",
+        "config": {"workload": f"Poisson {args.rate:g} req/s for {args.duration:g} s over {len(pool)} R-MAT/ER "
+                               f"graphs, pairs log-uniform [1e3, 4e6]",
+                   "pool_pairs": total, "build_workers": args.build_workers, "parallelism": f"replicas x{dist.world}"},
+        "p50_ms": batched["p50_ms"], "p99_ms": batched["p99_ms"], "batched": batched, "one_by_one": single,
+        "speedup_vs_one_by_one": round(batched["graphs_per_s"] / single["graphs_per_s"], 3),
+        "e2e": {"value": round(units / secs, 2), "unit": "graphs/s",
+                "h2d_bytes_per_step": int(8 * sum(sizes[k] for k in pick)), "d2h_bytes_per_step": 8 * len(pick)},
+        "gpu_launches": int(launches), "clocks": clock_info,
+    }
+
+
 # ------------------------------------------------------------------------------------------------------------
 # Reference arm: the CPU oracle
 # ------------------------------------------------------------------------------------------------------------
@@ -416,7 +520,7 @@ def run_reference(args, dist: Dist):
     import oracle
     if dist.rank != 0:
         return None
-    if args.workload == "batch":
+    if args.workload in ("batch", "serve"):
         return {"impl": "reference", "unavailable": "the oracle arm is defined for the single-graph workloads"}
     spec = graphgen.config(args.workload)
     hs, hd = spec.edges()
@@ -456,7 +560,12 @@ def main():
     build.build()
     tc.load_library()
     dist.init("nccl")
-    out = run_batch(args, dist) if args.workload == "batch" else run_single(args, dist)
+    if args.workload == "batch":
+        out = run_batch(args, dist)
+    elif args.workload == "serve":
+        out = run_serve(args, dist)
+    else:
+        out = run_single(args, dist)
     dist.close()
     if dist.rank == 0:
         print(json.dumps(out), flush=True)

@@ -153,6 +153,68 @@ TC_API tc_status tc_count_per_vertex_noalloc(tc_graph* g, uint64_t* d_per_vertex
  */
 TC_API tc_status tc_count_batch(tc_graph* const* gs, int32_t num_graphs, uint64_t* out_counts, void* stream);
 
+/*
+ * Serving loop (no counterpart in the paper; it drives the traversal of tc_count for a stream of requests).
+ * A server admits submitted requests by device memory, builds their CSRs concurrently on its own streams, keeps
+ * them resident, and counts every graph that is ready whenever the previous launch finishes (continuous batching
+ * through tc_count_batch), or one graph per launch when batching is 0.  All waits are host-side.
+ */
+typedef struct tc_server tc_server; /* opaque */
+
+typedef struct tc_server_config {
+  int32_t build_workers;      /* threads that copy and build admitted requests, one stream each (0: 4)           */
+  int32_t max_batch;          /* most graphs per counting launch (0: 4096)                                        */
+  int32_t batching;           /* 1: continuous batching; 0: one graph per launch                                  */
+  int32_t max_inflight;       /* most admitted, unfinished requests (0: 8192)                                     */
+  int64_t hbm_reserve_bytes;  /* device memory never used by admissions (< 0: 8 GiB)                              */
+  int64_t hbm_budget_bytes;   /* if > 0, an upper bound on the admission budget                                   */
+} tc_server_config;
+
+typedef struct tc_request_result {
+  uint64_t id;          /* as returned by tc_server_submit */
+  uint64_t triangles;   /* T of the request's graph (valid when status == TC_OK) */
+  int32_t status;       /* tc_status of the request */
+  int32_t reserved;
+  int64_t t_submit_ns;  /* steady-clock timestamps: submitted, admitted, CSR built, count available */
+  int64_t t_admit_ns;
+  int64_t t_built_ns;
+  int64_t t_done_ns;
+} tc_request_result;
+
+typedef struct tc_server_stats {
+  int64_t submitted, admitted, completed, failed;
+  int64_t launches;         /* counting launches (batched or single) */
+  int64_t max_batch_seen;   /* most graphs in one launch so far */
+  int64_t budget_bytes;     /* admission budget: free device memory at creation minus the reserve */
+  int64_t held_bytes;       /* estimated bytes held by admitted, unfinished requests */
+  int64_t peak_held_bytes;
+  int64_t pending;          /* submitted, not yet admitted */
+} tc_server_stats;
+
+/* tc_server_create — start a server on the current device (cfg may be NULL for defaults).  The admission budget is
+ * the free device memory now, minus hbm_reserve_bytes.  A request is admitted when its estimated peak footprint
+ * fits in what admitted requests leave of the budget (a request alone is always admitted if it fits the budget). */
+TC_API tc_status tc_server_create(const tc_server_config* cfg, tc_server** out);
+
+/* tc_server_submit — queue a request: the graph given by num_edges HOST pairs (src[i], dst[i]) on [0, num_vertices)
+ * (pinned memory gives the fastest copies).  The arrays must stay valid and unchanged until the request's result
+ * has been returned by tc_server_poll.  *id_out (may be NULL) receives the request id.  TC_ERR_NO_MEMORY if the
+ * request alone exceeds the budget.  Thread-safe. */
+TC_API tc_status tc_server_submit(tc_server* s, const int32_t* src, const int32_t* dst, int64_t num_edges,
+                                  int64_t num_vertices, uint64_t* id_out);
+
+/* tc_server_poll — move up to max_results finished requests into out (host array) and set *n_out; waits up to
+ * timeout_ms (0: no wait) for at least one.  A failed request has a non-zero status.  Thread-safe. */
+TC_API tc_status tc_server_poll(tc_server* s, tc_request_result* out, int32_t max_results, int32_t timeout_ms,
+                                int32_t* n_out);
+
+/* tc_server_get_stats — counters of the server so far. */
+TC_API tc_status tc_server_get_stats(tc_server* s, tc_server_stats* out);
+
+/* tc_server_destroy — stop the server: requests not yet admitted are dropped, admitted ones finish; results not
+ * polled are discarded.  NULL is a no-op. */
+TC_API void tc_server_destroy(tc_server* s);
+
 /* tc_graph_get_info — sizes of g (valid fields depend on whether g is built). */
 TC_API tc_status tc_graph_get_info(const tc_graph* g, tc_graph_info* info);
 

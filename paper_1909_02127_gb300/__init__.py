@@ -42,8 +42,27 @@ class tc_graph_info(ctypes.Structure):
                 ("built", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class tc_server_config(ctypes.Structure):
+    _fields_ = [("build_workers", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("batching", ctypes.c_int32),
+                ("max_inflight", ctypes.c_int32), ("hbm_reserve_bytes", ctypes.c_int64),
+                ("hbm_budget_bytes", ctypes.c_int64)]
+
+
+class tc_request_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("triangles", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64),
+                ("t_built_ns", ctypes.c_int64), ("t_done_ns", ctypes.c_int64)]
+
+
+class tc_server_stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in ("submitted", "admitted", "completed", "failed", "launches",
+                                                    "max_batch_seen", "budget_bytes", "held_bytes",
+                                                    "peak_held_bytes", "pending")]
+
+
 EXPORTED = ["tc_load_edges", "tc_build", "tc_count", "tc_count_device", "tc_count_per_vertex",
-            "tc_count_per_vertex_noalloc", "tc_count_batch",
+            "tc_count_per_vertex_noalloc", "tc_count_batch", "tc_server_create", "tc_server_submit",
+            "tc_server_poll", "tc_server_get_stats", "tc_server_destroy",
             "tc_graph_get_info", "tc_copy_csr", "tc_free", "tc_last_error", "tc_kernel_launches"]
 
 _lib = None
@@ -81,6 +100,16 @@ def load_library(path: str = LIB_PATH):
     lib.tc_copy_csr.restype = st
     lib.tc_free.argtypes = [vp]
     lib.tc_free.restype = None
+    lib.tc_server_create.argtypes = [ctypes.POINTER(tc_server_config), ctypes.POINTER(vp)]
+    lib.tc_server_create.restype = st
+    lib.tc_server_submit.argtypes = [vp, vp, vp, i64, i64, ctypes.POINTER(ctypes.c_uint64)]
+    lib.tc_server_submit.restype = st
+    lib.tc_server_poll.argtypes = [vp, ctypes.POINTER(tc_request_result), i32, i32, ctypes.POINTER(i32)]
+    lib.tc_server_poll.restype = st
+    lib.tc_server_get_stats.argtypes = [vp, ctypes.POINTER(tc_server_stats)]
+    lib.tc_server_get_stats.restype = st
+    lib.tc_server_destroy.argtypes = [vp]
+    lib.tc_server_destroy.restype = None
     lib.tc_kernel_launches.argtypes = []
     lib.tc_kernel_launches.restype = ctypes.c_uint64
     lib.tc_last_error.argtypes = []
@@ -273,6 +302,79 @@ def tc_copy_csr(g: int, stream=None):
 def tc_free(g: int) -> None:
     if g:
         load_library().tc_free(g)
+
+
+def tc_server_create(build_workers: int = 4, max_batch: int = 4096, batching: bool = True, max_inflight: int = 8192,
+                     hbm_reserve_bytes: int = -1, hbm_budget_bytes: int = 0) -> int:
+    cfg = tc_server_config(build_workers, max_batch, 1 if batching else 0, max_inflight, hbm_reserve_bytes,
+                           hbm_budget_bytes)
+    out = ctypes.c_void_p()
+    _check(load_library().tc_server_create(ctypes.byref(cfg), ctypes.byref(out)))
+    return out.value
+
+
+def tc_server_submit(s: int, src_ptr: int, dst_ptr: int, num_edges: int, num_vertices: int) -> int:
+    """Raw submit: src_ptr/dst_ptr are host addresses that must stay valid until the result is polled (the Server
+    class keeps them alive)."""
+    rid = ctypes.c_uint64(0)
+    _check(load_library().tc_server_submit(s, src_ptr, dst_ptr, num_edges, num_vertices, ctypes.byref(rid)))
+    return int(rid.value)
+
+
+def tc_server_poll(s: int, max_results: int = 4096, timeout_ms: int = 0):
+    buf = (tc_request_result * max(1, max_results))()
+    k = ctypes.c_int32(0)
+    _check(load_library().tc_server_poll(s, buf, max_results, timeout_ms, ctypes.byref(k)))
+    return [{name: getattr(buf[i], name) for name, _ in tc_request_result._fields_} for i in range(k.value)]
+
+
+def tc_server_get_stats(s: int) -> dict:
+    st = tc_server_stats()
+    _check(load_library().tc_server_get_stats(s, ctypes.byref(st)))
+    return {name: getattr(st, name) for name, _ in tc_server_stats._fields_}
+
+
+def tc_server_destroy(s: int) -> None:
+    if s:
+        load_library().tc_server_destroy(s)
+
+
+class Server:
+    """Owning wrapper over a tc_server: submit(src, dst, n) with host arrays (kept alive until their result is
+    polled), poll(), stats(), close()."""
+
+    def __init__(self, **cfg):
+        self.handle = tc_server_create(**cfg)
+        self._keep = {}
+
+    def submit(self, src, dst, num_vertices: int) -> int:
+        sp, dp, m, flags, keep = _edge_ptrs(src, dst)
+        if flags != TC_PTR_HOST:
+            raise ValueError("server requests take host arrays")
+        rid = tc_server_submit(self.handle, sp, dp, m, num_vertices)
+        self._keep[rid] = keep
+        return rid
+
+    def poll(self, max_results: int = 4096, timeout_ms: int = 0):
+        out = tc_server_poll(self.handle, max_results, timeout_ms)
+        for r in out:
+            self._keep.pop(r["id"], None)
+        return out
+
+    def stats(self) -> dict:
+        return tc_server_get_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            tc_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Graph:

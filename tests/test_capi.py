@@ -78,6 +78,14 @@ def test_argument_errors_without_gpu(lib):
     assert lib.tc_count_batch(None, -1, None, None) == tc.TC_ERR_INVALID_ARG
     assert lib.tc_count_batch(None, 0, None, None) == tc.TC_OK
     lib.tc_free(None)  # no-op
+    # serving loop: argument checks that return before any device call
+    rid = ctypes.c_uint64()
+    assert lib.tc_server_create(None, None) == tc.TC_ERR_INVALID_ARG
+    assert lib.tc_server_submit(None, None, None, 0, 0, ctypes.byref(rid)) == tc.TC_ERR_INVALID_ARG
+    k = ctypes.c_int32()
+    assert lib.tc_server_poll(None, None, 0, 0, ctypes.byref(k)) == tc.TC_ERR_INVALID_ARG
+    assert lib.tc_server_get_stats(None, None) == tc.TC_ERR_INVALID_ARG
+    lib.tc_server_destroy(None)  # no-op
 
 
 def test_missing_library_fails_loudly(tmp_path):

@@ -1,0 +1,87 @@
+"""Serving loop: every request's count is the same alone and in the mix (tolerance 0), with continuous batching
+and with one graph per launch, and under a tight device-memory budget."""
+import time
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tc():
+    import torch
+    import paper_1909_02127_gb300 as tc
+    from paper_1909_02127_gb300 import build
+    build.build()
+    torch.cuda.init()
+    return tc
+
+
+@pytest.fixture(scope="module")
+def requests_and_solo(tc):
+    pool = [sp for sp in graphgen.serve_pool(96) if sp.num_edges <= 400_000]
+    edges = [sp.edges() for sp in pool]
+    solo = []
+    for sp, (s, d) in zip(pool, edges):
+        g = tc.tc_load_edges(s, d, sp.n)
+        tc.tc_build(g)
+        solo.append(tc.tc_count(g))
+        tc.tc_free(g)
+    # the solo path itself against the oracle on the smaller graphs
+    for sp, (s, d), T in list(zip(pool, edges, solo))[:24]:
+        assert oracle.count(s, d, sp.n)[0] == T
+    return pool, edges, solo
+
+
+def _run(tc, pool, edges, order, **cfg):
+    got = {}
+    with tc.Server(**cfg) as srv:
+        ids = {}
+        for k in order:
+            s, d = edges[k]
+            ids[srv.submit(s, d, pool[k].n)] = k
+        deadline = time.time() + 120
+        while len(got) < len(ids) and time.time() < deadline:
+            for r in srv.poll(timeout_ms=100):
+                assert r["status"] == 0, r
+                assert r["t_submit_ns"] <= r["t_admit_ns"] <= r["t_built_ns"] <= r["t_done_ns"]
+                got.setdefault(ids[r["id"]], []).append(r["triangles"])
+        stats = srv.stats()
+    assert sum(len(v) for v in got.values()) == len(order)
+    return got, stats
+
+
+def test_alone_equals_in_the_mix(tc, requests_and_solo):
+    pool, edges, solo = requests_and_solo
+    rng = np.random.default_rng(5)
+    order = list(rng.permutation(len(pool))) + list(rng.integers(0, len(pool), size=64))  # with repeats
+    for batching in (True, False):
+        got, stats = _run(tc, pool, edges, order, batching=batching, build_workers=4)
+        for k, counts in got.items():
+            assert all(c == solo[k] for c in counts), (k, counts, solo[k])
+        if batching:
+            assert stats["max_batch_seen"] > 1  # requests did share launches
+        else:
+            assert stats["max_batch_seen"] == 1
+
+
+def test_tight_memory_budget(tc, requests_and_solo):
+    pool, edges, solo = requests_and_solo
+    budget = 48 << 20
+    order = [k for k in range(len(pool)) if 32 * pool[k].num_edges + 48 * pool[k].n + (1 << 20) <= budget]
+    assert len(order) > 10
+    got, stats = _run(tc, pool, edges, order, hbm_budget_bytes=budget, build_workers=8)
+    for k, counts in got.items():
+        assert counts == [solo[k]]
+    assert stats["peak_held_bytes"] <= budget
+    # a request larger than the whole budget is refused at submission
+    big = max(range(len(pool)), key=lambda k: pool[k].num_edges)
+    with tc.Server(hbm_budget_bytes=1 << 20) as srv:
+        s, d = edges[big]
+        with pytest.raises(tc.TCError) as e:
+            srv.submit(s, d, pool[big].n)
+        assert e.value.status == tc.TC_ERR_NO_MEMORY
