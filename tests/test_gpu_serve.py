@@ -45,8 +45,10 @@ def _run(tc, pool, edges, order, **cfg):
             s, d = edges[k]
             ids[srv.submit(s, d, pool[k].n)] = k
         deadline = time.time() + 120
-        while len(got) < len(ids) and time.time() < deadline:
+        received = 0
+        while received < len(ids) and time.time() < deadline:
             for r in srv.poll(timeout_ms=100):
+                received += 1
                 assert r["status"] == 0, r
                 assert r["t_submit_ns"] <= r["t_admit_ns"] <= r["t_built_ns"] <= r["t_done_ns"]
                 got.setdefault(ids[r["id"]], []).append(r["triangles"])
