@@ -1,40 +1,59 @@
 // tc_build.cu — from an edge list to the oriented, relabelled CSR and the source bins.
 //
 // Steps (all on the caller's stream):
-//   pack      validate ids, drop self-loops, key = (min << B) | max                     (Def. 1: undirected)
-//   sort      LSD radix sort on bits [0, 2B)
-//   unique    keep the first of each run of equal keys                                   (simple graph)
-//   degree    deg(x) = number of distinct edges at x                                     (NE = degree, Sec. III-A)
-//   rank      sort (deg, id) -> rank(x); perm[rank] = x                                   (the visiting order)
-//   relabel   edge {a,b} -> (min(rank a, rank b), max(...)): it now points up the order   (UMO, Sec. III-A/III-C)
-//   sort      full radix sort of the relabelled keys: rows by source, ascending targets
+//   pack      validate ids, drop self-loops, key = (min << B) | max; count the input pairs at each vertex
+//   rank      sort (count, id) -> rank(x); perm[rank] = x                                 (the visiting order)
+//   relabel   pair {a,b} -> (min(rank a, rank b), max(...)): it now points up the order   (UMO, Sec. III-A/III-C)
+//   sort      LSD radix sort of the relabelled keys on bits [0, 2B): rows by source, ascending targets
+//   unique    keep the first of each run of equal keys                                   (simple graph, Def. 1)
 //   csr       row lengths padded to a multiple of 4 (pad id n), int64 offsets by a scan, int32 columns
 //   bins      w(u) = padded work of u's second hops; sources with d+(u) >= 2 and a candidate 2-path are kept
 //             (the 2-look-ahead of Sec. III-C: a source needs two out-neighbours to close a triangle) and put in
 //             the warp bin, or in the block bin when w(u) is large.
 //
-// Relabelling by rank gives the kernel two things: hubs get the highest ids, so a bitmap over the top ids answers
-// most closing-edge tests; and hub rows, which are re-read by many sources, sit together in memory.
+// The visiting order only has to be a total order for every triangle to be found exactly once (Sec. III-C); it
+// is chosen to follow the degree (NE, Sec. III-A) because that bounds d+(u).  The degree used for ranking counts
+// the input pairs at each vertex, repeats included, so it is known straight after ingest and the pairs can be
+// relabelled before the one sort that also removes the repeats.  Relabelling by rank gives the kernel two things:
+// hubs get the highest ids, so a bitmap over the top ids answers most closing-edge tests; and hub rows, which are
+// re-read by many sources, sit together in memory.
 #include "tc_internal.cuh"
 #include "tc_prims.cuh"
 
 namespace tc {
 namespace {
 
+// Warp-aggregated increment: lanes with the same target add once.
+__device__ __forceinline__ void agg_inc(int32_t* cnt, uint32_t idx, bool active) {
+  const uint32_t key = active ? idx : 0xffffffffu;
+  const unsigned peers = __match_any_sync(kFull, key);
+  if (active && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[idx], __popc(peers));
+}
+
 __global__ void k_pack(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t len, int64_t n,
-                       int B, uint64_t* __restrict__ keys, uint32_t* __restrict__ err) {
+                       int B, uint64_t* __restrict__ keys, int32_t* __restrict__ indeg, uint32_t* __restrict__ err) {
   const uint64_t sentinel = (1ull << (2 * B)) - 1ull;
   bool bad = false;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t a = src[i], b = dst[i];
-    uint64_t key = sentinel;
-    if (a < 0 || b < 0 || a >= n || b >= n) {
-      bad = true;
-    } else if (a != b) {
-      const uint64_t lo = (uint64_t)(a < b ? a : b), hi = (uint64_t)(a < b ? b : a);
-      key = (lo << B) | hi;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < len; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    int32_t a = 0, b = 0;
+    bool pair = false;
+    if (i < len) {
+      a = src[i];
+      b = dst[i];
+      uint64_t key = sentinel;
+      if (a < 0 || b < 0 || a >= n || b >= n) {
+        bad = true;
+      } else if (a != b) {
+        const uint64_t lo = (uint64_t)(a < b ? a : b), hi = (uint64_t)(a < b ? b : a);
+        key = (lo << B) | hi;
+        pair = true;
+      }
+      keys[i] = key;
     }
-    keys[i] = key;
+    agg_inc(indeg, (uint32_t)a, pair);
+    agg_inc(indeg, (uint32_t)b, pair);
   }
   if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(err, 1u);
 }
@@ -85,30 +104,18 @@ __global__ void __launch_bounds__(kUThreads) k_unique_scatter(const uint64_t* __
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *m = (int64_t)part[blockIdx.x] + tot;
 }
 
-// ---- degree, rank, relabel ---------------------------------------------------------------------------------
-// Warp-aggregated increment: lanes with the same target add once.
-__device__ __forceinline__ void agg_inc(int32_t* cnt, uint32_t idx, bool active) {
-  const uint32_t key = active ? idx : 0xffffffffu;
-  const unsigned peers = __match_any_sync(kFull, key);
-  if (active && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[idx], __popc(peers));
-}
-
-__global__ void k_degree(const uint64_t* __restrict__ ukeys, int64_t m, int B, int32_t* __restrict__ deg) {
-  const uint64_t mask = (1ull << B) - 1ull;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < m; base += stride) {
-    const int64_t i = base + threadIdx.x;
-    const bool ok = i < m;
-    const uint64_t k = ok ? ukeys[i] : 0;
-    agg_inc(deg, (uint32_t)(k >> B), ok);
-    agg_inc(deg, (uint32_t)(k & mask), ok);
+// ---- rank, relabel --------------------------------------------------------------------------------------------
+// (deg << B) | id, in id order: a stable sort on the degree bits alone gives the (degree, id) order.
+__global__ void k_rank_keys(const int32_t* __restrict__ deg, int64_t n, int B, uint64_t* __restrict__ rkeys,
+                            int* __restrict__ maxdeg) {
+  int mx = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int d = deg[i];
+    rkeys[i] = ((uint64_t)(uint32_t)d << B) | (uint64_t)i;
+    mx = max(mx, d);
   }
-}
-
-// (deg << B) | id: ascending order of these keys is the (degree, id) order.
-__global__ void k_rank_keys(const int32_t* __restrict__ deg, int64_t n, int B, uint64_t* __restrict__ rkeys) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    rkeys[i] = ((uint64_t)(uint32_t)deg[i] << B) | (uint64_t)i;
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(maxdeg, mx);
 }
 
 __global__ void k_rank(const uint64_t* __restrict__ sorted, int64_t n, int B, int32_t* __restrict__ rank,
@@ -121,22 +128,29 @@ __global__ void k_rank(const uint64_t* __restrict__ sorted, int64_t n, int B, in
   }
 }
 
-__global__ void k_relabel(const uint64_t* __restrict__ ukeys, int64_t m, int B, const int32_t* __restrict__ rank,
-                          uint64_t* __restrict__ okeys, int32_t* __restrict__ odeg) {
+// Pair keys (lo << B) | hi (or the sentinel) -> (min rank << B) | max rank (the sentinel stays).
+__global__ void k_relabel(const uint64_t* __restrict__ keys, int64_t len, int B, const int32_t* __restrict__ rank,
+                          uint64_t* __restrict__ okeys) {
   const uint64_t mask = (1ull << B) - 1ull;
+  const uint64_t sentinel = (1ull << (2 * B)) - 1ull;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = keys[i];
+    uint64_t o = sentinel;
+    if (k != sentinel) {
+      const uint32_t ra = (uint32_t)rank[k >> B], rb = (uint32_t)rank[k & mask];
+      o = ((uint64_t)(ra < rb ? ra : rb) << B) | (uint64_t)(ra < rb ? rb : ra);
+    }
+    okeys[i] = o;
+  }
+}
+
+// d+(s) from the distinct oriented keys (sorted, so equal sources are adjacent and aggregate within a warp).
+__global__ void k_outdeg(const uint64_t* __restrict__ ukeys, int64_t m, int B, int32_t* __restrict__ odeg) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < m; base += stride) {
     const int64_t i = base + threadIdx.x;
     const bool ok = i < m;
-    uint32_t s = 0;
-    if (ok) {
-      const uint64_t k = ukeys[i];
-      const uint32_t ra = (uint32_t)rank[k >> B], rb = (uint32_t)rank[k & mask];
-      s = ra < rb ? ra : rb;
-      const uint32_t d = ra < rb ? rb : ra;
-      okeys[i] = ((uint64_t)s << B) | d;
-    }
-    agg_inc(odeg, s, ok);
+    agg_inc(odeg, ok ? (uint32_t)(ukeys[i] >> B) : 0u, ok);
   }
 }
 
@@ -232,7 +246,7 @@ tc_status pack_edges(tc_graph* g, const int32_t* src, const int32_t* dst, int64_
                      uint32_t* d_err, cudaStream_t s) {
   if (len <= 0) return TC_OK;
   k_pack<<<grid_for(len, 256), 256, 0, s>>>(src, dst, len, g->n, g->key_bits, g->keys.as<uint64_t>() + offset,
-                                            d_err);
+                                            g->indeg.as<int32_t>(), d_err);
   note_launch();
   TC_CUDA(cudaGetLastError());
   return TC_OK;
@@ -255,10 +269,11 @@ tc_status build_graph(tc_graph* g, cudaStream_t s) {
   const int64_t n1 = n > 0 ? n : 1;
   const uint64_t sentinel = (1ull << (2 * B)) - 1ull;
   tc_status st = TC_OK;
-  Buf alt, part, counters, deg, odeg, ukeys, okeys, rkeys, rkeys_alt, rank, ustart, plen;
+  Buf alt, part, counters, odeg, ukeys, rkeys, rkeys_alt, rank, ustart, plen;
   int64_t m = 0;
   BinCounters hb{};
   int64_t total_padded = 0;
+  int32_t maxdeg = 0;
   auto launched = [&](const char* what) {
     note_launch();
     return cuda_status(cudaGetLastError(), what);
@@ -266,73 +281,71 @@ tc_status build_graph(tc_graph* g, cudaStream_t s) {
 
   do {
     if ((st = buf_alloc(a, counters, 64, s))) break;
-    // ---- sort + unique: g->keys -> ukeys (m distinct undirected edges, sorted by (lo, hi)) ----
+    // ---- rank: stable sort of (count << B) | id on the count bits ----
+    if ((st = buf_alloc(a, rank, (size_t)n1 * 4, s))) break;
+    if ((st = buf_alloc(a, g->perm, (size_t)n1 * 4, s))) break;
+    if (n > 0) {
+      if ((st = buf_alloc(a, rkeys, (size_t)n * 8, s))) break;
+      if ((st = buf_alloc(a, rkeys_alt, (size_t)n * 8, s))) break;
+      if ((st = cuda_status(cudaMemsetAsync(counters.p, 0, 8, s), "memset maxdeg"))) break;
+      k_rank_keys<<<grid_for(n, 256), 256, 0, s>>>(g->indeg.as<int32_t>(), n, B, rkeys.as<uint64_t>(),
+                                                   counters.as<int>());
+      if ((st = launched("k_rank_keys"))) break;
+      if ((st = cuda_status(cudaMemcpyAsync(&maxdeg, counters.p, 4, cudaMemcpyDeviceToHost, s), "copy maxdeg")))
+        break;
+      if ((st = cuda_status(cudaStreamSynchronize(s), "sync maxdeg"))) break;
+      int dbits = 0;
+      while (dbits < 32 && (1ll << dbits) <= (int64_t)maxdeg) ++dbits;
+      uint64_t* rs = nullptr;
+      if ((st = radix_sort_u64(a, rkeys.as<uint64_t>(), rkeys_alt.as<uint64_t>(), n, B, B + dbits, &rs, s))) break;
+      k_rank<<<grid_for(n, 256), 256, 0, s>>>(rs, n, B, rank.as<int32_t>(), g->perm.as<int32_t>());
+      if ((st = launched("k_rank"))) break;
+      buf_release(a, rkeys, s);
+      buf_release(a, rkeys_alt, s);
+    }
+    buf_release(a, g->indeg, s);
+
+    // ---- relabel, sort, unique: ukeys = distinct (rank s << B) | rank d with s < d, sorted ----
     if (M > 0) {
       uint64_t* sorted = nullptr;
       if ((st = buf_alloc(a, alt, (size_t)M * 8, s))) break;
-      if ((st = radix_sort_u64(a, g->keys.as<uint64_t>(), alt.as<uint64_t>(), M, 0, 2 * B, &sorted, s))) break;
-      const bool in_keys = sorted == g->keys.as<uint64_t>();
+      k_relabel<<<grid_for(M, 256), 256, 0, s>>>(g->keys.as<uint64_t>(), M, B, rank.as<int32_t>(),
+                                                 alt.as<uint64_t>());
+      if ((st = launched("k_relabel"))) break;
+      if ((st = radix_sort_u64(a, alt.as<uint64_t>(), g->keys.as<uint64_t>(), M, 0, 2 * B, &sorted, s))) break;
+      const bool in_alt = sorted == alt.as<uint64_t>();
+      uint64_t* uout = in_alt ? g->keys.as<uint64_t>() : alt.as<uint64_t>();
       const int64_t tiles = (M + kUTile - 1) / kUTile;
       if ((st = buf_alloc(a, part, (size_t)tiles * 4, s))) break;
       k_unique_count<<<(unsigned)tiles, kUThreads, 0, s>>>(sorted, M, sentinel, part.as<uint32_t>());
       if ((st = launched("k_unique_count"))) break;
       if ((st = exclusive_scan_u32(a, part.as<uint32_t>(), tiles, s))) break;
-      uint64_t* uout = in_keys ? alt.as<uint64_t>() : g->keys.as<uint64_t>();
       k_unique_scatter<<<(unsigned)tiles, kUThreads, 0, s>>>(sorted, M, sentinel, part.as<uint32_t>(), uout,
                                                               counters.as<int64_t>());
       if ((st = launched("k_unique_scatter"))) break;
       if ((st = cuda_status(cudaMemcpyAsync(&m, counters.p, 8, cudaMemcpyDeviceToHost, s), "copy m"))) break;
       if ((st = cuda_status(cudaStreamSynchronize(s), "sync m"))) break;
       buf_release(a, part, s);
-      // ukeys takes the buffer holding the unique keys; okeys the other one (free now)
-      if (in_keys) {
-        ukeys = alt;
-        okeys = g->keys;
-      } else {
+      if (in_alt) {
         ukeys = g->keys;
-        okeys = alt;
+        g->keys = Buf{};
+      } else {
+        ukeys = alt;
+        alt = Buf{};
       }
-      alt = Buf{};
-      g->keys = Buf{};
-    }
-    g->m = m;
-
-    // ---- degree and rank ----
-    if ((st = buf_alloc(a, deg, (size_t)n1 * 4, s))) break;
-    if ((st = buf_alloc(a, rank, (size_t)n1 * 4, s))) break;
-    if ((st = buf_alloc(a, g->perm, (size_t)n1 * 4, s))) break;
-    if ((st = cuda_status(cudaMemsetAsync(deg.p, 0, (size_t)n1 * 4, s), "memset deg"))) break;
-    if (m > 0) {
-      k_degree<<<grid_for(m, 256), 256, 0, s>>>(ukeys.as<uint64_t>(), m, B, deg.as<int32_t>());
-      if ((st = launched("k_degree"))) break;
-    }
-    if (n > 0) {
-      if ((st = buf_alloc(a, rkeys, (size_t)n * 8, s))) break;
-      if ((st = buf_alloc(a, rkeys_alt, (size_t)n * 8, s))) break;
-      k_rank_keys<<<grid_for(n, 256), 256, 0, s>>>(deg.as<int32_t>(), n, B, rkeys.as<uint64_t>());
-      if ((st = launched("k_rank_keys"))) break;
-      uint64_t* rs = nullptr;
-      if ((st = radix_sort_u64(a, rkeys.as<uint64_t>(), rkeys_alt.as<uint64_t>(), n, 0, 2 * B, &rs, s))) break;
-      k_rank<<<grid_for(n, 256), 256, 0, s>>>(rs, n, B, rank.as<int32_t>(), g->perm.as<int32_t>());
-      if ((st = launched("k_rank"))) break;
-      buf_release(a, rkeys, s);
-      buf_release(a, rkeys_alt, s);
-    }
-    buf_release(a, deg, s);
-
-    // ---- relabel + sort: okeys = (rank s << B) | rank d with s < d, sorted ----
-    if ((st = buf_alloc(a, odeg, (size_t)n1 * 4, s))) break;
-    if ((st = cuda_status(cudaMemsetAsync(odeg.p, 0, (size_t)n1 * 4, s), "memset odeg"))) break;
-    uint64_t* osorted = nullptr;
-    if (m > 0) {
-      k_relabel<<<grid_for(m, 256), 256, 0, s>>>(ukeys.as<uint64_t>(), m, B, rank.as<int32_t>(),
-                                                 okeys.as<uint64_t>(), odeg.as<int32_t>());
-      if ((st = launched("k_relabel"))) break;
-      if ((st = radix_sort_u64(a, okeys.as<uint64_t>(), ukeys.as<uint64_t>(), m, 0, 2 * B, &osorted, s))) break;
+      buf_release(a, alt, s);
+      buf_release(a, g->keys, s);
     }
     buf_release(a, rank, s);
+    g->m = m;
 
     // ---- offsets: unpadded starts (ustart) and padded offsets (off) ----
+    if ((st = buf_alloc(a, odeg, (size_t)n1 * 4, s))) break;
+    if ((st = cuda_status(cudaMemsetAsync(odeg.p, 0, (size_t)n1 * 4, s), "memset odeg"))) break;
+    if (m > 0) {
+      k_outdeg<<<grid_for(m, 256), 256, 0, s>>>(ukeys.as<uint64_t>(), m, B, odeg.as<int32_t>());
+      if ((st = launched("k_outdeg"))) break;
+    }
     if ((st = buf_alloc(a, ustart, (size_t)(n + 1) * 8, s))) break;
     if ((st = buf_alloc(a, g->off, (size_t)(n + 1) * 8, s))) break;
     if ((st = buf_alloc(a, plen, (size_t)n1 * 4, s))) break;
@@ -359,12 +372,11 @@ tc_status build_graph(tc_graph* g, cudaStream_t s) {
     k_fill<<<grid_for(ncol, 256), 256, 0, s>>>(g->col.as<int32_t>(), ncol, (int32_t)n);
     if ((st = launched("k_fill"))) break;
     if (m > 0) {
-      k_columns<<<grid_for(m, 256), 256, 0, s>>>(osorted, m, B, ustart.as<int64_t>(), g->off.as<int64_t>(),
-                                                 g->col.as<int32_t>());
+      k_columns<<<grid_for(m, 256), 256, 0, s>>>(ukeys.as<uint64_t>(), m, B, ustart.as<int64_t>(),
+                                                 g->off.as<int64_t>(), g->col.as<int32_t>());
       if ((st = launched("k_columns"))) break;
     }
     buf_release(a, ukeys, s);
-    buf_release(a, okeys, s);
 
     // ---- bins ----
     if ((st = buf_alloc(a, g->list, (size_t)n1 * 4, s))) break;
@@ -380,9 +392,10 @@ tc_status build_graph(tc_graph* g, cudaStream_t s) {
     if ((st = cuda_status(cudaStreamSynchronize(s), "sync bins"))) break;
   } while (0);
 
-  for (Buf* b : {&alt, &part, &counters, &deg, &odeg, &ukeys, &okeys, &rkeys, &rkeys_alt, &rank, &ustart, &plen})
+  for (Buf* b : {&alt, &part, &counters, &odeg, &ukeys, &rkeys, &rkeys_alt, &rank, &ustart, &plen})
     buf_release(a, *b, s);
   buf_release(a, g->keys, s);
+  buf_release(a, g->indeg, s);
   if (st != TC_OK) return st;
   g->wedges = (int64_t)hb.wedges;
   g->active = (int64_t)hb.active;

@@ -77,6 +77,7 @@ int bits_for(int64_t n) {
 
 void release_all(tc_graph* g, cudaStream_t s) {
   buf_release(g->alloc, g->keys, s);
+  buf_release(g->alloc, g->indeg, s);
   buf_release(g->alloc, g->off, s);
   buf_release(g->alloc, g->col, s);
   buf_release(g->alloc, g->list, s);
@@ -162,6 +163,10 @@ TC_API tc_status tc_load_edges(const int32_t* src, const int32_t* dst, int64_t n
   uint32_t h_err = 0;
   do {
     if ((st = buf_alloc(g->alloc, g->acc, 64, s))) break;
+    if ((st = buf_alloc(g->alloc, g->indeg, (size_t)(num_vertices > 0 ? num_vertices : 1) * 4, s))) break;
+    if ((st = cuda_status(cudaMemsetAsync(g->indeg.p, 0, (size_t)(num_vertices > 0 ? num_vertices : 1) * 4, s),
+                          "memset indeg")))
+      break;
     if (cudaMallocHost((void**)&g->host_total, 64) != cudaSuccess) {
       (void)cudaGetLastError();
       g->host_total = nullptr;

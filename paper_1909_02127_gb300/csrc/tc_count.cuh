@@ -99,20 +99,36 @@ __device__ __forceinline__ uint32_t test_quad(const int4 q, const C& c, unsigned
   return (h0 + h1) + (h2 + h3);
 }
 
-// One long row (quads [q0, q0 + nq)) walked by the calling warp.
+// One long row (quads [q0, q0 + nq)) walked by the calling warp in windows of 128 quads, four independent loads in
+// flight per lane.  Trip counts and branches depend only on nq, so the warp never diverges; in the last window a
+// lane whose quad lies past the row tests the pad id n (never a member) instead of loading.
 template <bool PV, class C>
 __device__ __forceinline__ uint32_t long_row(const int4* __restrict__ col4, uint32_t q0, uint32_t nq, const C& c,
-                                             unsigned long long* pv, int32_t v) {
+                                             unsigned long long* pv, int32_t v, int32_t pad) {
+  const uint32_t lane = threadIdx.x & 31;
+  const int4* p = col4 + q0 + lane;
   uint32_t hits = 0;
-  const int lane = threadIdx.x & 31;
-  uint32_t q = lane;
-  for (; q + 96 < nq; q += 128) {  // four independent loads in flight per lane
-    const int4 a = __ldg(&col4[q0 + q]), b = __ldg(&col4[q0 + q + 32]);
-    const int4 e = __ldg(&col4[q0 + q + 64]), f = __ldg(&col4[q0 + q + 96]);
+  uint32_t rem = nq;
+  for (; rem >= 128; rem -= 128, p += 128) {
+    const int4 a = __ldg(p), b = __ldg(p + 32), e = __ldg(p + 64), f = __ldg(p + 96);
     hits += (test_quad<PV>(a, c, pv, v) + test_quad<PV>(b, c, pv, v)) +
             (test_quad<PV>(e, c, pv, v) + test_quad<PV>(f, c, pv, v));
   }
-  for (; q < nq; q += 32) hits += test_quad<PV>(__ldg(&col4[q0 + q]), c, pv, v);
+  if (rem > 0) {
+    const int4 none = make_int4(pad, pad, pad, pad);
+    const int4 a = lane < rem ? __ldg(p) : none;
+    const int4 b = lane + 32 < rem ? __ldg(p + 32) : none;
+    if (rem > 64) {
+      const int4 e = lane + 64 < rem ? __ldg(p + 64) : none;
+      const int4 f = lane + 96 < rem ? __ldg(p + 96) : none;
+      hits += (test_quad<PV>(a, c, pv, v) + test_quad<PV>(b, c, pv, v)) +
+              (test_quad<PV>(e, c, pv, v) + test_quad<PV>(f, c, pv, v));
+    } else if (rem > 32) {
+      hits += test_quad<PV>(a, c, pv, v) + test_quad<PV>(b, c, pv, v);
+    } else {
+      hits += test_quad<PV>(a, c, pv, v);
+    }
+  }
   return hits;
 }
 
@@ -214,7 +230,7 @@ __device__ __forceinline__ uint32_t warp_hops(const CsrView& g, int64_t beg, int
       longs &= longs - 1;
       const uint32_t q0 = __shfl_sync(kFull, ro.q0, k), nq = __shfl_sync(kFull, ro.nq, k);
       const int32_t vk = PV ? __shfl_sync(kFull, v, k) : 0;
-      hits += long_row<PV>(col4, q0, nq, c, pv, vk);
+      hits += long_row<PV>(col4, q0, nq, c, pv, vk, (int32_t)g.n);
     }
     const bool is_short = ro.nq > 0 && !is_long;
     const unsigned shorts = __ballot_sync(kFull, is_short);
@@ -313,7 +329,7 @@ __device__ __forceinline__ uint32_t block_hops(const CsrView& g, int64_t beg, in
       if (lane == 0) k = atomicAdd(br.next, 1u);
       k = __shfl_sync(kFull, k, 0);
       if (k >= NL) break;
-      hits += long_row<PV>(col4, br.lq0[k], br.lnq[k], c, pv, PV ? br.lv[k] : 0);
+      hits += long_row<PV>(col4, br.lq0[k], br.lnq[k], c, pv, PV ? br.lv[k] : 0, (int32_t)g.n);
     }
     // short rows: equal contiguous shares of the quad stream
     const uint32_t per = (Q + kWarpsPerCTA - 1) / kWarpsPerCTA;

@@ -109,6 +109,7 @@ struct tc_graph {
   int64_t num_pairs = 0;
   int key_bits = 1;          // B: bits per vertex id in packed keys
   tc::Buf keys;              // packed (lo << B) | hi keys, until tc_build
+  tc::Buf indeg;             // int32[n]: input pairs at each vertex (self-loops excluded), until tc_build
   bool built = false;
   // built state
   int64_t m = 0;

@@ -214,9 +214,10 @@ def test_csr_structure(tc):
     keep = lo != hi
     und = np.unique(lo[keep].astype(np.int64) * n + hi[keep])
     deg = np.bincount(np.concatenate([und // n, und % n]), minlength=n)
-    # perm is the (degree, id) order
+    # perm is the (count, id) order, count = input pairs at the vertex (self-loops excluded, repeats included)
+    cnt = np.bincount(np.concatenate([hs[keep], hd[keep]]), minlength=n)
     np.testing.assert_array_equal(np.sort(perm), np.arange(n))
-    key = deg[perm].astype(np.int64) * n + perm
+    key = cnt[perm].astype(np.int64) * n + perm
     assert np.all(np.diff(key) > 0)
     assert off[0] == 0 and np.all(off % 4 == 0) and off[-1] == col.size == info["csr_entries"]
     real = col < n
