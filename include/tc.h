@@ -154,6 +154,18 @@ TC_API tc_status tc_count_per_vertex_noalloc(tc_graph* g, uint64_t* d_per_vertex
 TC_API tc_status tc_count_batch(tc_graph* const* gs, int32_t num_graphs, uint64_t* out_counts, void* stream);
 
 /*
+ * Batch plans — tc_count_batch for a fixed set of graphs counted repeatedly.  tc_batch_plan_create uploads the
+ * batch's work table once and captures the launch sequence (zero the counters, the persistent kernel, the copy of
+ * the counts to pinned host memory) as a CUDA graph on `stream`; tc_batch_plan_run replays it with one graph launch
+ * and copies the counts to out_counts (host, num_graphs entries), blocking until they are valid.  The graphs must
+ * stay built and must not be freed while the plan exists.  (No counterpart in the paper.)
+ */
+typedef struct tc_batch_plan tc_batch_plan; /* opaque */
+TC_API tc_status tc_batch_plan_create(tc_graph* const* gs, int32_t num_graphs, void* stream, tc_batch_plan** out);
+TC_API tc_status tc_batch_plan_run(tc_batch_plan* p, uint64_t* out_counts, void* stream);
+TC_API void tc_batch_plan_free(tc_batch_plan* p); /* NULL is a no-op */
+
+/*
  * Serving loop (no counterpart in the paper; it drives the traversal of tc_count for a stream of requests).
  * A server admits submitted requests by device memory, builds their CSRs concurrently on its own streams, keeps
  * them resident, and counts every graph that is ready whenever the previous launch finishes (continuous batching
@@ -232,6 +244,30 @@ TC_API tc_status tc_copy_csr(const tc_graph* g, int64_t* offsets, int32_t* cols,
 
 /* tc_free — release g and all its device memory (stream-ordered on the last stream g used).  NULL is a no-op. */
 TC_API void tc_free(tc_graph* g);
+
+/*
+ * Tuning (no counterpart in the paper).  The counting kernel gives a source a whole thread block when its work
+ * w(u) (padded second-hop entries) exceeds a threshold, and one warp otherwise; the best threshold depends on the
+ * graph's size.  The table maps size classes (by distinct edges m) to thresholds and is consulted by tc_build.
+ * Counts never depend on it.  Process-wide; thread-safe.
+ */
+#define TC_TUNING_MAX_CLASSES 16
+typedef struct tc_tuning {
+  int32_t num_classes;                                 /* 1..TC_TUNING_MAX_CLASSES */
+  int32_t reserved;
+  int64_t batch_warp_max_edges;                        /* in tc_count_batch and batch plans, graphs with m at most
+                                                          this run every source one warp each: across many graphs
+                                                          there is parallelism enough, and a block per source costs
+                                                          more than it saves */
+  int64_t class_max_edges[TC_TUNING_MAX_CLASSES];      /* ascending; class i holds graphs with m <= class_max_edges[i]
+                                                          (the last class also holds every larger graph) */
+  int64_t block_min_work[TC_TUNING_MAX_CLASSES];       /* threshold for class i, >= 0 */
+} tc_tuning;
+
+/* tc_set_tuning — replace the table (TC_ERR_INVALID_ARG if malformed).  Applies to graphs built afterwards. */
+TC_API tc_status tc_set_tuning(const tc_tuning* t);
+/* tc_get_tuning — copy the current table (the built-in default until tc_set_tuning is called). */
+TC_API tc_status tc_get_tuning(tc_tuning* t);
 
 /* tc_kernel_launches — number of CUDA kernels this library has launched in the process so far (all threads).
  * A diagnostic with no counterpart in the paper: benchmarks difference it around a timed region. */

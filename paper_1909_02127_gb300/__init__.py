@@ -42,6 +42,16 @@ class tc_graph_info(ctypes.Structure):
                 ("built", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+TC_TUNING_MAX_CLASSES = 16
+
+
+class tc_tuning(ctypes.Structure):
+    _fields_ = [("num_classes", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("batch_warp_max_edges", ctypes.c_int64),
+                ("class_max_edges", ctypes.c_int64 * TC_TUNING_MAX_CLASSES),
+                ("block_min_work", ctypes.c_int64 * TC_TUNING_MAX_CLASSES)]
+
+
 class tc_server_config(ctypes.Structure):
     _fields_ = [("build_workers", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("batching", ctypes.c_int32),
                 ("max_inflight", ctypes.c_int32), ("hbm_reserve_bytes", ctypes.c_int64),
@@ -62,8 +72,10 @@ class tc_server_stats(ctypes.Structure):
 
 EXPORTED = ["tc_load_edges", "tc_build", "tc_count", "tc_count_device", "tc_count_per_vertex",
             "tc_count_per_vertex_noalloc", "tc_count_batch", "tc_server_create", "tc_server_submit",
-            "tc_server_poll", "tc_server_get_stats", "tc_server_destroy",
-            "tc_graph_get_info", "tc_copy_csr", "tc_free", "tc_last_error", "tc_kernel_launches"]
+            "tc_server_poll", "tc_server_get_stats", "tc_server_destroy", "tc_batch_plan_create",
+            "tc_batch_plan_run", "tc_batch_plan_free",
+            "tc_graph_get_info", "tc_copy_csr", "tc_free", "tc_last_error", "tc_kernel_launches", "tc_set_tuning",
+            "tc_get_tuning"]
 
 _lib = None
 
@@ -110,12 +122,81 @@ def load_library(path: str = LIB_PATH):
     lib.tc_server_get_stats.restype = st
     lib.tc_server_destroy.argtypes = [vp]
     lib.tc_server_destroy.restype = None
+    lib.tc_batch_plan_create.argtypes = [ctypes.POINTER(vp), i32, vp, ctypes.POINTER(vp)]
+    lib.tc_batch_plan_create.restype = st
+    lib.tc_batch_plan_run.argtypes = [vp, u64p, vp]
+    lib.tc_batch_plan_run.restype = st
+    lib.tc_batch_plan_free.argtypes = [vp]
+    lib.tc_batch_plan_free.restype = None
+    lib.tc_set_tuning.argtypes = [ctypes.POINTER(tc_tuning)]
+    lib.tc_set_tuning.restype = st
+    lib.tc_get_tuning.argtypes = [ctypes.POINTER(tc_tuning)]
+    lib.tc_get_tuning.restype = st
     lib.tc_kernel_launches.argtypes = []
     lib.tc_kernel_launches.restype = ctypes.c_uint64
     lib.tc_last_error.argtypes = []
     lib.tc_last_error.restype = ctypes.c_char_p
     _lib = lib
+    _apply_tuning_file(lib)
     return lib
+
+
+TUNING_FILE = os.path.join(_HERE, "tuning.json")
+
+
+def _apply_tuning_file(lib, path: str = TUNING_FILE) -> bool:
+    """Install the autotuner's table when it was measured on this kind of device (name and SM count match)."""
+    if not os.path.exists(path):
+        return False
+    try:
+        import json
+        import torch
+        if not torch.cuda.is_available():
+            return False
+        with open(path) as f:
+            data = json.load(f)
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        if data.get("device") != props.name or int(data.get("sms", -1)) != props.multi_processor_count:
+            return False
+        t = _tuning_struct(data["classes"], data.get("batch_warp_max_edges", 1 << 25))
+        return lib.tc_set_tuning(ctypes.byref(t)) == TC_OK
+    except Exception:
+        return False
+
+
+def _tuning_struct(classes, batch_warp_max_edges: int = 1 << 25) -> "tc_tuning":
+    t = tc_tuning()
+    t.num_classes = len(classes)
+    t.batch_warp_max_edges = int(batch_warp_max_edges)
+    for i, (max_edges, work) in enumerate(classes):
+        t.class_max_edges[i] = int(max_edges)
+        t.block_min_work[i] = int(work)
+    return t
+
+
+def tc_set_tuning(classes, batch_warp_max_edges: Optional[int] = None) -> None:
+    """classes: [(max_edges, block_min_work), ...] with ascending max_edges; batch_warp_max_edges: keep the
+    current value if None."""
+    if not 1 <= len(classes) <= TC_TUNING_MAX_CLASSES:
+        raise ValueError("1..16 classes")
+    if batch_warp_max_edges is None:
+        cur = tc_tuning()
+        _check(load_library().tc_get_tuning(ctypes.byref(cur)))
+        batch_warp_max_edges = cur.batch_warp_max_edges
+    t = _tuning_struct(classes, batch_warp_max_edges)
+    _check(load_library().tc_set_tuning(ctypes.byref(t)))
+
+
+def tc_get_tuning():
+    t = tc_tuning()
+    _check(load_library().tc_get_tuning(ctypes.byref(t)))
+    return [(int(t.class_max_edges[i]), int(t.block_min_work[i])) for i in range(t.num_classes)]
+
+
+def tc_get_batch_warp_max_edges() -> int:
+    t = tc_tuning()
+    _check(load_library().tc_get_tuning(ctypes.byref(t)))
+    return int(t.batch_warp_max_edges)
 
 
 def _check(status: int):
@@ -279,6 +360,26 @@ def tc_count_batch(gs: Sequence[int], stream=None) -> np.ndarray:
     _check(lib.tc_count_batch(arr, len(gs), out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
                               _stream_ptr(stream)))
     return out
+
+
+def tc_batch_plan_create(gs: Sequence[int], stream=None) -> int:
+    arr = (ctypes.c_void_p * len(gs))(*gs)
+    out = ctypes.c_void_p()
+    _check(load_library().tc_batch_plan_create(arr, len(gs), _stream_ptr(stream), ctypes.byref(out)))
+    return out.value
+
+
+def tc_batch_plan_run(plan: int, num_graphs: int, stream=None, out: Optional[np.ndarray] = None) -> np.ndarray:
+    if out is None:
+        out = np.zeros(num_graphs, dtype=np.uint64)
+    _check(load_library().tc_batch_plan_run(plan, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                            _stream_ptr(stream)))
+    return out
+
+
+def tc_batch_plan_free(plan: int) -> None:
+    if plan:
+        load_library().tc_batch_plan_free(plan)
 
 
 def tc_graph_get_info(g: int) -> dict:

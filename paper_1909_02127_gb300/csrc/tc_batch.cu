@@ -6,6 +6,10 @@
 // warp drains the warp-bin space four sources at a time.  Per-source counts are added to counts[g] (one atomic per
 // warp per run of consecutive sources of the same graph).  The loops end when the cursors pass the totals: there
 // is no waiting on other CTAs.
+#include <string.h>
+
+#include <new>
+#include <string>
 #include <vector>
 
 #include "tc_count.cuh"
@@ -76,7 +80,11 @@ __global__ void __launch_bounds__(kCountThreads, 2)
     __syncwarp();
     int cur_g = -1;
     unsigned long long acc = 0;
-    constexpr int kChunk = 4;
+    // Chunks of consecutive sources: the graph is found by one search per chunk and then followed forward, and its
+    // view stays in registers while the chunk stays inside it.
+    constexpr int kChunk = 16;
+    CsrView v{};
+    int64_t gbeg = 0, gend = 0;  // [pw[cur_g], pw[cur_g + 1])
     while (true) {
       long long idx = 0;
       if (lane == 0) idx = (long long)atomicAdd(&cursors[1], (unsigned long long)kChunk);
@@ -84,21 +92,91 @@ __global__ void __launch_bounds__(kCountThreads, 2)
       if (idx >= NW) break;
       const int64_t e = idx + kChunk < NW ? idx + kChunk : NW;
       for (int64_t i = idx; i < e; ++i) {
-        const int g = find_graph(t.pw, G, i);
-        if (g != cur_g) {
+        if (i < gbeg || i >= gend) {
+          const int g = (cur_g >= 0 && i >= gend && i < __ldg(&t.pw[cur_g + 2])) ? cur_g + 1
+                                                                                 : find_graph(t.pw, G, i);
           acc = warp_sum(acc);
           if (lane == 0 && acc && cur_g >= 0) atomicAdd(&counts[cur_g], acc);
           acc = 0;
           cur_g = g;
+          v = t.views[g];
+          gbeg = __ldg(&t.pw[g]);
+          gend = __ldg(&t.pw[g + 1]);
         }
-        const CsrView v = t.views[g];
-        const int32_t u = v.list[v.n - v.nw + (i - __ldg(&t.pw[g]))];
+        const int64_t k = i - gbeg;  // the graph's warp work: nbw block-bin sources, then its warp bin
+        const int32_t u = k < v.nbw ? v.list[k] : v.list[v.n - v.nw + (k - v.nbw)];
         acc += dev::warp_source<false>(u, v, region, ltab, r, nullptr);
       }
     }
     acc = warp_sum(acc);
     if (lane == 0 && acc && cur_g >= 0) atomicAdd(&counts[cur_g], acc);
   }
+}
+
+// Device layout of a batch: views | pb | pw | counts | cursors, built from host handles.
+struct BatchLayout {
+  size_t views_bytes, pre_bytes, table_bytes, counts_bytes, total_bytes;
+  int64_t nb_total, nw_total;
+};
+
+tc_status check_batch(tc_graph* const* gs, int32_t num_graphs, const char* who) {
+  for (int32_t i = 0; i < num_graphs; ++i) {
+    if (!gs[i]) {
+      set_error(std::string(who) + ": NULL graph handle");
+      return TC_ERR_INVALID_ARG;
+    }
+    if (!gs[i]->built) {
+      set_error(std::string(who) + ": a graph is not built");
+      return TC_ERR_STATE;
+    }
+  }
+  return TC_OK;
+}
+
+BatchLayout batch_table(tc_graph* const* gs, int32_t num_graphs, std::vector<unsigned char>& host) {
+  const size_t G = (size_t)num_graphs;
+  BatchLayout L{};
+  L.views_bytes = ((G * sizeof(CsrView)) + 255) / 256 * 256;
+  L.pre_bytes = ((G + 1) * 8 + 255) / 256 * 256;
+  L.table_bytes = L.views_bytes + 2 * L.pre_bytes;
+  L.counts_bytes = (G * 8 + 255) / 256 * 256;
+  L.total_bytes = L.table_bytes + L.counts_bytes + 64;
+  host.assign(L.table_bytes, 0);
+  CsrView* hv = reinterpret_cast<CsrView*>(host.data());
+  int64_t* hpb = reinterpret_cast<int64_t*>(host.data() + L.views_bytes);
+  int64_t* hpw = reinterpret_cast<int64_t*>(host.data() + L.views_bytes + L.pre_bytes);
+  hpb[0] = hpw[0] = 0;
+  const int64_t warp_max = batch_warp_max_edges();
+  for (size_t i = 0; i < G; ++i) {
+    hv[i] = gs[i]->view();
+    if (gs[i]->m <= warp_max) hv[i].nbw = hv[i].nb;  // this graph's block-bin sources run one warp each
+    hpb[i + 1] = hpb[i] + (hv[i].nb - hv[i].nbw);
+    hpw[i + 1] = hpw[i] + hv[i].nw + hv[i].nbw;
+  }
+  L.nb_total = hpb[G];
+  L.nw_total = hpw[G];
+  return L;
+}
+
+// Zero the counts and cursors, launch the persistent kernel, copy the counts to `host_counts` (stream-ordered).
+tc_status batch_launch(unsigned char* base, const BatchLayout& L, int32_t num_graphs, uint64_t* host_counts,
+                       cudaStream_t s) {
+  unsigned long long* counts = reinterpret_cast<unsigned long long*>(base + L.table_bytes);
+  unsigned long long* cursors = reinterpret_cast<unsigned long long*>(base + L.table_bytes + L.counts_bytes);
+  TC_CUDA(cudaMemsetAsync(counts, 0, L.counts_bytes + 64, s));
+  if (L.nb_total + L.nw_total > 0) {
+    BatchTable t;
+    t.views = reinterpret_cast<const CsrView*>(base);
+    t.pb = reinterpret_cast<const int64_t*>(base + L.views_bytes);
+    t.pw = reinterpret_cast<const int64_t*>(base + L.views_bytes + L.pre_bytes);
+    t.num_graphs = num_graphs;
+    const int64_t want = L.nb_total + (L.nw_total + kWarpsPerCTA - 1) / kWarpsPerCTA;
+    const int grid = (int)(want < 2 * kNumSMs ? want : 2 * kNumSMs);
+    k_count_batch<<<grid, kCountThreads, dev::kCountSmem, s>>>(t, counts, cursors);
+    TC_CUDA(cudaGetLastError());
+  }
+  TC_CUDA(cudaMemcpyAsync(host_counts, counts, (size_t)num_graphs * 8, cudaMemcpyDeviceToHost, s));
+  return TC_OK;
 }
 
 }  // namespace
@@ -113,63 +191,109 @@ extern "C" TC_API tc_status tc_count_batch(tc_graph* const* gs, int32_t num_grap
     return TC_ERR_INVALID_ARG;
   }
   if (num_graphs == 0) return TC_OK;
-  for (int32_t i = 0; i < num_graphs; ++i) {
-    if (!gs[i]) {
-      set_error("tc_count_batch: NULL graph handle");
-      return TC_ERR_INVALID_ARG;
-    }
-    if (!gs[i]->built) {
-      set_error("tc_count_batch: a graph is not built");
-      return TC_ERR_STATE;
-    }
-  }
+  TC_TRY(check_batch(gs, num_graphs, "tc_count_batch"));
   cudaStream_t s = (cudaStream_t)stream;
   const Allocator& a = gs[0]->alloc;
-  const size_t G = (size_t)num_graphs;
-  // host table: views | pb | pw, then device: counts | cursors
-  const size_t views_bytes = ((G * sizeof(CsrView)) + 255) / 256 * 256;
-  const size_t pre_bytes = ((G + 1) * 8 + 255) / 256 * 256;
-  const size_t table_bytes = views_bytes + 2 * pre_bytes;
-  const size_t counts_bytes = (G * 8 + 255) / 256 * 256;
-  std::vector<unsigned char> host(table_bytes, 0);
-  CsrView* hv = reinterpret_cast<CsrView*>(host.data());
-  int64_t* hpb = reinterpret_cast<int64_t*>(host.data() + views_bytes);
-  int64_t* hpw = reinterpret_cast<int64_t*>(host.data() + views_bytes + pre_bytes);
-  hpb[0] = hpw[0] = 0;
-  for (size_t i = 0; i < G; ++i) {
-    hv[i] = gs[i]->view();
-    hpb[i + 1] = hpb[i] + gs[i]->nb;
-    hpw[i + 1] = hpw[i] + gs[i]->nw;
-  }
+  std::vector<unsigned char> host;
+  const BatchLayout L = batch_table(gs, num_graphs, host);
+  TC_CUDA(cudaFuncSetAttribute(k_count_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, dev::kCountSmem));
   Buf dev;
-  TC_TRY(buf_alloc(a, dev, table_bytes + counts_bytes + 64, s));
-  tc_status st = TC_OK;
-  do {
-    unsigned char* base = dev.as<unsigned char>();
-    if ((st = cuda_status(cudaMemcpyAsync(base, host.data(), table_bytes, cudaMemcpyHostToDevice, s), "H2D table")))
-      break;
-    unsigned long long* counts = reinterpret_cast<unsigned long long*>(base + table_bytes);
-    unsigned long long* cursors = reinterpret_cast<unsigned long long*>(base + table_bytes + counts_bytes);
-    if ((st = cuda_status(cudaMemsetAsync(counts, 0, counts_bytes + 64, s), "memset counts"))) break;
-    BatchTable t;
-    t.views = reinterpret_cast<const CsrView*>(base);
-    t.pb = reinterpret_cast<const int64_t*>(base + views_bytes);
-    t.pw = reinterpret_cast<const int64_t*>(base + views_bytes + pre_bytes);
-    t.num_graphs = num_graphs;
-    if (hpb[G] + hpw[G] > 0) {
-      if ((st = cuda_status(cudaFuncSetAttribute(k_count_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 dev::kCountSmem),
-                            "smem attr")))
-        break;
-      const int64_t want = hpb[G] + (hpw[G] + kWarpsPerCTA - 1) / kWarpsPerCTA;
-      const int grid = (int)(want < 2 * kNumSMs ? want : 2 * kNumSMs);
-      k_count_batch<<<grid, kCountThreads, dev::kCountSmem, s>>>(t, counts, cursors); note_launch();
-      if ((st = cuda_status(cudaGetLastError(), "k_count_batch"))) break;
-    }
-    if ((st = cuda_status(cudaMemcpyAsync(out_counts, counts, G * 8, cudaMemcpyDeviceToHost, s), "D2H counts")))
-      break;
+  TC_TRY(buf_alloc(a, dev, L.total_bytes, s));
+  tc_status st = cuda_status(cudaMemcpyAsync(dev.p, host.data(), L.table_bytes, cudaMemcpyHostToDevice, s), "H2D");
+  if (st == TC_OK) st = batch_launch(dev.as<unsigned char>(), L, num_graphs, out_counts, s);
+  if (st == TC_OK) {
+    if (L.nb_total + L.nw_total > 0) note_launch();
     st = cuda_status(cudaStreamSynchronize(s), "tc_count_batch sync");
-  } while (0);
+  }
   buf_release(a, dev, s);
   return st;
+}
+
+// ---- batch plans: the launch sequence of a fixed set of graphs, captured once as a CUDA graph ---------------------
+struct tc_batch_plan {
+  std::vector<tc_graph*> graphs;
+  tc::Allocator alloc;
+  tc::Buf dev;
+  uint64_t* host_counts = nullptr;  // pinned
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool launches_kernel = false;
+};
+
+extern "C" TC_API void tc_batch_plan_free(tc_batch_plan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->host_counts) cudaFreeHost(p->host_counts);
+  cudaStream_t s = p->graphs.empty() ? nullptr : p->graphs[0]->last_stream;
+  tc::buf_release(p->alloc, p->dev, s);
+  delete p;
+}
+
+extern "C" TC_API tc_status tc_batch_plan_create(tc_graph* const* gs, int32_t num_graphs, void* stream,
+                                                 tc_batch_plan** out) {
+  if (!out || num_graphs <= 0 || !gs) {
+    set_error("tc_batch_plan_create: bad arguments");
+    return TC_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  TC_TRY(check_batch(gs, num_graphs, "tc_batch_plan_create"));
+  cudaStream_t s = (cudaStream_t)stream;
+  tc_batch_plan* p = new (std::nothrow) tc_batch_plan();
+  if (!p) {
+    set_error("tc_batch_plan_create: host allocation failed");
+    return TC_ERR_NO_MEMORY;
+  }
+  p->graphs.assign(gs, gs + num_graphs);
+  p->alloc = gs[0]->alloc;
+  std::vector<unsigned char> host;
+  const BatchLayout L = batch_table(gs, num_graphs, host);
+  p->launches_kernel = L.nb_total + L.nw_total > 0;
+  tc_status st = TC_OK;
+  do {
+    if ((st = cuda_status(cudaFuncSetAttribute(k_count_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               dev::kCountSmem),
+                          "smem attr")))
+      break;
+    if ((st = buf_alloc(p->alloc, p->dev, L.total_bytes, s))) break;
+    if ((st = cuda_status(cudaMallocHost((void**)&p->host_counts, (size_t)num_graphs * 8), "pinned counts"))) break;
+    if ((st = cuda_status(cudaMemcpyAsync(p->dev.p, host.data(), L.table_bytes, cudaMemcpyHostToDevice, s), "H2D")))
+      break;
+    if ((st = cuda_status(cudaStreamSynchronize(s), "sync table"))) break;
+    // capture: memset counts and cursors -> persistent kernel -> D2H of the counts.  Capture happens on a private
+    // stream (the legacy default stream cannot be captured); the plan is replayed on the caller's stream.
+    cudaStream_t cap = nullptr;
+    if ((st = cuda_status(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream"))) break;
+    cudaError_t begin = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    tc_status launch = TC_OK;
+    cudaError_t end = cudaSuccess;
+    if (begin == cudaSuccess) {
+      launch = batch_launch(p->dev.as<unsigned char>(), L, num_graphs, p->host_counts, cap);
+      end = cudaStreamEndCapture(cap, &p->graph);
+    }
+    cudaStreamDestroy(cap);
+    if ((st = cuda_status(begin, "begin capture"))) break;
+    if ((st = launch)) break;
+    if ((st = cuda_status(end, "end capture"))) break;
+    if ((st = cuda_status(cudaGraphInstantiate(&p->exec, p->graph, 0), "instantiate"))) break;
+  } while (0);
+  if (st != TC_OK) {
+    tc_batch_plan_free(p);
+    return st;
+  }
+  *out = p;
+  return TC_OK;
+}
+
+extern "C" TC_API tc_status tc_batch_plan_run(tc_batch_plan* p, uint64_t* out_counts, void* stream) {
+  if (!p || !out_counts) {
+    set_error("tc_batch_plan_run: bad arguments");
+    return TC_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  TC_CUDA(cudaGraphLaunch(p->exec, s));
+  if (p->launches_kernel) note_launch();
+  TC_CUDA(cudaStreamSynchronize(s));
+  memcpy(out_counts, p->host_counts, p->graphs.size() * 8);
+  return TC_OK;
 }

@@ -186,8 +186,8 @@ struct BinCounters {
 };
 
 __global__ void k_bins(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                       const int64_t* __restrict__ ustart, int64_t n, int32_t* __restrict__ list,
-                       BinCounters* __restrict__ bc) {
+                       const int64_t* __restrict__ ustart, int64_t n, int64_t block_min_work,
+                       int32_t* __restrict__ list, BinCounters* __restrict__ bc) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -208,7 +208,7 @@ __global__ void k_bins(const int64_t* __restrict__ off, const int32_t* __restric
     wsum += (unsigned long long)wtrue;
     if (d > dmax) dmax = (int)d;
     const bool keep = d >= 2 && wtrue > 0;
-    const bool blk = keep && wpad > kBlockMinWork;
+    const bool blk = keep && wpad > block_min_work;
     const bool wrp = keep && !blk;
     act += keep ? 1 : 0;
     const unsigned mb = __ballot_sync(kFull, blk);
@@ -383,7 +383,8 @@ tc_status build_graph(tc_graph* g, cudaStream_t s) {
     if ((st = cuda_status(cudaMemsetAsync(counters.p, 0, sizeof(BinCounters), s), "memset bins"))) break;
     if (n > 0) {
       k_bins<<<grid_for(n, 256), 256, 0, s>>>(g->off.as<int64_t>(), g->col.as<int32_t>(), ustart.as<int64_t>(), n,
-                                              g->list.as<int32_t>(), counters.as<BinCounters>());
+                                              block_min_work_for(m), g->list.as<int32_t>(),
+                                              counters.as<BinCounters>());
       if ((st = launched("k_bins"))) break;
     }
     if ((st = cuda_status(cudaMemcpyAsync(&hb, counters.p, sizeof(BinCounters), cudaMemcpyDeviceToHost, s),

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -17,6 +18,34 @@ std::atomic<unsigned long long> g_launches{0};
 }  // namespace
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+std::mutex g_tuning_mutex;
+// Built-in default, measured on GB300: graphs up to ~2^25 edges run fastest with every source in the warp bin;
+// larger ones with heavy sources (w(u) > 2^15) spread over a whole block.
+tc_tuning g_tuning = [] {
+  tc_tuning t{};
+  t.num_classes = 2;
+  t.class_max_edges[0] = int64_t(1) << 25;
+  t.block_min_work[0] = int64_t(1) << 40;
+  t.class_max_edges[1] = int64_t(1) << 62;
+  t.block_min_work[1] = int64_t(1) << 15;
+  t.batch_warp_max_edges = int64_t(1) << 25;
+  return t;
+}();
+}  // namespace
+
+int64_t batch_warp_max_edges() {
+  std::lock_guard<std::mutex> lk(g_tuning_mutex);
+  return g_tuning.batch_warp_max_edges;
+}
+
+int64_t block_min_work_for(int64_t m) {
+  std::lock_guard<std::mutex> lk(g_tuning_mutex);
+  for (int i = 0; i < g_tuning.num_classes; ++i)
+    if (m <= g_tuning.class_max_edges[i]) return g_tuning.block_min_work[i];
+  return g_tuning.block_min_work[g_tuning.num_classes - 1];
+}
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
@@ -106,6 +135,33 @@ tc_status check_built(const tc_graph* g) {
 extern "C" {
 
 TC_API const char* tc_last_error(void) { return g_last_error.c_str(); }
+
+TC_API tc_status tc_set_tuning(const tc_tuning* t) {
+  if (!t || t->num_classes < 1 || t->num_classes > TC_TUNING_MAX_CLASSES) {
+    set_error("tc_set_tuning: num_classes must be in 1..TC_TUNING_MAX_CLASSES");
+    return TC_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < t->num_classes; ++i) {
+    if (t->block_min_work[i] < 0 || t->batch_warp_max_edges < 0 ||
+        (i > 0 && t->class_max_edges[i] <= t->class_max_edges[i - 1])) {
+      set_error("tc_set_tuning: thresholds must be >= 0 and class bounds ascending");
+      return TC_ERR_INVALID_ARG;
+    }
+  }
+  std::lock_guard<std::mutex> lk(g_tuning_mutex);
+  g_tuning = *t;
+  return TC_OK;
+}
+
+TC_API tc_status tc_get_tuning(tc_tuning* t) {
+  if (!t) {
+    set_error("tc_get_tuning: NULL argument");
+    return TC_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_tuning_mutex);
+  *t = g_tuning;
+  return TC_OK;
+}
 
 TC_API uint64_t tc_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 

@@ -67,7 +67,9 @@ constexpr int kWarpLowSlots = 128;                 // per-warp hash of N+(u) ent
 constexpr int kBlockLowSlots = 2048;               // per-CTA hash of the same
 constexpr int kBlockRows = kCountThreads;          // rows (v in N+(u)) staged per CTA pass
 constexpr int kLongQuads = 16;                     // rows of >= 16 quads (64 ids) are walked by a whole warp
-constexpr int64_t kBlockMinWork = 1 << 15;         // sources with more candidate 2-paths go to a whole CTA
+// The warp/block split of sources (w(u) above the threshold -> a whole CTA) comes from the tuning table.
+int64_t block_min_work_for(int64_t m);
+int64_t batch_warp_max_edges();
 
 // Per-graph view used by the counting kernels.  Vertices are relabelled by rank in the (degree, id) order, so
 // every oriented edge goes from a lower to a higher id and rows hold ascending ids.  Rows start on 16-byte
@@ -81,6 +83,8 @@ struct CsrView {
   int32_t nw;           // warp-bin sources
   int32_t base_w;       // per-warp bitmap covers ids [base_w, n]
   int32_t base_b;       // per-CTA bitmap covers ids [base_b, n]
+  int32_t nbw;          // batches only: block-bin sources that are run one warp each (0 or nb)
+  int32_t pad;
 };
 
 // ------------------------------------------------------------------------------------------------------------
@@ -134,6 +138,8 @@ struct tc_graph {
     v.nw = (int32_t)nw;
     v.base_w = (int32_t)(n > tc::kWarpBitmapBits ? n - tc::kWarpBitmapBits : 0);
     v.base_b = (int32_t)(n > tc::kBlockBitmapBits ? n - tc::kBlockBitmapBits : 0);
+    v.nbw = 0;
+    v.pad = 0;
     return v;
   }
 };

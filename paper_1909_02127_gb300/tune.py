@@ -1,0 +1,137 @@
+"""Autotuner for the counting kernel's source split (warp per source vs block per source).
+
+For R-MAT and uniform graphs of increasing size it builds each graph once per candidate threshold, times the count
+(CUDA events, median of several launches), keeps the fastest threshold per graph, and writes a size-class table
+(class bounds at the geometric midpoints of the graphs' edge counts) to tuning.json, keyed by device name and SM
+count.  The binding installs that table through tc_set_tuning when the device matches.  Counts do not depend on
+the table; only speed does.
+
+    python -m paper_1909_02127_gb300.tune [--quick]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+CANDIDATES = [1 << 12, 1 << 13, 1 << 14, 1 << 15, 1 << 16, 1 << 17, 1 << 18, 1 << 20, 1 << 40]
+
+
+def time_count(tc, g, d_total, reps):
+    import torch
+    s = torch.cuda.current_stream()
+    tc.tc_count_device(g, d_total, s)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        a.record(s)
+        tc.tc_count_device(g, d_total, s)
+        b.record(s)
+    torch.cuda.synchronize()
+    ms = sorted(a.elapsed_time(b) for a, b in ev)
+    return ms[len(ms) // 2]
+
+
+def main():
+    import torch
+
+    import graphgen
+    import paper_1909_02127_gb300 as tc
+    from paper_1909_02127_gb300 import build
+
+    p = argparse.ArgumentParser()
+    p.add_argument("--quick", action="store_true")
+    p.add_argument("--out", default=tc.TUNING_FILE)
+    args = p.parse_args()
+    build.build()
+    tc.load_library()
+    scales = [14, 17, 20, 22] if args.quick else [12, 14, 16, 18, 20, 21, 22, 23, 24]
+    specs = [graphgen.rmat(sc, 16, graphgen.BASE_SEED + 500 + sc, name=f"rmat{sc}") for sc in scales]
+    specs += [graphgen.er(1 << 20, 16 << 20, graphgen.BASE_SEED + 600, name="er n=2^20")]
+    reps = 3 if args.quick else 5
+    d_total = torch.zeros(1, dtype=torch.int64, device="cuda")
+    results = []
+    for spec in specs:
+        ds, dd = spec.edges(device="cuda")
+        row = {"graph": spec.name, "times_ms": {}}
+        count = None
+        for cand in CANDIDATES:
+            tc.tc_set_tuning([(1 << 62, cand)])
+            g = tc.tc_load_edges(ds, dd, spec.n)
+            try:
+                tc.tc_build(g)
+                row["m"] = tc.tc_graph_get_info(g)["num_edges"]
+                row["times_ms"][str(cand)] = time_count(tc, g, d_total, reps)
+                c = int(d_total.item())
+                if count is not None and c != count:
+                    raise RuntimeError("count changed with the tuning")
+                count = c
+            finally:
+                tc.tc_free(g)
+        row["best"] = int(min(row["times_ms"], key=row["times_ms"].get))
+        results.append(row)
+        print(row["graph"], row["m"], row["best"], {k: round(v, 3) for k, v in row["times_ms"].items()}, flush=True)
+        del ds, dd
+        torch.cuda.empty_cache()
+    # size classes from the skewed (R-MAT) series, where the split matters; a graph keeps the previous class's
+    # threshold when that is within 2% of its best, so measurement noise does not split classes
+    series = sorted((r for r in results if r["graph"].startswith("rmat")), key=lambda r: r["m"])
+    classes = []
+    for i, r in enumerate(series):
+        bound = int(math.sqrt(r["m"] * series[i + 1]["m"])) if i + 1 < len(series) else 1 << 62
+        t = r["times_ms"]
+        choice = r["best"]
+        if classes and str(classes[-1][1]) in t and t[str(classes[-1][1])] <= 1.02 * t[str(choice)]:
+            choice = classes[-1][1]
+        if classes and classes[-1][1] == choice:
+            classes[-1][0] = bound
+        else:
+            classes.append([bound, choice])
+    # batches: how large a graph may be and still run all its sources one warp each (timed on the batch mix)
+    tc.tc_set_tuning([tuple(c) for c in classes])
+    mix = graphgen.batch_mix(512 if args.quick else 1024)
+    handles = []
+    for sp in mix:
+        s_, d_ = sp.edges(device="cuda")
+        handles.append(tc.tc_load_edges(s_, d_, sp.n))
+        tc.tc_build(handles[-1])
+    batch_times = {}
+    ref = None
+    for cand in (0, 1 << 20, 1 << 22, 1 << 25, 1 << 62):
+        tc.tc_set_tuning([tuple(c) for c in classes], batch_warp_max_edges=cand)
+        got = tc.tc_count_batch(handles)
+        torch.cuda.synchronize()
+        if ref is not None and not (got == ref).all():
+            raise RuntimeError("batch counts changed with the tuning")
+        ref = got
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            tc.tc_count_batch(handles)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        batch_times[str(cand)] = sorted(ts)[len(ts) // 2]
+    for h in handles:
+        tc.tc_free(h)
+    batch_warp = int(min(batch_times, key=batch_times.get))
+    print("batch", {k: round(v, 3) for k, v in batch_times.items()}, flush=True)
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    out = {"device": props.name, "sms": props.multi_processor_count, "cc": f"{props.major}.{props.minor}",
+           "classes": classes, "batch_warp_max_edges": batch_warp, "batch_times_ms": batch_times,
+           "measurements": results}
+    with open(args.out, "w") as f:
+        json.dump(out, f, indent=1)
+    tc.tc_set_tuning([tuple(c) for c in classes], batch_warp_max_edges=batch_warp)
+    print(json.dumps({"classes": classes, "batch_warp_max_edges": batch_warp}))
+
+
+if __name__ == "__main__":
+    main()

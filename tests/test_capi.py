@@ -86,6 +86,10 @@ def test_argument_errors_without_gpu(lib):
     assert lib.tc_server_poll(None, None, 0, 0, ctypes.byref(k)) == tc.TC_ERR_INVALID_ARG
     assert lib.tc_server_get_stats(None, None) == tc.TC_ERR_INVALID_ARG
     lib.tc_server_destroy(None)  # no-op
+    plan = ctypes.c_void_p()
+    assert lib.tc_batch_plan_create(None, 0, None, ctypes.byref(plan)) == tc.TC_ERR_INVALID_ARG
+    assert lib.tc_batch_plan_run(None, None, None) == tc.TC_ERR_INVALID_ARG
+    lib.tc_batch_plan_free(None)  # no-op
 
 
 def test_missing_library_fails_loudly(tmp_path):
@@ -97,3 +101,18 @@ def test_missing_library_fails_loudly(tmp_path):
             tc.load_library(str(tmp_path / "nope.so"))
     finally:
         tc._lib = saved
+
+
+def test_tuning_table_round_trip_without_gpu(lib):
+    import paper_1909_02127_gb300 as tc
+    saved = tc.tc_get_tuning()
+    try:
+        tc.tc_set_tuning([(1000, 5), (1 << 40, 1 << 15)])
+        assert tc.tc_get_tuning() == [(1000, 5), (1 << 40, 1 << 15)]
+        with pytest.raises(tc.TCError):
+            tc.tc_set_tuning([(1000, 5), (10, 7)])  # bounds not ascending
+        with pytest.raises(tc.TCError):
+            tc.tc_set_tuning([(1000, -1)])
+        assert tc.tc_get_tuning() == [(1000, 5), (1 << 40, 1 << 15)]
+    finally:
+        tc.tc_set_tuning(saved)

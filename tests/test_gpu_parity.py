@@ -56,9 +56,15 @@ def test_closed_forms(tc, name, g):
 
 @pytest.mark.parametrize("n", [200, 1500, 4300])
 def test_complete_graph_block_bin(tc, n):
-    """K_n: d+(u) runs from 0 to n-1 and the heavy sources go to the block bin (a whole CTA each)."""
+    """K_n: d+(u) runs from 0 to n-1; with a low threshold the heavy sources go to the block bin (a whole CTA
+    each) and the light ones to the warp bin."""
     src, dst, n, T, t = graphs.complete(n)
-    got, gt, info = gpu_counts(tc, src, dst, n)
+    saved = tc.tc_get_tuning()
+    try:
+        tc.tc_set_tuning([(1 << 62, 1 << 12)])
+        got, gt, info = gpu_counts(tc, src, dst, n)
+    finally:
+        tc.tc_set_tuning(saved)
     assert got == math.comb(n, 3)
     np.testing.assert_array_equal(gt, t)
     if n >= 1500:
@@ -285,6 +291,12 @@ def test_batch_equals_solo(tc):
         assert solo == expect
         got = tc.tc_count_batch(handles)
         assert got.tolist() == expect
+        plan = tc.tc_batch_plan_create(handles)
+        try:
+            for _ in range(3):  # the captured sequence zeroes its counters on every replay
+                assert tc.tc_batch_plan_run(plan, len(handles)).tolist() == expect
+        finally:
+            tc.tc_batch_plan_free(plan)
         # repeated handles and reversed order
         rev = handles[::-1] + handles[:5]
         got = tc.tc_count_batch(rev)
@@ -292,3 +304,22 @@ def test_batch_equals_solo(tc):
     finally:
         for h in handles:
             tc.tc_free(h)
+
+
+def test_counts_do_not_depend_on_tuning(tc):
+    spec = graphgen.rmat(15, 16, 51)
+    hs, hd = spec.edges()
+    T, _, t = oracle.count(hs, hd, spec.n, per_vertex=True)
+    saved = tc.tc_get_tuning()
+    try:
+        for table in ([(1 << 62, 0)], [(1 << 62, 1 << 40)], [(1 << 62, 1 << 12)], [(100, 0), (1 << 62, 1 << 40)]):
+            tc.tc_set_tuning(table)
+            got, gt, info = gpu_counts(tc, hs, hd, spec.n)
+            assert got == T
+            np.testing.assert_array_equal(gt, t)
+            if table == [(1 << 62, 0)]:
+                assert info["bin_warp"] == 0 and info["bin_block"] > 0
+            if table == [(1 << 62, 1 << 40)]:
+                assert info["bin_block"] == 0
+    finally:
+        tc.tc_set_tuning(saved)
