@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--build-workers", type=int, default=6, help="serve: concurrent CSR builders")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--allocator", default="library", choices=["library", "torch"],
+                   help="device memory for graphs: the library's pool, or torch's caching allocator")
     return p.parse_args()
 
 
@@ -217,11 +219,12 @@ def run_single(args, dist: Dist):
     torch.cuda.synchronize()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
     d_total = torch.zeros(1, dtype=torch.int64, device=dev)
+    alloc = "torch" if args.allocator == "torch" else None
 
     def step(events=None):
         if events:
             events[0].record(stream)
-        g = tc.tc_load_edges(ds, dd, spec.n, stream=stream)
+        g = tc.tc_load_edges(ds, dd, spec.n, stream=stream, allocator=alloc)
         tc.tc_build(g, stream)
         if events:
             events[1].record(stream)
@@ -281,7 +284,7 @@ def run_single(args, dist: Dist):
         hs = ds.cpu().pin_memory()
         hd = dd.cpu().pin_memory()
         for _ in range(max(1, min(args.warmup, 2))):
-            g = tc.tc_load_edges(hs, hd, spec.n, stream=stream)
+            g = tc.tc_load_edges(hs, hd, spec.n, stream=stream, allocator=alloc)
             tc.tc_build(g, stream)
             tc.tc_count(g, stream)
             tc.tc_free(g)
@@ -289,7 +292,7 @@ def run_single(args, dist: Dist):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            g = tc.tc_load_edges(hs, hd, spec.n, stream=stream)
+            g = tc.tc_load_edges(hs, hd, spec.n, stream=stream, allocator=alloc)
             tc.tc_build(g, stream)
             T_e2e = tc.tc_count(g, stream)
             tc.tc_free(g)
@@ -321,6 +324,7 @@ def run_single(args, dist: Dist):
         "warmup": args.warmup, "ms_per_step": round(statistics.mean(step_ms), 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32/uint64 (exact integer)", "data": "synthetic",
         "config": {"workload": spec.name, "n": spec.n, "generated_pairs": spec.num_edges, "m": m,
+                   "allocator": args.allocator,
                    "wedges": info["num_wedges"], "triangles": T_ref, "seed": spec.seed,
                    "l2": "2x L2 buffer written between timed steps; edge list (8 B/pair) exceeds L2",
                    "parallelism": f"replicas x{dist.world}"},
@@ -544,7 +548,8 @@ def run_reference(args, dist: Dist):
         "value": round(value, 5), "unit": "GTEPS", "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(statistics.mean(times) * 1e3, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32/uint64 (exact integer)", "data": "synthetic",
-        "config": {"workload": spec.name, "n": spec.n, "generated_pairs": spec.num_edges, "m": m, "triangles": T},
+        "config": {"workload": spec.name, "n": spec.n, "generated_pairs": spec.num_edges, "m": m,
+                   "allocator": args.allocator, "triangles": T},
         "cpu_baseline": {"value": round(value, 5), "unit": "GTEPS", "cores": cores, "kind": "oracle",
                          "sample": f"whole {spec.name} graph per step (sort+CSR+merge count)"},
         "e2e": {"value": round(value, 5), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

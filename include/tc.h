@@ -15,8 +15,9 @@
  *  - Streams: `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.  All device work of
  *    a call is ordered on that stream.
  *  - Ids: vertex ids are int32 in [0, n).  Counts are exact uint64.
- *  - Memory: every device buffer is obtained from the graph's allocator (tc_allocator, or cudaMallocAsync on the
- *    call's stream when none is given) and returned to it; the graph owns its buffers until tc_free.
+ *  - Memory: every device buffer is obtained from the graph's allocator (tc_allocator; when none is given, a
+ *    stream-ordered pool that the library keeps per device and that holds on to freed memory) and returned to it;
+ *    the graph owns its buffers until tc_free.
  *  - Threads: a tc_graph may be used by one host thread at a time.
  */
 #ifndef TC_H
@@ -83,7 +84,7 @@ typedef struct tc_graph_info {
  *                arrays once the call returns.
  *   num_edges    >= 0 and < 2^32 - 1.
  *   num_vertices n >= 0; every endpoint must lie in [0, n), else TC_ERR_OUT_OF_RANGE and no graph is returned.
- *   alloc        device memory provider, or NULL for cudaMallocAsync/cudaFreeAsync on the call's stream.  The
+ *   alloc        device memory provider, or NULL for the library's per-device stream-ordered pool.  The
  *                struct is copied; its functions must stay valid until tc_free.
  *   out          receives the new graph handle (set to NULL on failure).
  * Self-loops and repeated pairs are accepted and removed by tc_build (the simple-graph reading of Def. 1).

@@ -2,8 +2,9 @@
 GPUs", HPEC 2019).
 
 Argument marshalling only: every step of the computation runs in the CUDA kernels of ``csrc/`` behind the C ABI of
-``include/tc.h``.  The functions carry the C names.  PyTorch supplies device memory (through the allocator hook)
-and streams.  There is no CPU fallback: if ``libtc.so`` is missing, every call raises.
+``include/tc.h``.  The functions carry the C names.  PyTorch supplies streams and, on request (allocator="torch"),
+device memory through the allocator hook; by default the library's own stream-ordered pool is used.  There is no
+CPU fallback: if ``libtc.so`` is missing, every call raises.
 """
 from __future__ import annotations
 
@@ -296,9 +297,10 @@ def _edge_ptrs(src, dst):
     return s.ctypes.data, d.ctypes.data, s.size, TC_PTR_HOST, (s, d)
 
 
-def tc_load_edges(src, dst, num_vertices: int, stream=None, allocator="torch") -> int:
+def tc_load_edges(src, dst, num_vertices: int, stream=None, allocator=None) -> int:
     """Load the undirected pairs (src[i], dst[i]) of a graph on [0, num_vertices); returns a tc_graph handle.
-    allocator: "torch" (torch's caching allocator), None (cudaMallocAsync inside the library)."""
+    allocator: None (the library's per-device stream-ordered pool) or "torch" (torch's caching allocator, through
+    a callback per allocation)."""
     lib = load_library()
     sp, dp, m, flags, keep = _edge_ptrs(src, dst)
     alloc = ctypes.byref(torch_allocator().struct) if allocator == "torch" else None
@@ -481,7 +483,7 @@ class Server:
 class Graph:
     """Owning wrapper: Graph(src, dst, n) loads and builds; count() / count_per_vertex(); freed on close()."""
 
-    def __init__(self, src, dst, num_vertices: int, stream=None, allocator="torch", build: bool = True):
+    def __init__(self, src, dst, num_vertices: int, stream=None, allocator=None, build: bool = True):
         self.handle = tc_load_edges(src, dst, num_vertices, stream=stream, allocator=allocator)
         self.stream = stream
         if build:

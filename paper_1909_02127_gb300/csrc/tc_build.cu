@@ -30,30 +30,83 @@ __device__ __forceinline__ void agg_inc(int32_t* cnt, uint32_t idx, bool active)
   if (active && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[idx], __popc(peers));
 }
 
-__global__ void k_pack(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t len, int64_t n,
-                       int B, uint64_t* __restrict__ keys, int32_t* __restrict__ indeg, uint32_t* __restrict__ err) {
+// Ingest: validate, drop self-loops, pack, and count the input pairs at each vertex.  Counts are first combined per
+// tile of kPackTile pairs in a shared-memory hash (hubs repeat often; the table has twice as many slots as a tile
+// has endpoints), then added to global memory once per distinct vertex of the tile; a vertex that finds no slot
+// within kPackProbe probes is added directly.
+constexpr int kPackThreads = 256;
+constexpr int kPackItems = 4;
+constexpr int kPackTile = kPackThreads * kPackItems;  // 1024 pairs, <= 2048 distinct endpoints
+constexpr int kPackSlots = 4096;
+constexpr int kPackProbe = 8;
+
+__device__ __forceinline__ void pack_count(int32_t* skey, int32_t* scnt, int32_t* used, int32_t* nused,
+                                           int32_t* indeg, int32_t x) {
+  uint32_t s = ((uint32_t)x * 2654435761u) >> 20;  // 12 bits
+  for (int p = 0; p < kPackProbe; ++p) {
+    const int32_t k = skey[s];
+    if (k == x) {
+      atomicAdd(&scnt[s], 1);
+      return;
+    }
+    if (k < 0) {
+      const int32_t prev = atomicCAS(&skey[s], -1, x);
+      if (prev == -1) {
+        used[atomicAdd(nused, 1)] = (int32_t)s;
+        atomicAdd(&scnt[s], 1);
+        return;
+      }
+      if (prev == x) {
+        atomicAdd(&scnt[s], 1);
+        return;
+      }
+    }
+    s = (s + 1) & (kPackSlots - 1);
+  }
+  atomicAdd(&indeg[x], 1);
+}
+
+__global__ void __launch_bounds__(kPackThreads) k_pack(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                                                       int64_t len, int64_t n, int B, uint64_t* __restrict__ keys,
+                                                       int32_t* __restrict__ indeg, uint32_t* __restrict__ err) {
+  __shared__ int32_t skey[kPackSlots];
+  __shared__ int32_t scnt[kPackSlots];
+  __shared__ int32_t used[2 * kPackTile];
+  __shared__ int32_t nused;
   const uint64_t sentinel = (1ull << (2 * B)) - 1ull;
+  for (int i = threadIdx.x; i < kPackSlots; i += kPackThreads) {
+    skey[i] = -1;
+    scnt[i] = 0;
+  }
+  if (threadIdx.x == 0) nused = 0;
+  __syncthreads();
   bool bad = false;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < len; base += stride) {
-    const int64_t i = base + threadIdx.x;
-    int32_t a = 0, b = 0;
-    bool pair = false;
-    if (i < len) {
-      a = src[i];
-      b = dst[i];
+  for (int64_t tile = (int64_t)blockIdx.x * kPackTile; tile < len; tile += (int64_t)gridDim.x * kPackTile) {
+    for (int j = 0; j < kPackItems; ++j) {
+      const int64_t i = tile + j * kPackThreads + threadIdx.x;
+      if (i >= len) break;
+      const int32_t a = src[i], b = dst[i];
       uint64_t key = sentinel;
       if (a < 0 || b < 0 || a >= n || b >= n) {
         bad = true;
       } else if (a != b) {
-        const uint64_t lo = (uint64_t)(a < b ? a : b), hi = (uint64_t)(a < b ? b : a);
-        key = (lo << B) | hi;
-        pair = true;
+        key = ((uint64_t)(a < b ? a : b) << B) | (uint64_t)(a < b ? b : a);
+        pack_count(skey, scnt, used, &nused, indeg, a);
+        pack_count(skey, scnt, used, &nused, indeg, b);
       }
       keys[i] = key;
     }
-    agg_inc(indeg, (uint32_t)a, pair);
-    agg_inc(indeg, (uint32_t)b, pair);
+    __syncthreads();
+    const int nu = nused;
+    for (int t = threadIdx.x; t < nu; t += kPackThreads) {
+      const int32_t slot = used[t];
+      atomicAdd(&indeg[skey[slot]], scnt[slot]);
+      skey[slot] = -1;
+      scnt[slot] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) nused = 0;
+    __syncthreads();
   }
   if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(err, 1u);
 }
@@ -245,8 +298,10 @@ __global__ void k_unpermute(const unsigned long long* __restrict__ by_rank, cons
 tc_status pack_edges(tc_graph* g, const int32_t* src, const int32_t* dst, int64_t len, int64_t offset,
                      uint32_t* d_err, cudaStream_t s) {
   if (len <= 0) return TC_OK;
-  k_pack<<<grid_for(len, 256), 256, 0, s>>>(src, dst, len, g->n, g->key_bits, g->keys.as<uint64_t>() + offset,
-                                            g->indeg.as<int32_t>(), d_err);
+  const int64_t tiles = (len + kPackTile - 1) / kPackTile;
+  const int grid = (int)(tiles < 4 * kNumSMs ? tiles : 4 * kNumSMs);
+  k_pack<<<grid, kPackThreads, 0, s>>>(src, dst, len, g->n, g->key_bits, g->keys.as<uint64_t>() + offset,
+                                       g->indeg.as<int32_t>(), d_err);
   note_launch();
   TC_CUDA(cudaGetLastError());
   return TC_OK;

@@ -55,11 +55,44 @@ tc_status cuda_status(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? TC_ERR_NO_MEMORY : TC_ERR_CUDA;
 }
 
+namespace {
+// The library's own stream-ordered pool per device, used when a graph has no allocator.  It keeps freed memory
+// (release threshold: unlimited), so repeated builds do not map and unmap device memory at every synchronisation.
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pools[64] = {};
+
+cudaMemPool_t library_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(g_pool_mutex);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;
+    (void)cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[dev] = p;
+  }
+  return g_pools[dev];
+}
+}  // namespace
+
 void* Allocator::alloc(size_t bytes, cudaStream_t s) const {
   if (bytes == 0) bytes = 16;
   if (has_user) return user.alloc(bytes, (void*)s, user.ctx);
   void* p = nullptr;
-  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+  cudaMemPool_t pool = library_pool();
+  const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMallocAsync(&p, bytes, s);
+  if (e != cudaSuccess) {
     (void)cudaGetLastError();
     return nullptr;
   }

@@ -25,7 +25,7 @@ def tc():
 def test_noalloc_matches_per_vertex_twice(tc, spec):
     import torch
     hs, hd = spec.edges()
-    g = tc.tc_load_edges(hs, hd, spec.n)
+    g = tc.tc_load_edges(hs, hd, spec.n, allocator="torch")  # allocations visible to the counter below
     try:
         tc.tc_build(g)
         T_ref, t_ref = tc.tc_count_per_vertex(g)
