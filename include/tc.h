@@ -146,6 +146,21 @@ TC_API tc_status tc_count_per_vertex(tc_graph* g, uint64_t* per_vertex, uint64_t
 TC_API tc_status tc_count_per_vertex_noalloc(tc_graph* g, uint64_t* d_per_vertex, uint64_t* d_total, void* stream);
 
 /*
+ * tc_list_triangles — the matched subgraphs themselves (Sec. II-A: the outputs are the number of matches and the
+ * matched node id lists; Algorithm 1 returns M beside the count).  Lists the triangles whose first vertex in the
+ * visiting order has rank in [first_source, first_source + num_sources) (ranks run over [0, n); listing every
+ * triangle takes first_source = 0, num_sources = n, or several calls over consecutive ranges when the output would
+ * not fit in memory).  Each triangle is written once, as three int32 original ids in ascending order.
+ *   triples    capacity * 3 int32, host or device memory as `flags` says; the first min(found, capacity) triples
+ *              are written, in no particular order.
+ *   out_found  host pointer: the number of triangles in the range (it can exceed capacity: list again with more
+ *              room or a smaller range).
+ * Blocks until the outputs are valid.
+ */
+TC_API tc_status tc_list_triangles(tc_graph* g, int64_t first_source, int64_t num_sources, int32_t* triples,
+                                   int64_t capacity, uint64_t* out_found, uint32_t flags, void* stream);
+
+/*
  * tc_count_batch — count many built graphs in one persistent launch fed by a device work queue (the traversal of
  * tc_count applied to each graph independently; the batching itself has no counterpart in the paper).
  *   gs          num_graphs built graph handles (host array); the same handle may appear more than once.

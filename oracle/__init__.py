@@ -9,7 +9,9 @@ This module compiles it with g++ on first use and marshals numpy arrays to it.
 
 Parity status: oracle_count is pinned by closed forms, dense trace(A^3)/6 brute force and invariances
 (tests/test_oracle.py); oracle_vertex_triangles is pinned by the same closed forms, by the brute-force diagonal
-diag(A^3)/2 and by agreement with oracle_count's per-vertex output.
+diag(A^3)/2 and by agreement with oracle_count's per-vertex output; oracle_list_triangles is pinned by the clique
+closed form (every 3-subset listed) and by dense brute force (the right number of distinct triples, each a
+triangle) in tests/test_listing.py.
 """
 from __future__ import annotations
 
@@ -46,6 +48,8 @@ def _load():
         lib.oracle_vertex_triangles.argtypes = [i32p, i32p, ctypes.c_int64, ctypes.c_int32, i32p, ctypes.c_int64,
                                                 ctypes.c_int, u64p, i64p]
         lib.oracle_vertex_triangles.restype = ctypes.c_int
+        lib.oracle_list_triangles.argtypes = [i32p, i32p, ctypes.c_int64, ctypes.c_int32, i32p, ctypes.c_int64, u64p]
+        lib.oracle_list_triangles.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -81,6 +85,22 @@ def count(src, dst, n: int, per_vertex: bool = False, threads=None):
     if rc != 0:
         raise OracleError(f"oracle_count failed with code {rc}")
     return (int(T.value), int(m.value), t) if per_vertex else (int(T.value), int(m.value))
+
+
+def list_triangles(src, dst, n: int, capacity=None):
+    """Every triangle as an ascending id triple (shape (T, 3), in the order the enumeration finds them)."""
+    src, dst = _as_i32(src), _as_i32(dst)
+    lib = _load()
+    if capacity is None:
+        capacity = count(src, dst, n)[0]
+    out = np.zeros((max(int(capacity), 1), 3), dtype=np.int32)
+    T = ctypes.c_uint64(0)
+    rc = lib.oracle_list_triangles(src.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   dst.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), src.size, n,
+                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(capacity), ctypes.byref(T))
+    if rc != 0:
+        raise OracleError(f"oracle_list_triangles failed with code {rc}")
+    return out[: min(int(T.value), int(capacity))], int(T.value)
 
 
 def vertex_triangles(src, dst, n: int, xs, threads=None):

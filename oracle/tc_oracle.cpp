@@ -17,6 +17,9 @@
 // a < b, every c > b adjacent to both a and b closes one (this is the increasing-node-id visiting order that
 // Sec. III-A and Sec. III-C use to avoid duplicate matches).  The intersection is a merge of two sorted lists.
 //
+// oracle_list_triangles writes the triangles themselves (the matched node id lists of Sec. II-A) as the same
+// id-ordered triples a < b < c, in the order oracle_count finds them.
+//
 // oracle_vertex_triangles computes t(x) for chosen vertices straight from the definition
 //   t(x) = |{ {a,b} : a,b in N(x), a != b, {a,b} in E }|
 // without building any adjacency structure: one scan of the input collects N(x), a second collects the distinct
@@ -141,6 +144,58 @@ int oracle_count(const int32_t* src, const int32_t* dst, int64_t M, int32_t n, i
       per_vertex[x] = s;
     }
   }
+  return 0;
+}
+
+// The triangles themselves (the matched node id lists of Sec. II-A), as id triples a < b < c, enumerated exactly as
+// oracle_count counts them.  Writes min(T, capacity) triples to out (3 int32 each) and T to *out_T.
+// Returns 0, 1 (bad argument) or 2 (id out of range).  Single-threaded.
+int oracle_list_triangles(const int32_t* src, const int32_t* dst, int64_t M, int32_t n, int32_t* out,
+                          int64_t capacity, uint64_t* out_T) {
+  if (M < 0 || n < 0 || capacity < 0 || !out_T || (capacity > 0 && !out) || (M > 0 && (!src || !dst))) return 1;
+  std::vector<uint64_t> E;
+  if (int rc = simple_edges(src, dst, M, n, E)) return rc;
+  std::vector<int64_t> off((size_t)n + 1, 0);
+  for (uint64_t e : E) {
+    off[(e >> 32) + 1]++;
+    off[(uint32_t)e + 1]++;
+  }
+  for (int32_t x = 0; x < n; ++x) off[x + 1] += off[x];
+  std::vector<int32_t> adj((size_t)off[n]);
+  {
+    std::vector<int64_t> fill(off.begin(), off.end() - 1);
+    for (uint64_t e : E) {
+      const int32_t a = (int32_t)(e >> 32), b = (int32_t)(uint32_t)e;
+      adj[fill[a]++] = b;
+      adj[fill[b]++] = a;
+    }
+  }
+  for (int32_t x = 0; x < n; ++x) std::sort(adj.begin() + off[x], adj.begin() + off[x + 1]);
+  uint64_t T = 0;
+  for (uint64_t e : E) {
+    const int32_t a = (int32_t)(e >> 32), b = (int32_t)(uint32_t)e;
+    const int32_t* pa = std::lower_bound(adj.data() + off[a], adj.data() + off[a + 1], b + 1);
+    const int32_t* ea = adj.data() + off[a + 1];
+    const int32_t* pb = std::lower_bound(adj.data() + off[b], adj.data() + off[b + 1], b + 1);
+    const int32_t* eb = adj.data() + off[b + 1];
+    while (pa < ea && pb < eb) {
+      if (*pa < *pb) {
+        ++pa;
+      } else if (*pb < *pa) {
+        ++pb;
+      } else {
+        if ((int64_t)T < capacity) {
+          out[3 * T] = a;
+          out[3 * T + 1] = b;
+          out[3 * T + 2] = *pa;
+        }
+        ++T;
+        ++pa;
+        ++pb;
+      }
+    }
+  }
+  *out_T = T;
   return 0;
 }
 

@@ -72,7 +72,7 @@ class tc_server_stats(ctypes.Structure):
 
 
 EXPORTED = ["tc_load_edges", "tc_build", "tc_count", "tc_count_device", "tc_count_per_vertex",
-            "tc_count_per_vertex_noalloc", "tc_count_batch", "tc_server_create", "tc_server_submit",
+            "tc_count_per_vertex_noalloc", "tc_list_triangles", "tc_count_batch", "tc_server_create", "tc_server_submit",
             "tc_server_poll", "tc_server_get_stats", "tc_server_destroy", "tc_batch_plan_create",
             "tc_batch_plan_run", "tc_batch_plan_free",
             "tc_graph_get_info", "tc_copy_csr", "tc_free", "tc_last_error", "tc_kernel_launches", "tc_set_tuning",
@@ -103,6 +103,8 @@ def load_library(path: str = LIB_PATH):
     lib.tc_count_device.restype = st
     lib.tc_count_per_vertex.argtypes = [vp, vp, u64p, u32, vp]
     lib.tc_count_per_vertex.restype = st
+    lib.tc_list_triangles.argtypes = [vp, i64, i64, vp, i64, u64p, u32, vp]
+    lib.tc_list_triangles.restype = st
     lib.tc_count_per_vertex_noalloc.argtypes = [vp, vp, vp, vp]
     lib.tc_count_per_vertex_noalloc.restype = st
     lib.tc_count_batch.argtypes = [ctypes.POINTER(vp), i32, u64p, vp]
@@ -353,6 +355,25 @@ def tc_count_per_vertex_noalloc(g: int, d_per_vertex, d_total, stream=None) -> N
     pv = d_per_vertex if isinstance(d_per_vertex, int) else d_per_vertex.data_ptr()
     tot = d_total if isinstance(d_total, int) else d_total.data_ptr()
     _check(load_library().tc_count_per_vertex_noalloc(g, pv, tot, _stream_ptr(stream)))
+
+
+def tc_list_triangles(g: int, first_source: int = 0, num_sources: Optional[int] = None, capacity: Optional[int] = None,
+                      stream=None):
+    """Triangles whose first vertex (in the visiting order) has rank in [first_source, first_source+num_sources),
+    as an int32 array of shape (k, 3) of ascending original ids, and the number found (which exceeds k when the
+    capacity was too small).  capacity defaults to the graph's triangle count."""
+    lib = load_library()
+    n = tc_graph_get_info(g)["num_vertices"]
+    if num_sources is None:
+        num_sources = n - first_source
+    if capacity is None:
+        capacity = tc_count(g, stream)
+    out = np.zeros((max(int(capacity), 1), 3), dtype=np.int32)
+    found = ctypes.c_uint64(0)
+    _check(lib.tc_list_triangles(g, first_source, num_sources, out.ctypes.data, int(capacity), ctypes.byref(found),
+                                 TC_PTR_HOST, _stream_ptr(stream)))
+    k = min(int(found.value), int(capacity))
+    return out[:k], int(found.value)
 
 
 def tc_count_batch(gs: Sequence[int], stream=None) -> np.ndarray:

@@ -59,7 +59,8 @@ __global__ void __launch_bounds__(kCountThreads, 2)
       if (i >= NB) break;
       const int g = find_graph(t.pb, G, i);
       const CsrView v = t.views[g];
-      unsigned long long h = dev::block_source<false>(v.list[i - __ldg(&t.pb[g])], v, smem, br, ws, nullptr);
+      unsigned long long h =
+          dev::block_source<dev::kModeCount>(v.list[i - __ldg(&t.pb[g])], v, smem, br, ws, dev::Sink{});
       h = warp_sum(h);
       if (lane == 0) red[warp] = h;
       __syncthreads();
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(kCountThreads, 2)
         }
         const int64_t k = i - gbeg;  // the graph's warp work: nbw block-bin sources, then its warp bin
         const int32_t u = k < v.nbw ? v.list[k] : v.list[v.n - v.nw + (k - v.nbw)];
-        acc += dev::warp_source<false>(u, v, region, ltab, r, nullptr);
+        acc += dev::warp_source<dev::kModeCount>(u, v, region, ltab, r, dev::Sink{});
       }
     }
     acc = warp_sum(acc);

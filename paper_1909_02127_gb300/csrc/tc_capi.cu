@@ -381,6 +381,42 @@ TC_API tc_status tc_count_per_vertex(tc_graph* g, uint64_t* per_vertex, uint64_t
   return st;
 }
 
+TC_API tc_status tc_list_triangles(tc_graph* g, int64_t first_source, int64_t num_sources, int32_t* triples,
+                                   int64_t capacity, uint64_t* out_found, uint32_t flags, void* stream) {
+  TC_TRY(check_built(g));
+  if (flags != TC_PTR_HOST && flags != TC_PTR_DEVICE) {
+    set_error("tc_list_triangles: flags must be exactly one of TC_PTR_HOST, TC_PTR_DEVICE");
+    return TC_ERR_INVALID_ARG;
+  }
+  if (!out_found || capacity < 0 || (capacity > 0 && !triples) || first_source < 0 || num_sources < 0) {
+    set_error("tc_list_triangles: bad arguments");
+    return TC_ERR_INVALID_ARG;
+  }
+  if (first_source > g->n) first_source = g->n;
+  if (num_sources > g->n - first_source) num_sources = g->n - first_source;
+  cudaStream_t s = (cudaStream_t)stream;
+  g->last_stream = s;
+  const bool host = flags == TC_PTR_HOST;
+  Buf tmp;
+  int32_t* d_tri = triples;
+  if (host && capacity > 0) {
+    TC_TRY(buf_alloc(g->alloc, tmp, (size_t)capacity * 12, s));
+    d_tri = tmp.as<int32_t>();
+  }
+  uint64_t* words = g->acc.as<uint64_t>();  // [0]: found, [1]: work cursor
+  tc_status st = launch_list(g, first_source, num_sources, d_tri, capacity, words, words + 1, s);
+  if (st == TC_OK) st = cuda_status(cudaMemcpyAsync(g->host_total, words, 8, cudaMemcpyDeviceToHost, s), "D2H found");
+  if (st == TC_OK) st = cuda_status(cudaStreamSynchronize(s), "tc_list_triangles sync");
+  if (st == TC_OK && host && capacity > 0) {
+    const uint64_t found = *g->host_total;
+    const uint64_t k = found < (uint64_t)capacity ? found : (uint64_t)capacity;
+    if (k > 0) st = cuda_status(cudaMemcpy(triples, d_tri, (size_t)k * 12, cudaMemcpyDeviceToHost), "D2H triples");
+  }
+  buf_release(g->alloc, tmp, s);
+  if (st == TC_OK) *out_found = *g->host_total;
+  return st;
+}
+
 TC_API tc_status tc_graph_get_info(const tc_graph* g, tc_graph_info* info) {
   if (!g || !info) {
     set_error("tc_graph_get_info: NULL argument");

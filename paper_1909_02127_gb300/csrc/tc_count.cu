@@ -9,15 +9,14 @@
 namespace tc {
 namespace {
 
-template <bool PV>
+template <int MODE>
 __global__ void __launch_bounds__(kCountThreads, 2)
-    k_count(CsrView g, unsigned long long* __restrict__ total, unsigned long long* __restrict__ pv,
-            uint32_t* __restrict__ cursors) {
+    k_count(CsrView g, unsigned long long* __restrict__ total, dev::Sink sk, uint32_t* __restrict__ cursors) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint32_t ws[32];
   __shared__ unsigned long long red[kWarpsPerCTA];
   __shared__ int s_idx;
-  unsigned long long acc = dev::count_graph<PV>(g, pv, cursors, smem, ws, &s_idx);
+  unsigned long long acc = dev::count_graph<MODE>(g, sk, cursors, smem, ws, &s_idx);
   acc = warp_sum(acc);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
@@ -42,15 +41,75 @@ tc_status launch_count(const tc_graph* g, uint64_t* d_total, uint64_t* d_per_ver
   if (g->nb + g->nw == 0) return TC_OK;
   TC_CUDA(cudaMemsetAsync(d_cursors, 0, 2 * sizeof(uint32_t), s));
   const int grid = count_grid(g);
+  dev::Sink sk;
   if (d_per_vertex) {
-    TC_CUDA(cudaFuncSetAttribute(k_count<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dev::kCountSmem));
-    k_count<true><<<grid, kCountThreads, dev::kCountSmem, s>>>(g->view(), (unsigned long long*)d_total,
-                                                                (unsigned long long*)d_per_vertex, d_cursors);
+    sk.pv = (unsigned long long*)d_per_vertex;
+    TC_CUDA(cudaFuncSetAttribute(k_count<dev::kModeVertex>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 dev::kCountSmem));
+    k_count<dev::kModeVertex><<<grid, kCountThreads, dev::kCountSmem, s>>>(g->view(), (unsigned long long*)d_total,
+                                                                           sk, d_cursors);
   } else {
-    TC_CUDA(cudaFuncSetAttribute(k_count<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dev::kCountSmem));
-    k_count<false><<<grid, kCountThreads, dev::kCountSmem, s>>>(g->view(), (unsigned long long*)d_total, nullptr,
-                                                                 d_cursors);
+    TC_CUDA(cudaFuncSetAttribute(k_count<dev::kModeCount>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 dev::kCountSmem));
+    k_count<dev::kModeCount><<<grid, kCountThreads, dev::kCountSmem, s>>>(g->view(), (unsigned long long*)d_total,
+                                                                          sk, d_cursors);
   }
+  note_launch();
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+}  // namespace tc
+
+// ---- listing -------------------------------------------------------------------------------------------------------
+namespace tc {
+namespace {
+
+// Lists the triangles whose first vertex in the visiting order lies in ranks [first, first + count).  Warps take
+// sources four at a time; a source with fewer than two out-neighbours is skipped (it closes no 2-path).
+__global__ void __launch_bounds__(kCountThreads, 2)
+    k_list(CsrView g, int64_t first, int64_t count, dev::Sink sk, unsigned long long* __restrict__ cursor) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* region = smem + warp * dev::kWarpRegionWords;
+  const dev::Rows r = dev::warp_rows(region);
+  int32_t* ltab = dev::warp_low(region);
+  dev::zero_words(region, dev::kWarpBitmapWords, lane, 32);
+  for (int i = lane; i < kWarpLowSlots; i += 32) ltab[i] = -1;
+  __syncwarp();
+  constexpr int kChunk = 4;
+  while (true) {
+    long long idx = 0;
+    if (lane == 0) idx = (long long)atomicAdd(cursor, (unsigned long long)kChunk);
+    idx = __shfl_sync(kFull, idx, 0);
+    if (idx >= count) break;
+    const int64_t e = idx + kChunk < count ? idx + kChunk : count;
+    for (int64_t k = idx; k < e; ++k) {
+      const int32_t u = (int32_t)(first + k);
+      const int64_t beg = __ldg(&g.off[u]);
+      if (__ldg(&g.off[u + 1]) - beg < 4 || __ldg(&g.col[beg + 1]) >= g.n) continue;  // d+(u) < 2
+      dev::warp_source<dev::kModeList>(u, g, region, ltab, r, sk);
+    }
+  }
+}
+
+}  // namespace
+
+tc_status launch_list(const tc_graph* g, int64_t first, int64_t count, int32_t* d_triples, int64_t capacity,
+                      uint64_t* d_found, uint64_t* d_cursor, cudaStream_t s) {
+  TC_CUDA(cudaMemsetAsync(d_found, 0, sizeof(uint64_t), s));
+  TC_CUDA(cudaMemsetAsync(d_cursor, 0, sizeof(uint64_t), s));
+  if (count <= 0) return TC_OK;
+  dev::Sink sk;
+  sk.tri = d_triples;
+  sk.cursor = (unsigned long long*)d_found;
+  sk.capacity = (unsigned long long)(capacity > 0 ? capacity : 0);
+  sk.perm = g->perm.as<int32_t>();
+  const int64_t want = (count + kWarpsPerCTA - 1) / kWarpsPerCTA;
+  const int grid = (int)(want < 2 * kNumSMs ? want : 2 * kNumSMs);
+  TC_CUDA(cudaFuncSetAttribute(k_list, cudaFuncAttributeMaxDynamicSharedMemorySize, dev::kWarpSmem));
+  k_list<<<grid, kCountThreads, dev::kWarpSmem, s>>>(g->view(), first, count, sk,
+                                                     (unsigned long long*)d_cursor);
   note_launch();
   TC_CUDA(cudaGetLastError());
   return TC_OK;

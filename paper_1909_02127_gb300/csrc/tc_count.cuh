@@ -84,10 +84,52 @@ __device__ __forceinline__ void low_insert(const int32_t* __restrict__ row, int 
   }
 }
 
-template <bool PV, class C>
-__device__ __forceinline__ uint32_t test_quad(const int4 q, const C& c, unsigned long long* pv, int32_t v) {
+// What a closed 2-path produces besides the count.
+enum Mode { kModeCount = 0, kModeVertex = 1, kModeList = 2 };
+
+struct Sink {
+  unsigned long long* pv = nullptr;      // kModeVertex: t(x) in rank space
+  int32_t* tri = nullptr;                // kModeList: triples of original ids, 3 per triangle
+  unsigned long long* cursor = nullptr;  // kModeList: triangles found so far (also past `capacity`)
+  unsigned long long capacity = 0;       // kModeList: triples that fit in `tri`
+  const int32_t* perm = nullptr;         // kModeList: rank -> original id
+  int32_t u = 0;                         // kModeList: the current source
+};
+
+// Append the closed 2-paths u->v->w of this lane (h_i marks w_i) to the list.  Warp-collective: every lane calls it.
+__device__ __forceinline__ void list_hits(const int4 q, uint32_t h0, uint32_t h1, uint32_t h2, uint32_t h3,
+                                          const Sink& sk, int32_t v) {
+  const uint32_t cnt = h0 + h1 + h2 + h3;
+  const uint32_t incl = warp_inclusive_scan(cnt);
+  const uint32_t total = __shfl_sync(kFull, incl, 31);
+  if (total == 0) return;
+  unsigned long long base = 0;
+  if ((threadIdx.x & 31) == 31) base = atomicAdd(sk.cursor, (unsigned long long)total);
+  base = __shfl_sync(kFull, base, 31);
+  unsigned long long pos = base + incl - cnt;
+  const int32_t ws[4] = {q.x, q.y, q.z, q.w};
+  const uint32_t hs[4] = {h0, h1, h2, h3};
+  const int32_t a = __ldg(&sk.perm[sk.u]), b = __ldg(&sk.perm[v]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (!hs[i]) continue;
+    if (pos < sk.capacity) {  // the triangle as its sorted original ids
+      const int32_t c = __ldg(&sk.perm[ws[i]]);
+      const int32_t lo = min(a, min(b, c)), hi = max(a, max(b, c));
+      int32_t* t = sk.tri + 3 * pos;
+      t[0] = lo;
+      t[1] = a + b + c - lo - hi;
+      t[2] = hi;
+    }
+    ++pos;
+  }
+}
+
+template <int MODE, class C>
+__device__ __forceinline__ uint32_t test_quad(const int4 q, const C& c, const Sink& sk, int32_t v) {
   const uint32_t h0 = c(q.x), h1 = c(q.y), h2 = c(q.z), h3 = c(q.w);
-  if (PV) {
+  if (MODE == kModeVertex) {
+    unsigned long long* pv = sk.pv;
     if (h0) atomicAdd(&pv[q.x], 1ull);
     if (h1) atomicAdd(&pv[q.y], 1ull);
     if (h2) atomicAdd(&pv[q.z], 1ull);
@@ -96,23 +138,24 @@ __device__ __forceinline__ uint32_t test_quad(const int4 q, const C& c, unsigned
     if (s) atomicAdd(&pv[v], (unsigned long long)s);
     return s;
   }
+  if (MODE == kModeList) list_hits(q, h0, h1, h2, h3, sk, v);
   return (h0 + h1) + (h2 + h3);
 }
 
 // One long row (quads [q0, q0 + nq)) walked by the calling warp in windows of 128 quads, four independent loads in
 // flight per lane.  Trip counts and branches depend only on nq, so the warp never diverges; in the last window a
 // lane whose quad lies past the row tests the pad id n (never a member) instead of loading.
-template <bool PV, class C>
+template <int MODE, class C>
 __device__ __forceinline__ uint32_t long_row(const int4* __restrict__ col4, uint32_t q0, uint32_t nq, const C& c,
-                                             unsigned long long* pv, int32_t v, int32_t pad) {
+                                             const Sink& sk, int32_t v, int32_t pad) {
   const uint32_t lane = threadIdx.x & 31;
   const int4* p = col4 + q0 + lane;
   uint32_t hits = 0;
   uint32_t rem = nq;
   for (; rem >= 128; rem -= 128, p += 128) {
     const int4 a = __ldg(p), b = __ldg(p + 32), e = __ldg(p + 64), f = __ldg(p + 96);
-    hits += (test_quad<PV>(a, c, pv, v) + test_quad<PV>(b, c, pv, v)) +
-            (test_quad<PV>(e, c, pv, v) + test_quad<PV>(f, c, pv, v));
+    hits += (test_quad<MODE>(a, c, sk, v) + test_quad<MODE>(b, c, sk, v)) +
+            (test_quad<MODE>(e, c, sk, v) + test_quad<MODE>(f, c, sk, v));
   }
   if (rem > 0) {
     const int4 none = make_int4(pad, pad, pad, pad);
@@ -121,12 +164,12 @@ __device__ __forceinline__ uint32_t long_row(const int4* __restrict__ col4, uint
     if (rem > 64) {
       const int4 e = lane + 64 < rem ? __ldg(p + 64) : none;
       const int4 f = lane + 96 < rem ? __ldg(p + 96) : none;
-      hits += (test_quad<PV>(a, c, pv, v) + test_quad<PV>(b, c, pv, v)) +
-              (test_quad<PV>(e, c, pv, v) + test_quad<PV>(f, c, pv, v));
+      hits += (test_quad<MODE>(a, c, sk, v) + test_quad<MODE>(b, c, sk, v)) +
+              (test_quad<MODE>(e, c, sk, v) + test_quad<MODE>(f, c, sk, v));
     } else if (rem > 32) {
-      hits += test_quad<PV>(a, c, pv, v) + test_quad<PV>(b, c, pv, v);
+      hits += test_quad<MODE>(a, c, sk, v) + test_quad<MODE>(b, c, sk, v);
     } else {
-      hits += test_quad<PV>(a, c, pv, v);
+      hits += test_quad<MODE>(a, c, sk, v);
     }
   }
   return hits;
@@ -140,9 +183,9 @@ struct Rows {
 };
 
 // Walk quads [x0, x1) of the concatenated short rows 0..R-1 with one warp.
-template <bool PV, class C>
+template <int MODE, class C>
 __device__ __forceinline__ uint32_t walk(const Rows& r, int R, uint32_t x0, uint32_t x1,
-                                         const int4* __restrict__ col4, const C& c, unsigned long long* pv) {
+                                         const int4* __restrict__ col4, const C& c, const Sink& sk, int32_t pad) {
   uint32_t hits = 0;
   if (x0 >= x1) return 0;
   const int lane = threadIdx.x & 31;
@@ -166,10 +209,14 @@ __device__ __forceinline__ uint32_t walk(const Rows& r, int R, uint32_t x0, uint
     }
     const uint32_t starts = __reduce_or_sync(kFull, bit);
     const uint32_t x = base + lane;
-    if (x < x1) {
+    if (MODE == kModeList) {  // all lanes take part; a lane past x1 tests the pad id
+      const int own = x < x1 ? cur + __popc(starts & lt) : cur;
+      const int4 q = x < x1 ? __ldg(&col4[r.q0[own] + (x - r.P[own])]) : make_int4(pad, pad, pad, pad);
+      hits += test_quad<MODE>(q, c, sk, r.v[own]);
+    } else if (x < x1) {
       const int own = cur + __popc(starts & lt);
       const int4 q = __ldg(&col4[r.q0[own] + (x - r.P[own])]);
-      hits += test_quad<PV>(q, c, pv, PV ? r.v[own] : 0);
+      hits += test_quad<MODE>(q, c, sk, MODE != kModeCount ? r.v[own] : 0);
     }
     cur += __popc(starts);
   }
@@ -212,9 +259,9 @@ __device__ __forceinline__ uint32_t mark_row(const int32_t* __restrict__ row, in
 }
 
 // All second hops of source u for the calling warp, given its closing test.
-template <bool PV, class C>
+template <int MODE, class C>
 __device__ __forceinline__ uint32_t warp_hops(const CsrView& g, int64_t beg, int64_t len, const C& c, const Rows& r,
-                                              unsigned long long* pv) {
+                                              const Sink& sk) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
   const int4* col4 = reinterpret_cast<const int4*>(g.col);
@@ -229,8 +276,8 @@ __device__ __forceinline__ uint32_t warp_hops(const CsrView& g, int64_t beg, int
       const int k = __ffs(longs) - 1;
       longs &= longs - 1;
       const uint32_t q0 = __shfl_sync(kFull, ro.q0, k), nq = __shfl_sync(kFull, ro.nq, k);
-      const int32_t vk = PV ? __shfl_sync(kFull, v, k) : 0;
-      hits += long_row<PV>(col4, q0, nq, c, pv, vk, (int32_t)g.n);
+      const int32_t vk = MODE != kModeCount ? __shfl_sync(kFull, v, k) : 0;
+      hits += long_row<MODE>(col4, q0, nq, c, sk, vk, (int32_t)g.n);
     }
     const bool is_short = ro.nq > 0 && !is_long;
     const unsigned shorts = __ballot_sync(kFull, is_short);
@@ -242,10 +289,10 @@ __device__ __forceinline__ uint32_t warp_hops(const CsrView& g, int64_t beg, int
         const int k = __popc(shorts & lt);
         r.q0[k] = ro.q0;
         r.P[k] = incl - nq;
-        if (PV) r.v[k] = v;
+        if (MODE != kModeCount) r.v[k] = v;
       }
       __syncwarp();
-      hits += walk<PV>(r, __popc(shorts), 0, Q, col4, c, pv);
+      hits += walk<MODE>(r, __popc(shorts), 0, Q, col4, c, sk, (int32_t)g.n);
       __syncwarp();
     }
   }
@@ -254,10 +301,12 @@ __device__ __forceinline__ uint32_t warp_hops(const CsrView& g, int64_t beg, int
 
 // One source u, one warp.  bm is the warp's bitmap over [base_w, n] (all zero on entry and on return); ltab its
 // low-entry hash (all -1 on entry and on return).
-template <bool PV>
+template <int MODE>
 __device__ __forceinline__ uint32_t warp_source(int32_t u, const CsrView& g, uint32_t* bm, int32_t* ltab,
-                                                const Rows& r, unsigned long long* pv) {
+                                                const Rows& r, const Sink& sk_in) {
   const int lane = threadIdx.x & 31;
+  Sink sk = sk_in;
+  sk.u = u;
   const int64_t beg = __ldg(&g.off[u]), len = __ldg(&g.off[u + 1]) - beg;
   const int32_t* row = g.col + beg;
   const uint32_t nlow = warp_sum(mark_row(row, len, g.n, g.base_w, bm, true, lane, 32));
@@ -265,22 +314,22 @@ __device__ __forceinline__ uint32_t warp_source(int32_t u, const CsrView& g, uin
   constexpr uint32_t cap = (uint32_t)kWarpBitmapBits, lmask = (uint32_t)kWarpLowSlots - 1;
   uint32_t hits;
   if (nlow == 0) {
-    hits = warp_hops<PV>(g, beg, len, Closing<kLowNone>{bm, g.base_w, row, 0, cap}, r, pv);
+    hits = warp_hops<MODE>(g, beg, len, Closing<kLowNone>{bm, g.base_w, row, 0, cap}, r, sk);
   } else if (nlow <= (uint32_t)kWarpLowSlots / 2) {
     low_insert(row, (int)nlow, ltab, lmask, lane, 32);
     __syncwarp();
-    hits = warp_hops<PV>(g, beg, len, Closing<kLowHash>{bm, g.base_w, ltab, (int32_t)lmask, cap}, r, pv);
+    hits = warp_hops<MODE>(g, beg, len, Closing<kLowHash>{bm, g.base_w, ltab, (int32_t)lmask, cap}, r, sk);
     __syncwarp();
     for (int i = lane; i < kWarpLowSlots; i += 32) ltab[i] = -1;
   } else {
-    hits = warp_hops<PV>(g, beg, len, Closing<kLowSearch>{bm, g.base_w, row, (int32_t)nlow, cap}, r, pv);
+    hits = warp_hops<MODE>(g, beg, len, Closing<kLowSearch>{bm, g.base_w, row, (int32_t)nlow, cap}, r, sk);
   }
   __syncwarp();
   mark_row(row, len, g.n, g.base_w, bm, false, lane, 32);
   __syncwarp();
-  if (PV) {
+  if (MODE == kModeVertex) {
     const uint32_t s = warp_sum(hits);
-    if (lane == 0 && s) atomicAdd(&pv[u], (unsigned long long)s);
+    if (lane == 0 && s) atomicAdd(&sk.pv[u], (unsigned long long)s);
   }
   return hits;
 }
@@ -295,9 +344,9 @@ struct BlockRows {
   int32_t* ltab;
 };
 
-template <bool PV, class C>
+template <int MODE, class C>
 __device__ __forceinline__ uint32_t block_hops(const CsrView& g, int64_t beg, int64_t len, const C& c,
-                                               const BlockRows& br, uint32_t* ws, unsigned long long* pv) {
+                                               const BlockRows& br, uint32_t* ws, const Sink& sk) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int4* col4 = reinterpret_cast<const int4*>(g.col);
   uint32_t hits = 0;
@@ -314,12 +363,12 @@ __device__ __forceinline__ uint32_t block_hops(const CsrView& g, int64_t beg, in
     if (is_long) {
       br.lq0[lrank] = ro.q0;
       br.lnq[lrank] = ro.nq;
-      if (PV) br.lv[lrank] = v;
+      if (MODE != kModeCount) br.lv[lrank] = v;
     }
     if (is_short) {
       br.sr.q0[srank] = ro.q0;
       br.sr.P[srank] = pre;
-      if (PV) br.sr.v[srank] = v;
+      if (MODE != kModeCount) br.sr.v[srank] = v;
     }
     if (tid == 0) *br.next = 0;
     __syncthreads();
@@ -329,12 +378,12 @@ __device__ __forceinline__ uint32_t block_hops(const CsrView& g, int64_t beg, in
       if (lane == 0) k = atomicAdd(br.next, 1u);
       k = __shfl_sync(kFull, k, 0);
       if (k >= NL) break;
-      hits += long_row<PV>(col4, br.lq0[k], br.lnq[k], c, pv, PV ? br.lv[k] : 0, (int32_t)g.n);
+      hits += long_row<MODE>(col4, br.lq0[k], br.lnq[k], c, sk, MODE != kModeCount ? br.lv[k] : 0, (int32_t)g.n);
     }
     // short rows: equal contiguous shares of the quad stream
     const uint32_t per = (Q + kWarpsPerCTA - 1) / kWarpsPerCTA;
     const uint32_t x0 = min(Q, (uint32_t)warp * per), x1 = min(Q, x0 + per);
-    hits += walk<PV>(br.sr, (int)R, x0, x1, col4, c, pv);
+    hits += walk<MODE>(br.sr, (int)R, x0, x1, col4, c, sk, (int32_t)g.n);
     __syncthreads();
   }
   return hits;
@@ -342,10 +391,12 @@ __device__ __forceinline__ uint32_t block_hops(const CsrView& g, int64_t beg, in
 
 // One source u, the whole block.  bm is the block's bitmap over [base_b, n] (all zero on entry and on return);
 // br.ltab its low-entry hash (all -1 on entry and on return).
-template <bool PV>
+template <int MODE>
 __device__ __forceinline__ uint32_t block_source(int32_t u, const CsrView& g, uint32_t* bm, const BlockRows& br,
-                                                 uint32_t* ws, unsigned long long* pv) {
+                                                 uint32_t* ws, const Sink& sk_in) {
   const int tid = threadIdx.x, lane = tid & 31;
+  Sink sk = sk_in;
+  sk.u = u;
   const int64_t beg = __ldg(&g.off[u]), len = __ldg(&g.off[u + 1]) - beg;
   const int32_t* row = g.col + beg;
   uint32_t nlow;
@@ -354,19 +405,19 @@ __device__ __forceinline__ uint32_t block_source(int32_t u, const CsrView& g, ui
   constexpr uint32_t cap = (uint32_t)kBlockBitmapBits, lmask = (uint32_t)kBlockLowSlots - 1;
   uint32_t hits;
   if (nlow == 0) {
-    hits = block_hops<PV>(g, beg, len, Closing<kLowNone>{bm, g.base_b, row, 0, cap}, br, ws, pv);
+    hits = block_hops<MODE>(g, beg, len, Closing<kLowNone>{bm, g.base_b, row, 0, cap}, br, ws, sk);
   } else if (nlow <= (uint32_t)kBlockLowSlots / 2) {
     low_insert(row, (int)nlow, br.ltab, lmask, tid, kCountThreads);
     __syncthreads();
-    hits = block_hops<PV>(g, beg, len, Closing<kLowHash>{bm, g.base_b, br.ltab, (int32_t)lmask, cap}, br, ws, pv);
+    hits = block_hops<MODE>(g, beg, len, Closing<kLowHash>{bm, g.base_b, br.ltab, (int32_t)lmask, cap}, br, ws, sk);
     for (int i = tid; i < kBlockLowSlots; i += kCountThreads) br.ltab[i] = -1;  // block_hops ended with a barrier
   } else {
-    hits = block_hops<PV>(g, beg, len, Closing<kLowSearch>{bm, g.base_b, row, (int32_t)nlow, cap}, br, ws, pv);
+    hits = block_hops<MODE>(g, beg, len, Closing<kLowSearch>{bm, g.base_b, row, (int32_t)nlow, cap}, br, ws, sk);
   }
   mark_row(row, len, g.n, g.base_b, bm, false, tid, kCountThreads);
-  if (PV) {
+  if (MODE == kModeVertex) {
     const uint32_t s = warp_sum(hits);
-    if (lane == 0 && s) atomicAdd(&pv[u], (unsigned long long)s);
+    if (lane == 0 && s) atomicAdd(&sk.pv[u], (unsigned long long)s);
   }
   __syncthreads();
   return hits;
@@ -414,8 +465,8 @@ __device__ __forceinline__ void zero_words(uint32_t* p, int nwords, int t, int s
 
 // Count the triangles of one graph: block-bin sources first (one CTA each), then warp-bin sources.
 // cursors[0], cursors[1]: zeroed work counters of this graph.  Returns this thread's count.
-template <bool PV>
-__device__ __forceinline__ unsigned long long count_graph(const CsrView& g, unsigned long long* pv,
+template <int MODE>
+__device__ __forceinline__ unsigned long long count_graph(const CsrView& g, const Sink& sk,
                                                           uint32_t* cursors, uint32_t* smem, uint32_t* ws,
                                                           int* s_idx) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -431,7 +482,7 @@ __device__ __forceinline__ unsigned long long count_graph(const CsrView& g, unsi
       const int idx = *s_idx;
       __syncthreads();
       if (idx >= g.nb) break;
-      acc += block_source<PV>(g.list[idx], g, smem, br, ws, pv);
+      acc += block_source<MODE>(g.list[idx], g, smem, br, ws, sk);
     }
   }
   if (g.nw > 0) {
@@ -449,7 +500,7 @@ __device__ __forceinline__ unsigned long long count_graph(const CsrView& g, unsi
       idx = __shfl_sync(kFull, idx, 0);
       if (idx >= g.nw) break;
       const int e = min(idx + kChunk, g.nw);
-      for (int k = idx; k < e; ++k) acc += warp_source<PV>(wlist[k], g, region, ltab, r, pv);
+      for (int k = idx; k < e; ++k) acc += warp_source<MODE>(wlist[k], g, region, ltab, r, sk);
     }
   }
   return acc;
