@@ -15,7 +15,7 @@
 // on bit n - base, which is never set.
 //
 // Traversal.  Rows are 16-byte aligned and padded to whole quads, so every load is one aligned int4.  In warp mode
-// rows of >= kLongQuads quads are walked by the whole warp, four 32-quad steps in flight; shorter rows are
+// rows of >= kLongQuads quads are walked by the whole warp, two 32-quad steps in flight; shorter rows are
 // concatenated and cut into quads, and a warp walks this stream 32 quads at a time.  The row owning a lane's quad
 // is found without a search: the lanes holding the next 32 rows OR together one bit per row start inside the
 // window, and a lane's owner is the current row plus the number of starts below it (a popcount).  In block mode
@@ -142,9 +142,10 @@ __device__ __forceinline__ uint32_t test_quad(const int4 q, const C& c, const Si
   return (h0 + h1) + (h2 + h3);
 }
 
-// One long row (quads [q0, q0 + nq)) walked by the calling warp in windows of 128 quads, four independent loads in
-// flight per lane.  Trip counts and branches depend only on nq, so the warp never diverges; in the last window a
-// lane whose quad lies past the row tests the pad id n (never a member) instead of loading.
+// One long row (quads [q0, q0 + nq)) walked by the calling warp in windows of 64 quads, two independent loads in
+// flight per lane (measured faster than four: fewer registers and a cheaper tail).  Trip counts and branches
+// depend only on nq, so the warp never diverges; in the last window a lane whose quad lies past the row tests the
+// pad id n (never a member) instead of loading.
 template <int MODE, class C>
 __device__ __forceinline__ uint32_t long_row(const int4* __restrict__ col4, uint32_t q0, uint32_t nq, const C& c,
                                              const Sink& sk, int32_t v, int32_t pad) {
@@ -152,21 +153,15 @@ __device__ __forceinline__ uint32_t long_row(const int4* __restrict__ col4, uint
   const int4* p = col4 + q0 + lane;
   uint32_t hits = 0;
   uint32_t rem = nq;
-  for (; rem >= 128; rem -= 128, p += 128) {
-    const int4 a = __ldg(p), b = __ldg(p + 32), e = __ldg(p + 64), f = __ldg(p + 96);
-    hits += (test_quad<MODE>(a, c, sk, v) + test_quad<MODE>(b, c, sk, v)) +
-            (test_quad<MODE>(e, c, sk, v) + test_quad<MODE>(f, c, sk, v));
+  for (; rem >= 64; rem -= 64, p += 64) {
+    const int4 a = __ldg(p), b = __ldg(p + 32);
+    hits += test_quad<MODE>(a, c, sk, v) + test_quad<MODE>(b, c, sk, v);
   }
   if (rem > 0) {
     const int4 none = make_int4(pad, pad, pad, pad);
     const int4 a = lane < rem ? __ldg(p) : none;
-    const int4 b = lane + 32 < rem ? __ldg(p + 32) : none;
-    if (rem > 64) {
-      const int4 e = lane + 64 < rem ? __ldg(p + 64) : none;
-      const int4 f = lane + 96 < rem ? __ldg(p + 96) : none;
-      hits += (test_quad<MODE>(a, c, sk, v) + test_quad<MODE>(b, c, sk, v)) +
-              (test_quad<MODE>(e, c, sk, v) + test_quad<MODE>(f, c, sk, v));
-    } else if (rem > 32) {
+    if (rem > 32) {
+      const int4 b = lane + 32 < rem ? __ldg(p + 32) : none;
       hits += test_quad<MODE>(a, c, sk, v) + test_quad<MODE>(b, c, sk, v);
     } else {
       hits += test_quad<MODE>(a, c, sk, v);
