@@ -323,11 +323,9 @@ def run_single(args, dist: Dist):
         "value": round(value, 4), "unit": "GTEPS", "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(statistics.mean(step_ms), 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32/uint64 (exact integer)", "data": "synthetic",
-        "config": {"workload": spec.name, "n": spec.n, "generated_pairs": spec.num_edges, "m": m,
-                   "allocator": args.allocator,
-                   "wedges": info["num_wedges"], "triangles": T_ref, "seed": spec.seed,
-                   "l2": "2x L2 buffer written between timed steps; edge list (8 B/pair) exceeds L2",
-                   "parallelism": f"replicas x{dist.world}"},
+        "config": workload_config(spec, "2x L2 buffer written between timed steps; edge list (8 B/pair) exceeds L2",
+                                  dist.world),
+        "m": m, "wedges": info["num_wedges"], "triangles": T_ref, "allocator": args.allocator,
         "phases_ms": {"build": round(statistics.mean(build_ms), 4), "count": round(statistics.mean(count_ms), 4)},
         "count_gteps": round(m / mean_count_s / 1e9, 4),
         "triangles_per_s": round(T_ref / mean_count_s, 1),
@@ -341,18 +339,43 @@ def run_single(args, dist: Dist):
     return out
 
 
+# Graphs above this many generated pairs are sampled for the CPU legs: the oracle takes minutes on them.
+CPU_WHOLE_MAX_PAIRS = 1 << 25
+
+
+def workload_config(spec, l2, world):
+    """The workload's identity, the same on both arms."""
+    return {"workload": spec.name, "n": spec.n, "generated_pairs": spec.num_edges, "seed": spec.seed, "l2": l2,
+            "parallelism": f"replicas x{world}"}
+
+
+def cpu_sample(spec, scale):
+    """The graph the CPU legs time: the workload itself when it is small enough, else an R-MAT graph of the same
+    recipe (edge factor, noise, seed, id permutation) at a smaller scale; the rate per edge is the reported unit."""
+    import graphgen
+    if spec.num_edges <= CPU_WHOLE_MAX_PAIRS:
+        return spec, f"whole {spec.name} graph"
+    small = graphgen.rmat(scale, 16, spec.seed, permute=True, name=f"R-MAT scale {scale} ef 16 (permuted ids)")
+    return small, f"{small.name}, same recipe and seed as {spec.name}"
+
+
 def cpu_baseline(spec, ds, dd, T_expect):
-    """The oracle as it stands, on all host cores, on the same graph (whole graph: build + count)."""
+    """The oracle as it stands, on all host cores: the same graph when small enough, else a smaller graph of the
+    same recipe (build + count)."""
     import oracle
-    hs, hd = ds.cpu().numpy(), dd.cpu().numpy()
+    sample, what = cpu_sample(spec, 22)
+    if sample is spec:
+        hs, hd = ds.cpu().numpy(), dd.cpu().numpy()
+    else:
+        hs, hd = sample.edges()
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    T, m = oracle.count(hs, hd, spec.n, threads=cores)
+    T, m = oracle.count(hs, hd, sample.n, threads=cores)
     t = time.perf_counter() - t0
-    if T != T_expect:
+    if sample is spec and T != T_expect:
         raise RuntimeError(f"oracle {T} != GPU {T_expect}")
     return {"value": round(m / t / 1e9, 5), "unit": "GTEPS", "cores": cores, "kind": "oracle",
-            "sample": f"whole {spec.name} graph (sort+CSR+merge count), {t:.2f} s"}
+            "sample": f"{what} (sort+CSR+merge count), m = {m}, {t:.2f} s"}
 
 
 def run_batch(args, dist: Dist):
@@ -533,14 +556,15 @@ def run_reference(args, dist: Dist):
     if args.workload in ("batch", "serve"):
         return {"impl": "reference", "unavailable": "the oracle arm is defined for the single-graph workloads"}
     spec = graphgen.config(args.workload)
-    hs, hd = spec.edges()
+    sample, what = cpu_sample(spec, 21)
+    hs, hd = sample.edges()
     cores = os.cpu_count() or 1
     for _ in range(args.warmup):
-        oracle.count(hs, hd, spec.n, threads=cores)
+        oracle.count(hs, hd, sample.n, threads=cores)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        T, m = oracle.count(hs, hd, spec.n, threads=cores)
+        T, m = oracle.count(hs, hd, sample.n, threads=cores)
         times.append(time.perf_counter() - t0)
     value = m * len(times) / sum(times) / 1e9
     return {
@@ -548,10 +572,10 @@ def run_reference(args, dist: Dist):
         "value": round(value, 5), "unit": "GTEPS", "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(statistics.mean(times) * 1e3, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32/uint64 (exact integer)", "data": "synthetic",
-        "config": {"workload": spec.name, "n": spec.n, "generated_pairs": spec.num_edges, "m": m,
-                   "allocator": args.allocator, "triangles": T},
+        "config": workload_config(spec, "CPU arm: no device cache to flush", dist.world),
+        "sample_m": m, "sample_triangles": T,
         "cpu_baseline": {"value": round(value, 5), "unit": "GTEPS", "cores": cores, "kind": "oracle",
-                         "sample": f"whole {spec.name} graph per step (sort+CSR+merge count)"},
+                         "sample": f"{what} per step (sort+CSR+merge count), m = {m}"},
         "e2e": {"value": round(value, 5), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
