@@ -41,7 +41,10 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="rmat20",
-                   help="rmat20 | rmat26 | er4096 | batch | rmat<scale> (other R-MAT scales, edge factor 16)")
+                   help="rmat20 | rmat26 | er4096 | batch | serve | unfused | rmat<scale> (other R-MAT scales, edge factor 16)")
+    p.add_argument("--graph", default="rmat20", help="unfused: the graph the two counting paths are compared on")
+    p.add_argument("--unfused-chunk-bytes", type=int, default=0,
+                   help="unfused: bytes one round-2 pass may hold (0: the largest pass)")
     p.add_argument("--batch-graphs", type=int, default=4096)
     p.add_argument("--rate", type=float, default=2000.0, help="serve: mean request arrivals per second")
     p.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
@@ -378,6 +381,86 @@ def cpu_baseline(spec, ds, dd, T_expect):
             "sample": f"{what} (sort+CSR+merge count), m = {m}, {t:.2f} s"}
 
 
+def run_unfused(args, dist: Dist):
+    """The ablation of Algorithm 1's unfused loop: the same graph counted by tc_count_unfused (frontiers written to
+    memory and compacted each round) and by the fused kernel, both timed with CUDA events on one stream."""
+    import torch
+
+    import graphgen
+    import paper_1909_02127_gb300 as tc
+
+    dev = torch.device("cuda", dist.local)
+    torch.cuda.set_device(dev)
+    base = graphgen.config(args.graph)
+    spec = graphgen.GraphSpec(base.kind, base.n, base.num_edges, base.seed + dist.rank, base.scale, base.permute,
+                              base.name)
+    stream = torch.cuda.current_stream()
+    ds, dd = spec.edges(device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+    d_total = torch.zeros(1, dtype=torch.int64, device=dev)
+    g = tc.tc_load_edges(ds, dd, spec.n, stream=stream)
+    tc.tc_build(g, stream)
+    info = tc.tc_graph_get_info(g)
+    T = tc.tc_count(g, stream)
+    stats = None
+    for _ in range(max(1, args.warmup)):
+        T_u, stats = tc.tc_count_unfused(g, args.unfused_chunk_bytes, stream)
+        tc.tc_count_device(g, d_total, stream)
+        if T_u != T:
+            raise RuntimeError(f"unfused count {T_u} != fused {T}")
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    clocks = ClockSampler(dist.local)
+    launches0 = tc.tc_kernel_launches()
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.fill_(k)
+        evs[k][0].record(stream)
+        T_u, _ = tc.tc_count_unfused(g, args.unfused_chunk_bytes, stream)
+        evs[k][1].record(stream)
+        flush.fill_(k + 1)
+        evs[k][2].record(stream)
+        tc.tc_count_device(g, d_total, stream)
+        evs[k][3].record(stream)
+        if T_u != T:
+            raise RuntimeError("unfused count changed in the timed region")
+    torch.cuda.synchronize()
+    clock_info = clocks.stop()
+    dist.barrier()
+    launches = tc.tc_kernel_launches() - launches0
+    if int(d_total.item()) != T:
+        raise RuntimeError("fused count changed in the timed region")
+    tc.tc_free(g)
+    unf_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    fused_ms = [e[2].elapsed_time(e[3]) for e in evs]
+    m = info["num_edges"]
+    units, secs = aggregate(m * args.steps, sum(unf_ms) / 1e3, dist)
+    t_unf = statistics.mean(unf_ms) / 1e3
+    peak, peak_kind = measured_peaks()
+    # round-2 frontier bytes: per slot the column read, the keep-flag write, the scan's read and write of it and
+    # the compaction's read (5 x 4 B)
+    frontier_bytes = 20 * stats["frontier2"]
+    return {
+        "metric": "unfused-loop count GTEPS (Algorithm 1 frontiers materialised) vs the fused kernel",
+        "value": round(units / secs / 1e9, 4), "unit": "GTEPS", "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(statistics.mean(unf_ms), 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32/uint64 (exact integer)", "data": "synthetic",
+        "config": workload_config(spec, "2x L2 buffer written before each timed count", dist.world),
+        "m": m, "triangles": T, "wedges_padded": info["num_wedges"],
+        "unfused": {"ms": round(statistics.mean(unf_ms), 3), **stats,
+                    "chunk_bytes": args.unfused_chunk_bytes},
+        "fused": {"ms": round(statistics.mean(fused_ms), 4), "intermediate_bytes": 0,
+                  "gteps": round(m / (statistics.mean(fused_ms) / 1e3) / 1e9, 4)},
+        "slowdown_unfused_vs_fused": round(statistics.mean(unf_ms) / statistics.mean(fused_ms), 2),
+        "roofline": {"bound": "hbm", "kernel": "unfused loop (all of its kernels)",
+                     "achieved": round(frontier_bytes / t_unf / 1e9, 1), "peak": peak, "peak_kind": peak_kind,
+                     "unit": "GB/s", "frac": round(frontier_bytes / t_unf / 1e9 / peak, 4), "traffic": None,
+                     "algorithmic_bytes": frontier_bytes},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clock_info,
+    }
+
+
 def run_batch(args, dist: Dist):
     import numpy as np
     import torch
@@ -553,7 +636,7 @@ def run_reference(args, dist: Dist):
     import oracle
     if dist.rank != 0:
         return None
-    if args.workload in ("batch", "serve"):
+    if args.workload in ("batch", "serve", "unfused"):
         return {"impl": "reference", "unavailable": "the oracle arm is defined for the single-graph workloads"}
     spec = graphgen.config(args.workload)
     sample, what = cpu_sample(spec, 21)
@@ -599,6 +682,8 @@ def main():
         out = run_batch(args, dist)
     elif args.workload == "serve":
         out = run_serve(args, dist)
+    elif args.workload == "unfused":
+        out = run_unfused(args, dist)
     else:
         out = run_single(args, dist)
     dist.close()

@@ -11,7 +11,8 @@ Parity status: oracle_count is pinned by closed forms, dense trace(A^3)/6 brute 
 (tests/test_oracle.py); oracle_vertex_triangles is pinned by the same closed forms, by the brute-force diagonal
 diag(A^3)/2 and by agreement with oracle_count's per-vertex output; oracle_list_triangles is pinned by the clique
 closed form (every 3-subset listed) and by dense brute force (the right number of distinct triples, each a
-triangle) in tests/test_listing.py.
+triangle) in tests/test_listing.py.  frontiers.py (numpy) gives the frontier sizes of the unfused loop of
+Algorithm 1, pinned by closed forms and loop enumeration in tests/test_unfused.py.
 """
 from __future__ import annotations
 

@@ -65,6 +65,11 @@ class tc_request_result(ctypes.Structure):
                 ("t_built_ns", ctypes.c_int64), ("t_done_ns", ctypes.c_int64)]
 
 
+class tc_unfused_stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in ("candidates", "frontier1", "partials", "frontier2", "matches",
+                                                    "chunks", "peak_bytes", "reserved")]
+
+
 class tc_server_stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in ("submitted", "admitted", "completed", "failed", "launches",
                                                     "max_batch_seen", "budget_bytes", "held_bytes",
@@ -72,7 +77,7 @@ class tc_server_stats(ctypes.Structure):
 
 
 EXPORTED = ["tc_load_edges", "tc_build", "tc_count", "tc_count_device", "tc_count_per_vertex",
-            "tc_count_per_vertex_noalloc", "tc_list_triangles", "tc_count_batch", "tc_server_create", "tc_server_submit",
+            "tc_count_per_vertex_noalloc", "tc_list_triangles", "tc_count_unfused", "tc_count_batch", "tc_server_create", "tc_server_submit",
             "tc_server_poll", "tc_server_get_stats", "tc_server_destroy", "tc_batch_plan_create",
             "tc_batch_plan_run", "tc_batch_plan_free",
             "tc_graph_get_info", "tc_copy_csr", "tc_free", "tc_last_error", "tc_kernel_launches", "tc_set_tuning",
@@ -105,6 +110,8 @@ def load_library(path: str = LIB_PATH):
     lib.tc_count_per_vertex.restype = st
     lib.tc_list_triangles.argtypes = [vp, i64, i64, vp, i64, u64p, u32, vp]
     lib.tc_list_triangles.restype = st
+    lib.tc_count_unfused.argtypes = [vp, u64p, i64, ctypes.POINTER(tc_unfused_stats), vp]
+    lib.tc_count_unfused.restype = st
     lib.tc_count_per_vertex_noalloc.argtypes = [vp, vp, vp, vp]
     lib.tc_count_per_vertex_noalloc.restype = st
     lib.tc_count_batch.argtypes = [ctypes.POINTER(vp), i32, u64p, vp]
@@ -374,6 +381,15 @@ def tc_list_triangles(g: int, first_source: int = 0, num_sources: Optional[int] 
                                  TC_PTR_HOST, _stream_ptr(stream)))
     k = min(int(found.value), int(capacity))
     return out[:k], int(found.value)
+
+
+def tc_count_unfused(g: int, max_chunk_bytes: int = 0, stream=None):
+    """T by the unfused verification loop (materialised frontiers), and its frontier sizes as a dict."""
+    lib = load_library()
+    T = ctypes.c_uint64(0)
+    st = tc_unfused_stats()
+    _check(lib.tc_count_unfused(g, ctypes.byref(T), int(max_chunk_bytes), ctypes.byref(st), _stream_ptr(stream)))
+    return int(T.value), {name: int(getattr(st, name)) for name, _ in tc_unfused_stats._fields_ if name != "reserved"}
 
 
 def tc_count_batch(gs: Sequence[int], stream=None) -> np.ndarray:
