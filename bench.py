@@ -41,7 +41,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="rmat20",
-                   help="rmat20 | rmat26 | er4096 | batch | serve | unfused | rmat<scale> (other R-MAT scales, edge factor 16)")
+                   help="rmat20 | rmat26 | er4096 | batch | serve | unfused | prune | rmat<scale> (R-MAT, edge factor 16)")
     p.add_argument("--graph", default="rmat20", help="unfused: the graph the two counting paths are compared on")
     p.add_argument("--unfused-chunk-bytes", type=int, default=0,
                    help="unfused: bytes one round-2 pass may hold (0: the largest pass)")
@@ -528,6 +528,86 @@ def run_batch(args, dist: Dist):
     }
 
 
+def run_prune(args, dist: Dist):
+    """Does the NE filter to a fixpoint (2-core peeling) pay for itself on the batch mix?  The same graphs are
+    loaded and built plainly and pruned, and counted with one batch plan each; build and count are timed apart."""
+    import numpy as np
+    import torch
+
+    import graphgen
+    import paper_1909_02127_gb300 as tc
+
+    dev = torch.device("cuda", dist.local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    specs = graphgen.batch_mix(args.batch_graphs, graphgen.BASE_SEED + graphgen.BATCH_SEED_OFFSET
+                               + dist.rank * 1000003)
+    edges = [sp.edges(device=dev) for sp in specs]
+    torch.cuda.synchronize()
+
+    def build_all(pruned):
+        hs, removed, kept = [], 0, 0
+        t0 = time.perf_counter()
+        for sp, (s, d) in zip(specs, edges):
+            h = tc.tc_load_edges(s, d, sp.n, stream=stream)
+            if pruned:
+                removed += tc.tc_build_pruned(h, 0, stream)["edges_removed"]
+            else:
+                tc.tc_build(h, stream)
+            hs.append(h)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        kept = sum(tc.tc_graph_get_info(h)["num_edges"] for h in hs)
+        return hs, t, removed, kept
+
+    def count_all(hs):
+        plan = tc.tc_batch_plan_create(hs, stream)
+        got = np.zeros(len(hs), dtype=np.uint64)
+        for _ in range(args.warmup):
+            tc.tc_batch_plan_run(plan, len(hs), stream, got)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            tc.tc_batch_plan_run(plan, len(hs), stream, got)
+        torch.cuda.synchronize()
+        t = (time.perf_counter() - t0) / args.steps
+        tc.tc_batch_plan_free(plan)
+        return got.copy(), t
+
+    out = {}
+    counts = {}
+    clocks = ClockSampler(dist.local)
+    dist.barrier()
+    clocks.start()
+    l0 = tc.tc_kernel_launches()
+    for name, pruned in (("plain", False), ("pruned", True)):
+        for h in build_all(pruned)[0]:  # warm-up build (pool growth, first-call setup)
+            tc.tc_free(h)
+        hs, t_build, removed, kept = build_all(pruned)
+        counts[name], t_count = count_all(hs)
+        for h in hs:
+            tc.tc_free(h)
+        out[name] = {"build_s": round(t_build, 4), "count_ms": round(t_count * 1e3, 3), "edges_kept": kept,
+                     "edges_removed": removed}
+    launches = tc.tc_kernel_launches() - l0
+    clock_info = clocks.stop()
+    if not np.array_equal(counts["plain"], counts["pruned"]):
+        raise RuntimeError("pruned counts differ")
+    total = {k: v["build_s"] + v["count_ms"] / 1e3 for k, v in out.items()}
+    units, secs = aggregate(len(specs), total["pruned"], dist)
+    return {
+        "metric": "batch mix: build + one batched count, with the NE filter to a fixpoint (2-core) vs without",
+        "value": round(units / secs, 2), "unit": "graphs/s", "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total["pruned"] * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32/uint64 (exact integer)", "data": "synthetic",
+        "config": {"workload": f"batch of {len(specs)} graphs (ER/R-MAT mix, n log-uniform [64, 65536])",
+                   "parallelism": f"replicas x{dist.world}"},
+        **out, "pays": total["pruned"] < total["plain"],
+        "plain_graphs_per_s": round(len(specs) / total["plain"], 2),
+        "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clock_info,
+    }
+
+
 def run_serve(args, dist: Dist):
     """Replay one Poisson arrival trace against the serving loop twice: continuous batching, then one graph per
     launch.  Every result is checked against the graph's solo count."""
@@ -636,7 +716,7 @@ def run_reference(args, dist: Dist):
     import oracle
     if dist.rank != 0:
         return None
-    if args.workload in ("batch", "serve", "unfused"):
+    if args.workload in ("batch", "serve", "unfused", "prune"):
         return {"impl": "reference", "unavailable": "the oracle arm is defined for the single-graph workloads"}
     spec = graphgen.config(args.workload)
     sample, what = cpu_sample(spec, 21)
@@ -684,6 +764,8 @@ def main():
         out = run_serve(args, dist)
     elif args.workload == "unfused":
         out = run_unfused(args, dist)
+    elif args.workload == "prune":
+        out = run_prune(args, dist)
     else:
         out = run_single(args, dist)
     dist.close()

@@ -6,8 +6,8 @@
  * all-source breadth-first traversal (Sec. III, Algorithm 1): every source u advances to its neighbours v, every v
  * advances to its neighbours w, and the 2-path u-v-w is kept only when the non-tree (closing) edge u-w exists.  A
  * total order on the vertices — the unique mapping order of Sec. III-A and the duplicate avoidance of Sec. III-C —
- * makes each triangle appear exactly once; this library orders vertices by (degree, id) and traverses only edges
- * that go up in that order.  The answer is the number of matches |M|/|Q| (Algorithm 1, result line).
+ * makes each triangle appear exactly once; this library orders vertices by (number of input pairs at the vertex,
+ * id) and traverses only edges that go up in that order.  The answer is the number of matches |M|/|Q| (Algorithm 1, result line).
  *
  * Conventions for every entry point:
  *  - Status: each call returns a tc_status; nothing aborts the process.  tc_last_error() gives a message for the
@@ -67,7 +67,7 @@ typedef struct tc_graph_info {
   int64_t num_input_pairs; /* pairs given to tc_load_edges */
   int64_t num_edges;       /* m: distinct undirected edges after dropping self-loops and repeats */
   int64_t csr_entries;     /* column entries of the oriented CSR, rows padded to a multiple of 4 */
-  int64_t max_out_degree;  /* largest d+(u) in the (degree, id) orientation */
+  int64_t max_out_degree;  /* largest d+(u) in the orientation of tc_build */
   int64_t num_wedges;      /* W = sum over oriented edges u->v of d+(v): the candidate 2-paths u->v->w */
   int64_t active_sources;  /* sources with d+(u) >= 2 and at least one candidate 2-path */
   int64_t bin_warp;        /* sources handled one warp each */
@@ -95,13 +95,36 @@ TC_API tc_status tc_load_edges(const int32_t* src, const int32_t* dst, int64_t n
 
 /*
  * tc_build — the data structure and filtering steps before the traversal (Sec. III-B: CSR storage; Algorithm 1,
- * filtering: NE = degree, Sec. III-A; k-look-ahead pruning, Sec. III-C).  On the device: sort and de-duplicate the
- * edges, compute degrees, orient each edge from lower to higher (degree, id) (the unique mapping order of Sec.
- * III-A), build the oriented CSR (int64 row offsets, int32 sorted column ids) and bin the sources u by their
+ * filtering: NE = degree, Sec. III-A; k-look-ahead pruning, Sec. III-C).  On the device: rank the vertices by
+ * (number of input pairs at the vertex, self-loops excluded and repeats included; then id) — a total order that
+ * follows the degree (the unique mapping order of Sec. III-A; any total order counts each triangle once, Sec.
+ * III-C) — relabel every pair by rank so that it points up the order, sort and de-duplicate the pairs, build the
+ * oriented CSR (int64 row offsets, int32 sorted column ids of ranks) and bin the sources u by their
  * candidate-2-path work.  Sources with d+(u) < 2 are dropped (they cannot be the first vertex of a triangle).
  * Frees the edge buffers.  Idempotent: a second call returns TC_OK.  Synchronises `stream`.
  */
 TC_API tc_status tc_build(tc_graph* g, void* stream);
+
+/* What tc_build_pruned removed. */
+typedef struct tc_prune_stats {
+  int64_t rounds;           /* rounds that removed at least one edge */
+  int64_t edges_removed;    /* distinct undirected edges removed */
+  int64_t vertices_removed; /* vertices that had an edge before pruning and have none after */
+  int64_t reserved;
+} tc_prune_stats;
+
+/*
+ * tc_build_pruned — tc_build with the NE filter applied until it settles (Sec. III-A: NE is the degree, and it is
+ * updated after each filtering).  After the repeats are removed, each round drops every edge with an endpoint of
+ * degree below 2 in the current graph (such a vertex lies in no triangle, so neither does the edge), until a round
+ * removes nothing (the 2-core) or max_rounds rounds ran.  Counts, per-vertex counts and listings are unchanged;
+ * tc_graph_get_info describes the pruned graph (num_edges = edges kept).
+ *   max_rounds  >= 1: at most that many rounds; 0: until a round removes nothing, at most 65536 rounds (a long
+ *               path loses only its two end edges per round); negative: TC_ERR_INVALID_ARG.
+ *   stats       host pointer or NULL; zeroed when the graph was already built (nothing is re-run).
+ * Each round waits for the GPU once.  Errors as tc_build.
+ */
+TC_API tc_status tc_build_pruned(tc_graph* g, int32_t max_rounds, tc_prune_stats* stats, void* stream);
 
 /*
  * tc_count — the verification loop of Algorithm 1 for Q = K3, fused: for every source u, every v in N+(u) and
@@ -278,9 +301,9 @@ TC_API tc_status tc_graph_get_info(const tc_graph* g, tc_graph_info* info);
 
 /*
  * tc_copy_csr — copy the oriented CSR of a built graph to host memory, for inspection and tests (Sec. III-B: the
- * graph is stored in CSR).  The CSR is in rank space: vertex r is the r-th vertex in the (degree, id) order, and
- * row r holds N+(r), the ranks above r adjacent to it, ascending.  Each row starts at a multiple of 4 entries and
- * is padded to a multiple of 4 with the value n.
+ * graph is stored in CSR).  The CSR is in rank space: vertex r is the r-th vertex in the (input-pair count, id)
+ * order, and row r holds N+(r), the ranks above r adjacent to it, ascending.  Each row starts at a multiple of 4
+ * entries and is padded to a multiple of 4 with the value n.
  *   offsets  n+1 int64 row offsets (host).
  *   cols     csr_entries int32 column entries (host; see tc_graph_info.csr_entries), or NULL.
  *   perm     n int32 (host), or NULL: perm[r] = the original id of rank r.

@@ -12,7 +12,8 @@ Parity status: oracle_count is pinned by closed forms, dense trace(A^3)/6 brute 
 diag(A^3)/2 and by agreement with oracle_count's per-vertex output; oracle_list_triangles is pinned by the clique
 closed form (every 3-subset listed) and by dense brute force (the right number of distinct triples, each a
 triangle) in tests/test_listing.py.  frontiers.py (numpy) gives the frontier sizes of the unfused loop of
-Algorithm 1, pinned by closed forms and loop enumeration in tests/test_unfused.py.
+Algorithm 1, pinned by closed forms and loop enumeration in tests/test_unfused.py; prune.py (numpy) is the NE
+filter applied until it settles (the 2-core), pinned by networkx's k_core and closed forms in tests/test_prune.py.
 """
 from __future__ import annotations
 

@@ -65,6 +65,10 @@ class tc_request_result(ctypes.Structure):
                 ("t_built_ns", ctypes.c_int64), ("t_done_ns", ctypes.c_int64)]
 
 
+class tc_prune_stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in ("rounds", "edges_removed", "vertices_removed", "reserved")]
+
+
 class tc_unfused_stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in ("candidates", "frontier1", "partials", "frontier2", "matches",
                                                     "chunks", "peak_bytes", "reserved")]
@@ -76,7 +80,7 @@ class tc_server_stats(ctypes.Structure):
                                                     "peak_held_bytes", "pending")]
 
 
-EXPORTED = ["tc_load_edges", "tc_build", "tc_count", "tc_count_device", "tc_count_per_vertex",
+EXPORTED = ["tc_load_edges", "tc_build", "tc_build_pruned", "tc_count", "tc_count_device", "tc_count_per_vertex",
             "tc_count_per_vertex_noalloc", "tc_list_triangles", "tc_count_unfused", "tc_count_batch", "tc_server_create", "tc_server_submit",
             "tc_server_poll", "tc_server_get_stats", "tc_server_destroy", "tc_batch_plan_create",
             "tc_batch_plan_run", "tc_batch_plan_free",
@@ -102,6 +106,8 @@ def load_library(path: str = LIB_PATH):
     lib.tc_load_edges.restype = st
     lib.tc_build.argtypes = [vp, vp]
     lib.tc_build.restype = st
+    lib.tc_build_pruned.argtypes = [vp, i32, ctypes.POINTER(tc_prune_stats), vp]
+    lib.tc_build_pruned.restype = st
     lib.tc_count.argtypes = [vp, u64p, vp]
     lib.tc_count.restype = st
     lib.tc_count_device.argtypes = [vp, vp, vp]
@@ -321,6 +327,14 @@ def tc_load_edges(src, dst, num_vertices: int, stream=None, allocator=None) -> i
 
 def tc_build(g: int, stream=None) -> None:
     _check(load_library().tc_build(g, _stream_ptr(stream)))
+
+
+def tc_build_pruned(g: int, max_rounds: int = 0, stream=None) -> dict:
+    """tc_build on the 2-core (max_rounds = 0) or after max_rounds rounds of the NE filter; returns what was
+    removed."""
+    st = tc_prune_stats()
+    _check(load_library().tc_build_pruned(g, int(max_rounds), ctypes.byref(st), _stream_ptr(stream)))
+    return {name: int(getattr(st, name)) for name, _ in tc_prune_stats._fields_ if name != "reserved"}
 
 
 def tc_count(g: int, stream=None) -> int:

@@ -17,6 +17,7 @@
 // relabelled before the one sort that also removes the repeats.  Relabelling by rank gives the kernel two things:
 // hubs get the highest ids, so a bitmap over the top ids answers most closing-edge tests; and hub rows, which are
 // re-read by many sources, sit together in memory.
+#include "tc_build.cuh"
 #include "tc_internal.cuh"
 #include "tc_prims.cuh"
 
@@ -157,8 +158,44 @@ __global__ void __launch_bounds__(kUThreads) k_unique_scatter(const uint64_t* __
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *m = (int64_t)part[blockIdx.x] + tot;
 }
 
+// ---- NE filter to a fixpoint (2-core peeling) ------------------------------------------------------------------
+// One round: the degree of every vertex over the live distinct edges, then every edge with an endpoint of degree
+// below 2 is replaced by the sentinel (a vertex of degree 1 is in no triangle, so neither is its edge).
+__global__ void k_peel_degree(const uint64_t* __restrict__ keys, int64_t m, int B, uint64_t sentinel,
+                              int32_t* __restrict__ deg) {
+  const uint64_t mask = (1ull << B) - 1ull;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < m; base += stride) {  // warp-uniform trip count
+    const int64_t i = base + threadIdx.x;
+    const uint64_t k = i < m ? keys[i] : sentinel;
+    const bool live = k != sentinel;
+    agg_inc(deg, (uint32_t)(k >> B), live);
+    agg_inc(deg, (uint32_t)(k & mask), live);
+  }
+}
+
+__global__ void k_peel_kill(uint64_t* __restrict__ keys, int64_t m, int B, uint64_t sentinel,
+                            const int32_t* __restrict__ deg, unsigned long long* __restrict__ killed) {
+  const uint64_t mask = (1ull << B) - 1ull;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = keys[i];
+    const bool kill = k != sentinel && (deg[k >> B] < 2 || deg[k & mask] < 2);
+    if (kill) keys[i] = sentinel;
+    const unsigned b = __ballot_sync(__activemask(), kill);
+    if (kill && (threadIdx.x & 31) == __ffs(b) - 1) atomicAdd(killed, (unsigned long long)__popc(b));
+  }
+}
+
+__global__ void k_count_nonzero(const int32_t* __restrict__ deg, int64_t n, unsigned long long* __restrict__ nz) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+    const bool on = deg[x] > 0;
+    const unsigned b = __ballot_sync(__activemask(), on);
+    if (on && (threadIdx.x & 31) == __ffs(b) - 1) atomicAdd(nz, (unsigned long long)__popc(b));
+  }
+}
+
 // ---- rank, relabel --------------------------------------------------------------------------------------------
-// (deg << B) | id, in id order: a stable sort on the degree bits alone gives the (degree, id) order.
+// (count << B) | id, in id order: a stable sort on the count bits alone gives the (count, id) order.
 __global__ void k_rank_keys(const int32_t* __restrict__ deg, int64_t n, int B, uint64_t* __restrict__ rkeys,
                             int* __restrict__ maxdeg) {
   int mx = 0;
@@ -316,7 +353,87 @@ tc_status unpermute_counts(const tc_graph* g, const uint64_t* by_rank, uint64_t*
   return TC_OK;
 }
 
-tc_status build_graph(tc_graph* g, cudaStream_t s) {
+// Peels the m distinct keys in *ukeys to the 2-core (at most max_rounds rounds; <= 0: until a round removes
+// nothing, capped at kPeelMaxRounds) and compacts them; *m becomes the number left.
+constexpr int32_t kPeelMaxRounds = 1 << 16;
+
+tc_status peel_keys(const Allocator& a, Buf& ukeys, int64_t* m, int64_t n, int B, uint64_t sentinel,
+                    int32_t max_rounds, tc_prune_stats* ps, cudaStream_t s) {
+  const int32_t limit = max_rounds > 0 ? max_rounds : kPeelMaxRounds;
+  Buf deg, words, out, part;
+  tc_status st = TC_OK;
+  unsigned long long hw[2] = {0, 0};
+  int64_t nz_first = 0, nz_last = 0;
+  int32_t rounds = 0;
+  auto launched = [&](const char* what) {
+    note_launch();
+    return cuda_status(cudaGetLastError(), what);
+  };
+  do {
+    if ((st = buf_alloc(a, deg, (size_t)n * 4, s))) break;
+    if ((st = buf_alloc(a, words, 16, s))) break;
+    // pass: degrees over the live keys and how many vertices have one ([1]); with kill, the edges removed ([0])
+    auto pass = [&](bool kill) -> tc_status {
+      TC_CUDA(cudaMemsetAsync(deg.p, 0, (size_t)n * 4, s));
+      TC_CUDA(cudaMemsetAsync(words.p, 0, 16, s));
+      k_peel_degree<<<grid_for(*m, 256), 256, 0, s>>>(ukeys.as<uint64_t>(), *m, B, sentinel, deg.as<int32_t>());
+      TC_TRY(launched("k_peel_degree"));
+      k_count_nonzero<<<grid_for(n, 256), 256, 0, s>>>(deg.as<int32_t>(), n, words.as<unsigned long long>() + 1);
+      TC_TRY(launched("k_count_nonzero"));
+      if (kill) {
+        k_peel_kill<<<grid_for(*m, 256), 256, 0, s>>>(ukeys.as<uint64_t>(), *m, B, sentinel, deg.as<int32_t>(),
+                                                      words.as<unsigned long long>());
+        TC_TRY(launched("k_peel_kill"));
+      }
+      TC_CUDA(cudaMemcpyAsync(hw, words.p, 16, cudaMemcpyDeviceToHost, s));
+      TC_CUDA(cudaStreamSynchronize(s));
+      return TC_OK;
+    };
+    bool removed = true;
+    int32_t passes = 0;
+    while (removed && passes < limit) {
+      if ((st = pass(true))) break;
+      if (passes == 0) nz_first = (int64_t)hw[1];
+      nz_last = (int64_t)hw[1];  // vertices with an edge at the start of this round
+      ++passes;
+      removed = hw[0] > 0;
+    }
+    if (st) break;
+    rounds = removed ? passes : passes - 1;  // rounds that removed something
+    if (removed) {  // stopped by the limit: the degrees of what is left
+      if ((st = pass(false))) break;
+      nz_last = (int64_t)hw[1];
+    }
+    // compaction of the live keys (they stay sorted and distinct)
+    const int64_t tiles = (*m + kUTile - 1) / kUTile;
+    if ((st = buf_alloc(a, out, (size_t)*m * 8, s))) break;
+    if ((st = buf_alloc(a, part, (size_t)tiles * 4, s))) break;
+    k_unique_count<<<(unsigned)tiles, kUThreads, 0, s>>>(ukeys.as<uint64_t>(), *m, sentinel, part.as<uint32_t>());
+    if ((st = launched("k_unique_count"))) break;
+    if ((st = exclusive_scan_u32(a, part.as<uint32_t>(), tiles, s))) break;
+    k_unique_scatter<<<(unsigned)tiles, kUThreads, 0, s>>>(ukeys.as<uint64_t>(), *m, sentinel, part.as<uint32_t>(),
+                                                            out.as<uint64_t>(), words.as<int64_t>());
+    if ((st = launched("k_unique_scatter"))) break;
+    int64_t left = 0;
+    if ((st = cuda_status(cudaMemcpyAsync(&left, words.p, 8, cudaMemcpyDeviceToHost, s), "copy kept"))) break;
+    if ((st = cuda_status(cudaStreamSynchronize(s), "sync kept"))) break;
+    if (ps) {
+      ps->rounds = rounds;
+      ps->edges_removed = *m - left;
+      ps->vertices_removed = nz_first - nz_last;
+    }
+    *m = left;
+    buf_release(a, ukeys, s);
+    ukeys = out;
+    out = Buf{};
+  } while (0);
+  for (Buf* b : {&deg, &words, &out, &part}) buf_release(a, *b, s);
+  return st;
+}
+
+tc_status build_graph(tc_graph* g, cudaStream_t s) { return build_graph_pruned(g, -1, nullptr, s); }
+
+tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* ps, cudaStream_t s) {
   const Allocator& a = g->alloc;
   const int B = g->key_bits;
   const int64_t M = g->num_pairs;
@@ -392,6 +509,7 @@ tc_status build_graph(tc_graph* g, cudaStream_t s) {
       buf_release(a, g->keys, s);
     }
     buf_release(a, rank, s);
+    if (peel_rounds >= 0 && m > 0 && (st = peel_keys(a, ukeys, &m, n, B, sentinel, peel_rounds, ps, s))) break;
     g->m = m;
 
     // ---- offsets: unpadded starts (ustart) and padded offsets (off) ----

@@ -8,6 +8,7 @@
 #include <new>
 #include <string>
 
+#include "tc_build.cuh"
 #include "tc_internal.cuh"
 
 namespace tc {
@@ -311,6 +312,25 @@ TC_API tc_status tc_build(tc_graph* g, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   g->last_stream = s;
   tc_status st = build_graph(g, s);
+  if (st != TC_OK) return st;
+  g->built = true;
+  return TC_OK;
+}
+
+TC_API tc_status tc_build_pruned(tc_graph* g, int32_t max_rounds, tc_prune_stats* stats, void* stream) {
+  if (stats) memset(stats, 0, sizeof(*stats));
+  if (!g) {
+    set_error("tc_build_pruned: graph handle is NULL");
+    return TC_ERR_INVALID_ARG;
+  }
+  if (max_rounds < 0) {
+    set_error("tc_build_pruned: max_rounds is negative");
+    return TC_ERR_INVALID_ARG;
+  }
+  if (g->built) return TC_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  g->last_stream = s;
+  tc_status st = build_graph_pruned(g, max_rounds, stats, s);
   if (st != TC_OK) return st;
   g->built = true;
   return TC_OK;
