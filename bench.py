@@ -312,8 +312,11 @@ def run_single(args, dist: Dist):
     b_alg = algorithmic_bytes(info, grid)
     mean_count_s = statistics.mean(count_ms) / 1e3
     achieved = b_alg / mean_count_s / 1e9
-    traffic = profiled_traffic(args.workload)
-    roofline = {"bound": "hbm", "kernel": "k_count", "achieved": round(achieved, 1), "peak": peak,
+    ratio = tc.tc_get_isect_max_wedges_milli()
+    isect = ratio > 0 and m > 0 and 1000 * info["num_wedges"] <= ratio * m  # the kernel tc_count picks
+    traffic = None if isect else profiled_traffic(args.workload)
+    roofline = {"bound": "hbm", "kernel": "k_count_isect" if isect else "k_count", "achieved": round(achieved, 1),
+                "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": traffic, "algorithmic_bytes": b_alg}
 

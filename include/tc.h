@@ -142,6 +142,15 @@ TC_API tc_status tc_count(tc_graph* g, uint64_t* out_total, void* stream);
 TC_API tc_status tc_count_device(tc_graph* g, uint64_t* d_total, void* stream);
 
 /*
+ * tc_count_intersect — the same count by the other family of GPU triangle counters: segmented intersection
+ * (Sec. II-B: the operator that intersects the neighbour lists of each pair from two frontiers).  Every oriented
+ * edge u -> v of the built graph contributes |N+(u) ∩ N+(v)|, one lane per edge, by galloping search over the
+ * shorter list.  *out_total receives T (equal to tc_count).  Requires tc_build (else TC_ERR_STATE).  Blocks until
+ * *out_total (host memory) is valid.
+ */
+TC_API tc_status tc_count_intersect(tc_graph* g, uint64_t* out_total, void* stream);
+
+/*
  * tc_count_per_vertex — as tc_count, and also t(x), the number of triangles containing x, for every x in [0, n)
  * (the per-vertex view of the matches M of Algorithm 1).
  *   per_vertex  n uint64 entries, host or device memory as `flags` says (TC_PTR_HOST or TC_PTR_DEVICE);
@@ -318,7 +327,8 @@ TC_API void tc_free(tc_graph* g);
  * Tuning (no counterpart in the paper).  The counting kernel gives a source a whole thread block when its work
  * w(u) (padded second-hop entries) exceeds a threshold, and one warp otherwise; the best threshold depends on the
  * graph's size.  The table maps size classes (by distinct edges m) to thresholds and is consulted by tc_build.
- * Counts never depend on it.  Process-wide; thread-safe.
+ * It also picks, per graph, between the fused traversal and segmented intersection for tc_count.  Counts never
+ * depend on it.  Process-wide; thread-safe.
  */
 #define TC_TUNING_MAX_CLASSES 16
 typedef struct tc_tuning {
@@ -331,6 +341,10 @@ typedef struct tc_tuning {
   int64_t class_max_edges[TC_TUNING_MAX_CLASSES];      /* ascending; class i holds graphs with m <= class_max_edges[i]
                                                           (the last class also holds every larger graph) */
   int64_t block_min_work[TC_TUNING_MAX_CLASSES];       /* threshold for class i, >= 0 */
+  int64_t isect_max_wedges_milli;                      /* tc_count and tc_count_device count a graph with the
+                                                          segmented-intersection kernel (tc_count_intersect) when
+                                                          1000 * num_wedges <= this * num_edges, i.e. when it has
+                                                          few candidate 2-paths per edge; 0: never.  >= 0 */
 } tc_tuning;
 
 /* tc_set_tuning — replace the table (TC_ERR_INVALID_ARG if malformed).  Applies to graphs built afterwards. */

@@ -50,7 +50,8 @@ class tc_tuning(ctypes.Structure):
     _fields_ = [("num_classes", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("batch_warp_max_edges", ctypes.c_int64),
                 ("class_max_edges", ctypes.c_int64 * TC_TUNING_MAX_CLASSES),
-                ("block_min_work", ctypes.c_int64 * TC_TUNING_MAX_CLASSES)]
+                ("block_min_work", ctypes.c_int64 * TC_TUNING_MAX_CLASSES),
+                ("isect_max_wedges_milli", ctypes.c_int64)]
 
 
 class tc_server_config(ctypes.Structure):
@@ -81,7 +82,7 @@ class tc_server_stats(ctypes.Structure):
 
 
 EXPORTED = ["tc_load_edges", "tc_build", "tc_build_pruned", "tc_count", "tc_count_device", "tc_count_per_vertex",
-            "tc_count_per_vertex_noalloc", "tc_list_triangles", "tc_count_unfused", "tc_count_batch", "tc_server_create", "tc_server_submit",
+            "tc_count_per_vertex_noalloc", "tc_list_triangles", "tc_count_unfused", "tc_count_intersect", "tc_count_batch", "tc_server_create", "tc_server_submit",
             "tc_server_poll", "tc_server_get_stats", "tc_server_destroy", "tc_batch_plan_create",
             "tc_batch_plan_run", "tc_batch_plan_free",
             "tc_graph_get_info", "tc_copy_csr", "tc_free", "tc_last_error", "tc_kernel_launches", "tc_set_tuning",
@@ -118,6 +119,8 @@ def load_library(path: str = LIB_PATH):
     lib.tc_list_triangles.restype = st
     lib.tc_count_unfused.argtypes = [vp, u64p, i64, ctypes.POINTER(tc_unfused_stats), vp]
     lib.tc_count_unfused.restype = st
+    lib.tc_count_intersect.argtypes = [vp, u64p, vp]
+    lib.tc_count_intersect.restype = st
     lib.tc_count_per_vertex_noalloc.argtypes = [vp, vp, vp, vp]
     lib.tc_count_per_vertex_noalloc.restype = st
     lib.tc_count_batch.argtypes = [ctypes.POINTER(vp), i32, u64p, vp]
@@ -174,32 +177,37 @@ def _apply_tuning_file(lib, path: str = TUNING_FILE) -> bool:
         props = torch.cuda.get_device_properties(torch.cuda.current_device())
         if data.get("device") != props.name or int(data.get("sms", -1)) != props.multi_processor_count:
             return False
-        t = _tuning_struct(data["classes"], data.get("batch_warp_max_edges", 1 << 25))
+        t = _tuning_struct(data["classes"], data.get("batch_warp_max_edges", 1 << 25),
+                           data.get("isect_max_wedges_milli", 0))
         return lib.tc_set_tuning(ctypes.byref(t)) == TC_OK
     except Exception:
         return False
 
 
-def _tuning_struct(classes, batch_warp_max_edges: int = 1 << 25) -> "tc_tuning":
+def _tuning_struct(classes, batch_warp_max_edges: int = 1 << 25, isect_max_wedges_milli: int = 0) -> "tc_tuning":
     t = tc_tuning()
     t.num_classes = len(classes)
     t.batch_warp_max_edges = int(batch_warp_max_edges)
+    t.isect_max_wedges_milli = int(isect_max_wedges_milli)
     for i, (max_edges, work) in enumerate(classes):
         t.class_max_edges[i] = int(max_edges)
         t.block_min_work[i] = int(work)
     return t
 
 
-def tc_set_tuning(classes, batch_warp_max_edges: Optional[int] = None) -> None:
-    """classes: [(max_edges, block_min_work), ...] with ascending max_edges; batch_warp_max_edges: keep the
-    current value if None."""
+def tc_set_tuning(classes, batch_warp_max_edges: Optional[int] = None,
+                  isect_max_wedges_milli: Optional[int] = None) -> None:
+    """classes: [(max_edges, block_min_work), ...] with ascending max_edges; batch_warp_max_edges and
+    isect_max_wedges_milli: keep the current values if None."""
     if not 1 <= len(classes) <= TC_TUNING_MAX_CLASSES:
         raise ValueError("1..16 classes")
+    cur = tc_tuning()
+    _check(load_library().tc_get_tuning(ctypes.byref(cur)))
     if batch_warp_max_edges is None:
-        cur = tc_tuning()
-        _check(load_library().tc_get_tuning(ctypes.byref(cur)))
         batch_warp_max_edges = cur.batch_warp_max_edges
-    t = _tuning_struct(classes, batch_warp_max_edges)
+    if isect_max_wedges_milli is None:
+        isect_max_wedges_milli = cur.isect_max_wedges_milli
+    t = _tuning_struct(classes, batch_warp_max_edges, isect_max_wedges_milli)
     _check(load_library().tc_set_tuning(ctypes.byref(t)))
 
 
@@ -207,6 +215,12 @@ def tc_get_tuning():
     t = tc_tuning()
     _check(load_library().tc_get_tuning(ctypes.byref(t)))
     return [(int(t.class_max_edges[i]), int(t.block_min_work[i])) for i in range(t.num_classes)]
+
+
+def tc_get_isect_max_wedges_milli() -> int:
+    t = tc_tuning()
+    _check(load_library().tc_get_tuning(ctypes.byref(t)))
+    return int(t.isect_max_wedges_milli)
 
 
 def tc_get_batch_warp_max_edges() -> int:
@@ -395,6 +409,13 @@ def tc_list_triangles(g: int, first_source: int = 0, num_sources: Optional[int] 
                                  TC_PTR_HOST, _stream_ptr(stream)))
     k = min(int(found.value), int(capacity))
     return out[:k], int(found.value)
+
+
+def tc_count_intersect(g: int, stream=None) -> int:
+    """T by segmented intersection (one lane per oriented edge)."""
+    out = ctypes.c_uint64(0)
+    _check(load_library().tc_count_intersect(g, ctypes.byref(out), _stream_ptr(stream)))
+    return int(out.value)
 
 
 def tc_count_unfused(g: int, max_chunk_bytes: int = 0, stream=None):

@@ -10,6 +10,7 @@
 
 #include "tc_build.cuh"
 #include "tc_internal.cuh"
+#include "tc_isect.cuh"
 
 namespace tc {
 
@@ -39,6 +40,17 @@ tc_tuning g_tuning = [] {
 int64_t batch_warp_max_edges() {
   std::lock_guard<std::mutex> lk(g_tuning_mutex);
   return g_tuning.batch_warp_max_edges;
+}
+
+// The per-graph choice of counting kernel: segmented intersection for graphs with few candidate 2-paths per edge.
+bool use_intersection(const tc_graph* g) {
+  int64_t r;
+  {
+    std::lock_guard<std::mutex> lk(g_tuning_mutex);
+    r = g_tuning.isect_max_wedges_milli;
+  }
+  if (r <= 0 || g->m <= 0) return false;
+  return (long double)g->wedges * 1000.0L <= (long double)r * (long double)g->m;
 }
 
 int64_t block_min_work_for(int64_t m) {
@@ -173,6 +185,10 @@ TC_API const char* tc_last_error(void) { return g_last_error.c_str(); }
 TC_API tc_status tc_set_tuning(const tc_tuning* t) {
   if (!t || t->num_classes < 1 || t->num_classes > TC_TUNING_MAX_CLASSES) {
     set_error("tc_set_tuning: num_classes must be in 1..TC_TUNING_MAX_CLASSES");
+    return TC_ERR_INVALID_ARG;
+  }
+  if (t->isect_max_wedges_milli < 0) {
+    set_error("tc_set_tuning: isect_max_wedges_milli must be >= 0");
     return TC_ERR_INVALID_ARG;
   }
   for (int i = 0; i < t->num_classes; ++i) {
@@ -336,6 +352,22 @@ TC_API tc_status tc_build_pruned(tc_graph* g, int32_t max_rounds, tc_prune_stats
   return TC_OK;
 }
 
+TC_API tc_status tc_count_intersect(tc_graph* g, uint64_t* out_total, void* stream) {
+  TC_TRY(check_built(g));
+  if (!out_total) {
+    set_error("tc_count_intersect: out_total is NULL");
+    return TC_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  g->last_stream = s;
+  uint64_t* d_total = g->acc.as<uint64_t>();
+  TC_TRY(launch_count_isect(g, d_total, reinterpret_cast<uint32_t*>(d_total + 1), s));
+  TC_CUDA(cudaMemcpyAsync(g->host_total, d_total, 8, cudaMemcpyDeviceToHost, s));
+  TC_CUDA(cudaStreamSynchronize(s));
+  *out_total = *g->host_total;
+  return TC_OK;
+}
+
 TC_API tc_status tc_count_device(tc_graph* g, uint64_t* d_total, void* stream) {
   TC_TRY(check_built(g));
   if (!d_total) {
@@ -344,7 +376,9 @@ TC_API tc_status tc_count_device(tc_graph* g, uint64_t* d_total, void* stream) {
   }
   cudaStream_t s = (cudaStream_t)stream;
   g->last_stream = s;
-  return launch_count(g, d_total, nullptr, reinterpret_cast<uint32_t*>(g->acc.as<uint64_t>() + 1), s);
+  uint32_t* cursor = reinterpret_cast<uint32_t*>(g->acc.as<uint64_t>() + 1);
+  if (use_intersection(g)) return launch_count_isect(g, d_total, cursor, s);
+  return launch_count(g, d_total, nullptr, cursor, s);
 }
 
 TC_API tc_status tc_count(tc_graph* g, uint64_t* out_total, void* stream) {
@@ -356,7 +390,11 @@ TC_API tc_status tc_count(tc_graph* g, uint64_t* out_total, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   g->last_stream = s;
   uint64_t* d_total = g->acc.as<uint64_t>();
-  TC_TRY(launch_count(g, d_total, nullptr, reinterpret_cast<uint32_t*>(d_total + 1), s));
+  uint32_t* cursor = reinterpret_cast<uint32_t*>(d_total + 1);
+  if (use_intersection(g))
+    TC_TRY(launch_count_isect(g, d_total, cursor, s));
+  else
+    TC_TRY(launch_count(g, d_total, nullptr, cursor, s));
   TC_CUDA(cudaMemcpyAsync(g->host_total, d_total, 8, cudaMemcpyDeviceToHost, s));
   TC_CUDA(cudaStreamSynchronize(s));
   *out_total = *g->host_total;

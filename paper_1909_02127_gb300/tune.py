@@ -3,8 +3,11 @@
 For R-MAT and uniform graphs of increasing size it builds each graph once per candidate threshold, times the count
 (CUDA events, median of several launches), keeps the fastest threshold per graph, and writes a size-class table
 (class bounds at the geometric midpoints of the graphs' edge counts) to tuning.json, keyed by device name and SM
-count.  The binding installs that table through tc_set_tuning when the device matches.  Counts do not depend on
-the table; only speed does.
+count.  It then times both counting kernels — the fused traversal and segmented intersection — on uniform graphs of
+several sizes and mean degrees and on the R-MAT series, and keeps the wedges-per-edge threshold below which
+tc_count takes the intersection kernel that minimises the summed time relative to each graph's faster kernel.
+The binding installs the table through tc_set_tuning when the device matches.  Counts do not depend on the
+table; only speed does.
 
     python -m paper_1909_02127_gb300.tune [--quick]
 """
@@ -62,7 +65,7 @@ def main():
         row = {"graph": spec.name, "times_ms": {}}
         count = None
         for cand in CANDIDATES:
-            tc.tc_set_tuning([(1 << 62, cand)])
+            tc.tc_set_tuning([(1 << 62, cand)], isect_max_wedges_milli=0)
             g = tc.tc_load_edges(ds, dd, spec.n)
             try:
                 tc.tc_build(g)
@@ -123,14 +126,54 @@ def main():
         tc.tc_free(h)
     batch_warp = int(min(batch_times, key=batch_times.get))
     print("batch", {k: round(v, 3) for k, v in batch_times.items()}, flush=True)
+    # the per-graph choice of kernel: time both on every graph, then pick the threshold on W/m
+    method_specs = [graphgen.er(1 << lg, (deg << lg) // 2, graphgen.BASE_SEED + 700 + 10 * lg + deg,
+                                name=f"er n=2^{lg} deg {deg}")
+                    for lg in ((16, 20, 22) if args.quick else (16, 18, 20, 22)) for deg in (4, 8, 16)]
+    method_specs += [graphgen.rmat(sc, 16, graphgen.BASE_SEED + 500 + sc, name=f"rmat{sc}")
+                     for sc in ((14, 18) if args.quick else (12, 16, 20))]
+    method_rows = []
+    for spec in method_specs:
+        ds, dd = spec.edges(device="cuda")
+        g = tc.tc_load_edges(ds, dd, spec.n)
+        try:
+            tc.tc_build(g)
+            info = tc.tc_graph_get_info(g)
+            row = {"graph": spec.name, "m": info["num_edges"],
+                   "wedges_milli": (1000 * info["num_wedges"] + max(info["num_edges"], 1) - 1) // max(info["num_edges"], 1)}
+            counts = set()
+            for name, ratio in (("fused", 0), ("intersect", 1 << 62)):
+                tc.tc_set_tuning([tuple(c) for c in classes], batch_warp_max_edges=batch_warp,
+                                 isect_max_wedges_milli=ratio)
+                row[name + "_ms"] = time_count(tc, g, d_total, reps)
+                counts.add(int(d_total.item()))
+            if len(counts) != 1:
+                raise RuntimeError("the two kernels disagree")
+        finally:
+            tc.tc_free(g)
+        method_rows.append(row)
+        print(row, flush=True)
+        del ds, dd
+        torch.cuda.empty_cache()
+
+    def cost(t):
+        return sum((r["intersect_ms"] if 0 < r["wedges_milli"] <= t else r["fused_ms"])
+                   / min(r["intersect_ms"], r["fused_ms"]) for r in method_rows)
+
+    cands = [0] + sorted({r["wedges_milli"] for r in method_rows})
+    isect_ratio = min(cands, key=lambda t: (cost(t), t))
+    print("isect_max_wedges_milli", isect_ratio, {t: round(cost(t), 3) for t in cands}, flush=True)
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     out = {"device": props.name, "sms": props.multi_processor_count, "cc": f"{props.major}.{props.minor}",
            "classes": classes, "batch_warp_max_edges": batch_warp, "batch_times_ms": batch_times,
+           "isect_max_wedges_milli": isect_ratio, "method_measurements": method_rows,
            "measurements": results}
     with open(args.out, "w") as f:
         json.dump(out, f, indent=1)
-    tc.tc_set_tuning([tuple(c) for c in classes], batch_warp_max_edges=batch_warp)
-    print(json.dumps({"classes": classes, "batch_warp_max_edges": batch_warp}))
+    tc.tc_set_tuning([tuple(c) for c in classes], batch_warp_max_edges=batch_warp,
+                     isect_max_wedges_milli=isect_ratio)
+    print(json.dumps({"classes": classes, "batch_warp_max_edges": batch_warp,
+                      "isect_max_wedges_milli": isect_ratio}))
 
 
 if __name__ == "__main__":

@@ -114,5 +114,11 @@ def test_tuning_table_round_trip_without_gpu(lib):
         with pytest.raises(tc.TCError):
             tc.tc_set_tuning([(1000, -1)])
         assert tc.tc_get_tuning() == [(1000, 5), (1 << 40, 1 << 15)]
+        ratio = tc.tc_get_isect_max_wedges_milli()
+        tc.tc_set_tuning([(1 << 40, 1 << 15)], isect_max_wedges_milli=2500)
+        assert tc.tc_get_isect_max_wedges_milli() == 2500
+        with pytest.raises(tc.TCError):
+            tc.tc_set_tuning([(1 << 40, 1 << 15)], isect_max_wedges_milli=-1)
+        tc.tc_set_tuning([(1 << 40, 1 << 15)], isect_max_wedges_milli=ratio)
     finally:
         tc.tc_set_tuning(saved)
