@@ -17,6 +17,8 @@
 // relabelled before the one sort that also removes the repeats.  Relabelling by rank gives the kernel two things:
 // hubs get the highest ids, so a bitmap over the top ids answers most closing-edge tests; and hub rows, which are
 // re-read by many sources, sit together in memory.
+#include <climits>
+
 #include "tc_build.cuh"
 #include "tc_internal.cuh"
 #include "tc_prims.cuh"
@@ -208,13 +210,16 @@ __global__ void k_rank_keys(const int32_t* __restrict__ deg, int64_t n, int B, u
   if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(maxdeg, mx);
 }
 
+// rank[id] = r and perm[r] = id; rcount (may be null) receives the input-pair count of rank r.
 __global__ void k_rank(const uint64_t* __restrict__ sorted, int64_t n, int B, int32_t* __restrict__ rank,
-                       int32_t* __restrict__ perm) {
+                       int32_t* __restrict__ perm, int32_t* __restrict__ rcount) {
   const uint64_t mask = (1ull << B) - 1ull;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t id = (int32_t)(sorted[r] & mask);
+    const uint64_t k = sorted[r];
+    const int32_t id = (int32_t)(k & mask);
     rank[id] = (int32_t)r;
     perm[r] = id;
+    if (rcount) rcount[r] = (int32_t)(k >> B);
   }
 }
 
@@ -265,6 +270,350 @@ __global__ void k_columns(const uint64_t* __restrict__ okeys, int64_t m, int B, 
   }
 }
 
+// ---- bucketed orientation --------------------------------------------------------------------------------------
+// The default build groups the relabelled pairs by source without a full sort: count the pairs at each source,
+// scan, scatter each target into its source's bucket, then sort and de-duplicate every bucket on chip.  A bucket
+// of L pairs belongs to a source with at least L input pairs, and only the vertices ranked above it can be its
+// targets; those all have at least L input pairs too, so there are fewer than 2M / L of them.  Long buckets thus
+// have a narrow target range, and a shared-memory bitmap over that range sorts and de-duplicates them in one pass.
+constexpr int kSmallRow = 32;            // buckets of 2..32 pairs: one warp, bitonic sort in a register
+constexpr int kWarpRow = 256;            // up to 256 pairs: one warp, bitonic sort in registers (8 per lane)
+constexpr int kWarpBits = 1 << 15;       // target ranges up to 32768 ids: one warp, bitmap (4 KB)
+constexpr int kRowThreads = 256;         // block size of k_rows_warp
+constexpr int kBigThreads = 1024;        // other buckets: one block, bitmap (<= kBigBits ids) or bitonic sort
+constexpr int kBigBits = 1 << 20;        // block bitmap capacity (128 KB)
+
+struct RowCounters {
+  unsigned long long m;  // distinct edges
+  unsigned int nwarp;    // buckets for k_rows_warp
+  unsigned int nblock;   // buckets for k_rows_block
+  unsigned int err;      // a bucket broke the size bound (cannot happen for consistent counts)
+  unsigned int pad;
+};
+
+// Each pair {a, b} goes to the bucket of its lower-ranked endpoint as the higher rank.  Bucket s has room for the
+// input-pair count of s (an upper bound on its size) starting at pstart[s]; len[s] counts its pairs (the order in a
+// bucket is free).
+__global__ void k_bucket(const uint64_t* __restrict__ keys, int64_t npairs, int B, const int32_t* __restrict__ rank,
+                         const int64_t* __restrict__ pstart, int32_t* __restrict__ len, int32_t* __restrict__ tgt) {
+  const uint64_t mask = (1ull << B) - 1ull;
+  const uint64_t sentinel = (1ull << (2 * B)) - 1ull;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npairs;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = keys[i];
+    if (k == sentinel) continue;
+    const int32_t ra = rank[k >> B], rb = rank[k & mask];
+    const int32_t lo = ra < rb ? ra : rb, hi = ra < rb ? rb : ra;
+    const int32_t slot = atomicAdd(&len[lo], 1);
+    tgt[pstart[lo] + slot] = hi;
+  }
+}
+
+// Buckets of up to kSmallRow pairs, sorted and de-duplicated in place by one warp each (32 consecutive sources per
+// warp).  Longer buckets are listed for k_rows_warp (front of `lists`) when their target range fits a warp's bitmap
+// or they fit a warp's registers, and for k_rows_block (back of `lists`) otherwise.  d[s] = distinct targets of s.
+__global__ void k_rows_small(const int64_t* __restrict__ pstart, const int32_t* __restrict__ len, int64_t n,
+                             int32_t* __restrict__ tgt, int32_t* __restrict__ d, int32_t* __restrict__ lists,
+                             RowCounters* __restrict__ rc) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long msum = 0;
+  for (int64_t base = warp0 * 32; base < n; base += nwarps * 32) {
+    const int64_t sidx = base + lane;
+    int64_t ps = 0;
+    int32_t L = 0;
+    if (sidx < n) {
+      ps = pstart[sidx];
+      L = len[sidx];
+    }
+    const int64_t range = n - 1 - sidx;
+    const bool to_warp = L > kSmallRow && (range <= kWarpBits || L <= kWarpRow);
+    const bool to_block = L > kSmallRow && !to_warp;
+    const unsigned mw = __ballot_sync(kFull, to_warp), mb = __ballot_sync(kFull, to_block);
+    unsigned pw = 0, pb = 0;
+    if (lane == 0) {
+      if (mw) pw = atomicAdd(&rc->nwarp, (unsigned)__popc(mw));
+      if (mb) pb = atomicAdd(&rc->nblock, (unsigned)__popc(mb));
+    }
+    pw = __shfl_sync(kFull, pw, 0);
+    pb = __shfl_sync(kFull, pb, 0);
+    if (to_warp) lists[pw + __popc(mw & lt)] = (int32_t)sidx;
+    if (to_block) lists[n - 1 - (pb + __popc(mb & lt))] = (int32_t)sidx;
+    int32_t dd = L <= 1 ? L : 0;  // a bucket of one pair is sorted and distinct
+    unsigned todo = __ballot_sync(kFull, L >= 2 && L <= kSmallRow);
+    while (todo) {
+      const int k = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int64_t rps = __shfl_sync(kFull, ps, k);
+      const int32_t rl = __shfl_sync(kFull, L, k);
+      int32_t x = lane < rl ? tgt[rps + lane] : INT_MAX;
+#pragma unroll
+      for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+          const int32_t y = __shfl_xor_sync(kFull, x, j);
+          x = (((lane & j) == 0) == ((lane & kk) == 0)) ? min(x, y) : max(x, y);
+        }
+      }
+      const int32_t prev = __shfl_up_sync(kFull, x, 1);
+      const bool keep = x != INT_MAX && (lane == 0 || x != prev);
+      const unsigned km = __ballot_sync(kFull, keep);
+      if (keep) tgt[rps + __popc(km & lt)] = x;
+      if (lane == k) dd = __popc(km);
+    }
+    if (sidx < n && L <= kSmallRow) {
+      d[sidx] = dd;
+      msum += (unsigned long long)dd;
+    }
+  }
+  msum = warp_sum(msum);
+  if (lane == 0 && msum) atomicAdd(&rc->m, msum);
+}
+
+// Bitonic sort of p (a power of two) values in shared memory by `stride` cooperating threads at index t; sync()
+// separates the stages.
+struct BlockSync {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+template <class Sync>
+__device__ __forceinline__ void bitonic_smem(int32_t* v, int p, int t, int stride, Sync sync) {
+  for (int kk = 2; kk <= p; kk <<= 1) {
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      for (int i = t; i < p; i += stride) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const int32_t a = v[i], b = v[ixj];
+          if ((a > b) == ((i & kk) == 0)) {
+            v[i] = b;
+            v[ixj] = a;
+          }
+        }
+      }
+      sync();
+    }
+  }
+}
+
+// Bitonic sort of 32*T values held by a warp, value t of lane l at position 32t + l; then the distinct values are
+// written in order to out[0..) and their number returned (INT_MAX marks an empty position).
+template <int T>
+__device__ __forceinline__ uint32_t warp_sort_unique(int32_t (&x)[T], int32_t* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+#pragma unroll
+  for (int kk = 2; kk <= 32 * T; kk <<= 1) {
+#pragma unroll
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {
+        const int jt = j >> 5;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+          if (t & jt) continue;
+          const bool asc = ((t * 32 + lane) & kk) == 0;
+          const int32_t a = x[t], b = x[t + jt];
+          if ((a > b) == asc) {
+            x[t] = b;
+            x[t + jt] = a;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+          const int32_t y = __shfl_xor_sync(kFull, x[t], j);
+          const bool asc = ((t * 32 + lane) & kk) == 0;
+          x[t] = (((lane & j) == 0) == asc) ? min(x[t], y) : max(x[t], y);
+        }
+      }
+    }
+  }
+  uint32_t run = 0;
+  int32_t last = __shfl_sync(kFull, x[0], 0) - 1;  // differs from the first value
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int32_t up = __shfl_up_sync(kFull, x[t], 1);
+    const int32_t prev = lane == 0 ? last : up;
+    const bool keep = x[t] != INT_MAX && x[t] != prev;
+    const unsigned km = __ballot_sync(kFull, keep);
+    if (keep) out[run + __popc(km & lt)] = x[t];
+    run += __popc(km);
+    last = __shfl_sync(kFull, x[t], 31);
+  }
+  return run;
+}
+
+// Buckets listed for one warp each: a bitmap over the target range (s, n) in the warp's shared memory when the range
+// has at most kWarpBits ids, else (at most kWarpRow pairs) a bitonic sort in registers.
+__global__ void __launch_bounds__(kRowThreads) k_rows_warp(const int64_t* __restrict__ pstart,
+                                                           const int32_t* __restrict__ len, int64_t n,
+                                                           int32_t* __restrict__ tgt, int32_t* __restrict__ d,
+                                                           const int32_t* __restrict__ list,
+                                                           RowCounters* __restrict__ rc) {
+  __shared__ uint32_t bm_all[kRowThreads / 32][kWarpBits / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned rows = rc->nwarp;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  uint32_t* bm = bm_all[warp];
+  unsigned long long msum = 0;
+  for (unsigned r = gw; r < rows; r += nw) {
+    const int32_t sidx = list[r];
+    const int64_t ps = pstart[sidx];
+    const int32_t L = len[sidx];
+    const int64_t range = n - 1 - sidx;
+    uint32_t run;
+    if (range <= kWarpBits) {
+      const int words = (int)((range + 31) >> 5);
+      for (int w = lane; w < words; w += 32) bm[w] = 0u;
+      __syncwarp();
+      for (int32_t i = lane; i < L; i += 32) {
+        const int32_t b = tgt[ps + i] - sidx - 1;
+        atomicOr(&bm[b >> 5], 1u << (b & 31));
+      }
+      __syncwarp();
+      // lane l emits words [l*per, (l+1)*per) in order
+      const int per = (words + 31) >> 5;
+      const int w0 = min(words, lane * per), w1 = min(words, w0 + per);
+      uint32_t c = 0;
+      for (int w = w0; w < w1; ++w) c += __popc(bm[w]);
+      const uint32_t incl = warp_inclusive_scan(c);
+      uint32_t pos = incl - c;
+      run = __shfl_sync(kFull, incl, 31);
+      for (int w = w0; w < w1; ++w) {
+        uint32_t bits = bm[w];
+        while (bits) {
+          const int b = __ffs(bits) - 1;
+          bits &= bits - 1;
+          tgt[ps + pos++] = sidx + 1 + w * 32 + b;
+        }
+      }
+      __syncwarp();
+    } else if (L <= 64) {
+      int32_t x[2];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) x[t] = t * 32 + lane < L ? tgt[ps + t * 32 + lane] : INT_MAX;
+      run = warp_sort_unique<2>(x, tgt + ps);
+    } else if (L <= 128) {
+      int32_t x[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) x[t] = t * 32 + lane < L ? tgt[ps + t * 32 + lane] : INT_MAX;
+      run = warp_sort_unique<4>(x, tgt + ps);
+    } else {
+      int32_t x[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) x[t] = t * 32 + lane < L ? tgt[ps + t * 32 + lane] : INT_MAX;
+      run = warp_sort_unique<8>(x, tgt + ps);
+    }
+    if (lane == 0) d[sidx] = (int32_t)run;
+    msum += run;
+  }
+  if (lane == 0 && msum) atomicAdd(&rc->m, msum);
+}
+
+// Buckets listed for one block each (more than kWarpRow pairs, target range above kWarpBits): a bitmap over the
+// range when it has at most kBigBits ids, else a bitonic sort in shared memory (such a bucket has fewer than
+// 2M / kBigBits <= mid_max pairs).
+__global__ void __launch_bounds__(kBigThreads) k_rows_block(const int64_t* __restrict__ pstart,
+                                                            const int32_t* __restrict__ len, int64_t n,
+                                                            int32_t mid_max, int32_t* __restrict__ tgt,
+                                                            int32_t* __restrict__ d,
+                                                            const int32_t* __restrict__ lists,
+                                                            RowCounters* __restrict__ rc) {
+  extern __shared__ __align__(16) uint32_t blk_smem[];  // kBigBits / 32 words (>= mid_max ints)
+  __shared__ uint32_t ws[kBigThreads / 32];
+  const int tid = threadIdx.x;
+  const unsigned rows = rc->nblock;
+  for (unsigned r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int32_t sidx = lists[n - 1 - r];
+    const int64_t ps = pstart[sidx];
+    const int64_t L = len[sidx];
+    const int64_t range = n - 1 - sidx;
+    uint32_t total = 0;
+    if (range <= kBigBits) {
+      const int words = (int)((range + 31) >> 5);
+      for (int w = tid; w < words; w += kBigThreads) blk_smem[w] = 0u;
+      __syncthreads();
+      for (int64_t i = tid; i < L; i += kBigThreads) {
+        const int32_t b = tgt[ps + i] - sidx - 1;
+        atomicOr(&blk_smem[b >> 5], 1u << (b & 31));
+      }
+      __syncthreads();
+      const int per = (words + kBigThreads - 1) / kBigThreads;
+      const int w0 = min(words, tid * per), w1 = min(words, w0 + per);
+      uint32_t c = 0;
+      for (int w = w0; w < w1; ++w) c += __popc(blk_smem[w]);
+      uint32_t pos = block_exclusive_scan<uint32_t>(c, ws, &total);
+      for (int w = w0; w < w1; ++w) {
+        uint32_t bits = blk_smem[w];
+        while (bits) {
+          const int b = __ffs(bits) - 1;
+          bits &= bits - 1;
+          tgt[ps + pos++] = sidx + 1 + w * 32 + b;
+        }
+      }
+    } else if (L <= mid_max) {
+      int32_t* v = reinterpret_cast<int32_t*>(blk_smem);
+      int p = 2 * kWarpRow;
+      while (p < L) p <<= 1;
+      for (int i = tid; i < p; i += kBigThreads) v[i] = i < L ? tgt[ps + i] : INT_MAX;
+      __syncthreads();
+      bitonic_smem(v, p, tid, kBigThreads, BlockSync{});
+      for (int64_t c = 0; c < L; c += kBigThreads) {
+        const int64_t i = c + tid;
+        const bool keep = i < L && (i == 0 || v[i] != v[i - 1]);
+        uint32_t tot;
+        const uint32_t pos = total + block_exclusive_scan<uint32_t>(keep ? 1u : 0u, ws, &tot);
+        if (keep) tgt[ps + pos] = v[i];
+        total += tot;
+      }
+    } else if (tid == 0) {  // cannot happen for consistent counts: report and leave the bucket alone
+      atomicOr(&rc->err, 1u);
+    }
+    if (tid == 0) {
+      d[sidx] = (int32_t)total;
+      atomicAdd(&rc->m, (unsigned long long)total);
+    }
+    __syncthreads();
+  }
+}
+
+// Rows into the CSR: row s takes its d[s] sorted distinct targets, then pad ids up to its padded length.  A row of
+// one quad is written by its own lane with one 16-byte store; longer rows by the whole warp.
+__global__ void k_rows_copy(const int64_t* __restrict__ pstart, const int32_t* __restrict__ tgt,
+                            const int32_t* __restrict__ d, const int64_t* __restrict__ off, int64_t n,
+                            int32_t* __restrict__ col, int32_t pad) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = warp0 * 32; base < n; base += nwarps * 32) {
+    const int64_t sidx = base + lane;
+    int64_t ps = 0, o = 0;
+    int32_t dd = 0, pl = 0;
+    if (sidx < n) {
+      ps = pstart[sidx];
+      o = off[sidx];
+      dd = d[sidx];
+      pl = (int32_t)(off[sidx + 1] - o);
+    }
+    if (pl == 4) {
+      int4 q = make_int4(pad, pad, pad, pad);
+      q.x = tgt[ps];
+      if (dd > 1) q.y = tgt[ps + 1];
+      if (dd > 2) q.z = tgt[ps + 2];
+      if (dd > 3) q.w = tgt[ps + 3];
+      *reinterpret_cast<int4*>(col + o) = q;
+    }
+    unsigned todo = __ballot_sync(kFull, pl > 4);
+    while (todo) {
+      const int k = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int64_t rps = __shfl_sync(kFull, ps, k), ro = __shfl_sync(kFull, o, k);
+      const int32_t rd = __shfl_sync(kFull, dd, k), rpl = __shfl_sync(kFull, pl, k);
+      for (int32_t j = lane; j < rpl; j += 32) col[ro + j] = j < rd ? tgt[rps + j] : pad;
+    }
+  }
+}
+
 // ---- work estimate and binning ----------------------------------------------------------------------------------
 struct BinCounters {
   unsigned long long wedges;
@@ -275,8 +624,11 @@ struct BinCounters {
   int pad;
 };
 
+// w(u) = sum of the padded lengths of the rows of N+(u) (the entries the counting kernel reads in hop 2) and the
+// true 2-path count; sources with d+(u) >= 2 and a 2-path go to the block bin (w above the threshold) or the warp
+// bin.  Rows of up to 32 entries are summed by their own lane, longer ones by the whole warp.
 __global__ void k_bins(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                       const int64_t* __restrict__ ustart, int64_t n, int64_t block_min_work,
+                       const int32_t* __restrict__ dplus, int64_t n, int64_t block_min_work,
                        int32_t* __restrict__ list, BinCounters* __restrict__ bc) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
@@ -285,18 +637,41 @@ __global__ void k_bins(const int64_t* __restrict__ off, const int32_t* __restric
   int dmax = 0;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
     const int64_t u = base + threadIdx.x;
-    int64_t d = 0, wpad = 0, wtrue = 0;
+    int64_t b = 0;
+    int32_t d = 0;
     if (u < n) {
-      d = ustart[u + 1] - ustart[u];
-      const int64_t b = off[u];
+      d = dplus[u];
+      b = off[u];
+    }
+    int64_t wpad = 0, wtrue = 0;
+    if (d <= 32) {
       for (int64_t j = b; j < b + d; ++j) {
-        const int32_t v = col[j];
-        wpad += off[v + 1] - off[v];
-        wtrue += ustart[v + 1] - ustart[v];
+        const int32_t dv = dplus[col[j]];
+        wpad += (dv + 3) & ~3;
+        wtrue += dv;
+      }
+    }
+    unsigned longs = __ballot_sync(kFull, d > 32);
+    while (longs) {
+      const int k = __ffs(longs) - 1;
+      longs &= longs - 1;
+      const int64_t rb = __shfl_sync(kFull, b, k);
+      const int32_t rd = __shfl_sync(kFull, d, k);
+      int64_t p = 0, t = 0;
+      for (int32_t j = lane; j < rd; j += 32) {
+        const int32_t dv = dplus[col[rb + j]];
+        p += (dv + 3) & ~3;
+        t += dv;
+      }
+      p = warp_sum(p);
+      t = warp_sum(t);
+      if (lane == k) {
+        wpad = p;
+        wtrue = t;
       }
     }
     wsum += (unsigned long long)wtrue;
-    if (d > dmax) dmax = (int)d;
+    if (d > dmax) dmax = d;
     const bool keep = d >= 2 && wtrue > 0;
     const bool blk = keep && wpad > block_min_work;
     const bool wrp = keep && !blk;
@@ -431,6 +806,102 @@ tc_status peel_keys(const Allocator& a, Buf& ukeys, int64_t* m, int64_t n, int B
   return st;
 }
 
+// The bucketed orientation: from the pair keys, the ranks and each rank's input-pair count to g->off, g->col;
+// dplus (n entries, allocated here) receives d+(s); *m the distinct edges and *entries the padded column entries.
+tc_status bucket_csr(tc_graph* g, const int32_t* rank, const int32_t* rcount, Buf& dplus, int64_t* m,
+                     int64_t* entries, cudaStream_t s) {
+  const Allocator& a = g->alloc;
+  const int B = g->key_bits;
+  const int64_t M = g->num_pairs;
+  const int64_t n = g->n;
+  const int64_t n1 = n > 0 ? n : 1;
+  Buf pstart, len, tgt, lists, rcb, plen;
+  tc_status st = TC_OK;
+  auto launched = [&](const char* what) {
+    note_launch();
+    return cuda_status(cudaGetLastError(), what);
+  };
+  // a bucket whose targets span more than kBigBits ids has fewer than 2M / kBigBits <= mid_max pairs
+  int32_t mid_max = 2048;
+  while ((2 * M) / mid_max > (int64_t)kBigBits) mid_max <<= 1;
+  RowCounters hrc{};
+  do {
+    // bucket s has room for the input-pair count of s: 2 slots per pair in all
+    if ((st = buf_alloc(a, pstart, (size_t)(n + 1) * 8, s))) break;
+    if ((st = buf_alloc(a, len, (size_t)n1 * 4, s))) break;
+    if ((st = buf_alloc(a, tgt, (size_t)(M > 0 ? 2 * M : 1) * 4, s))) break;
+    if ((st = buf_alloc(a, dplus, (size_t)n1 * 4, s))) break;
+    if ((st = buf_alloc(a, lists, (size_t)n1 * 4, s))) break;
+    if ((st = buf_alloc(a, rcb, sizeof(RowCounters), s))) break;
+    if ((st = cuda_status(cudaMemsetAsync(len.p, 0, (size_t)n1 * 4, s), "memset len"))) break;
+    if ((st = cuda_status(cudaMemsetAsync(rcb.p, 0, sizeof(RowCounters), s), "memset rows"))) break;
+    if (n > 0) {
+      if ((st = exclusive_scan_i32_to_i64(a, rcount, pstart.as<int64_t>(), n, s))) break;
+    } else if ((st = cuda_status(cudaMemsetAsync(pstart.p, 0, 8, s), "memset pstart"))) {
+      break;
+    }
+    if (M > 0) {
+      k_bucket<<<grid_for(M, 256), 256, 0, s>>>(g->keys.as<uint64_t>(), M, B, rank, pstart.as<int64_t>(),
+                                                len.as<int32_t>(), tgt.as<int32_t>());
+      if ((st = launched("k_bucket"))) break;
+    }
+    buf_release(a, g->keys, s);
+    RowCounters* rc = rcb.as<RowCounters>();
+    int32_t* rlist = lists.as<int32_t>();
+    if (n > 0) {
+      k_rows_small<<<grid_for(n, 256), 256, 0, s>>>(pstart.as<int64_t>(), len.as<int32_t>(), n, tgt.as<int32_t>(),
+                                                    dplus.as<int32_t>(), rlist, rc);
+      if ((st = launched("k_rows_small"))) break;
+      k_rows_warp<<<4 * kNumSMs, kRowThreads, 0, s>>>(pstart.as<int64_t>(), len.as<int32_t>(), n,
+                                                      tgt.as<int32_t>(), dplus.as<int32_t>(), rlist, rc);
+      if ((st = launched("k_rows_warp"))) break;
+      const size_t blk_smem = (size_t)kBigBits / 8;
+      if ((st = cuda_status(cudaFuncSetAttribute(k_rows_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)blk_smem), "k_rows_block attribute")))
+        break;
+      k_rows_block<<<kNumSMs, kBigThreads, blk_smem, s>>>(pstart.as<int64_t>(), len.as<int32_t>(), n, mid_max,
+                                                          tgt.as<int32_t>(), dplus.as<int32_t>(), rlist, rc);
+      if ((st = launched("k_rows_block"))) break;
+    }
+    buf_release(a, len, s);
+    // padded offsets
+    if ((st = buf_alloc(a, g->off, (size_t)(n + 1) * 8, s))) break;
+    if ((st = buf_alloc(a, plen, (size_t)n1 * 4, s))) break;
+    if (n > 0) {
+      k_padded_len<<<grid_for(n, 256), 256, 0, s>>>(dplus.as<int32_t>(), n, plen.as<int32_t>());
+      if ((st = launched("k_padded_len"))) break;
+      if ((st = exclusive_scan_i32_to_i64(a, plen.as<int32_t>(), g->off.as<int64_t>(), n, s))) break;
+    } else if ((st = cuda_status(cudaMemsetAsync(g->off.p, 0, 8, s), "memset off"))) {
+      break;
+    }
+    buf_release(a, plen, s);
+    if ((st = cuda_status(cudaMemcpyAsync(entries, g->off.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, s),
+                          "copy entries")))
+      break;
+    if ((st = cuda_status(cudaMemcpyAsync(&hrc, rc, sizeof(RowCounters), cudaMemcpyDeviceToHost, s), "copy rows")))
+      break;
+    if ((st = cuda_status(cudaStreamSynchronize(s), "sync entries"))) break;
+    if (hrc.err) {
+      set_error("tc_build: a bucket's targets exceeded the range bound (inconsistent pair counts)");
+      st = TC_ERR_INTERNAL;
+      break;
+    }
+    *m = (int64_t)hrc.m;
+    // columns: rows then pad ids, and one spare quad of pad ids at the end
+    const int64_t ncol = *entries + 4;
+    if ((st = buf_alloc(a, g->col, (size_t)ncol * 4, s))) break;
+    k_fill<<<1, 32, 0, s>>>(g->col.as<int32_t>() + *entries, 4, (int32_t)n);
+    if ((st = launched("k_fill"))) break;
+    if (n > 0 && *entries > 0) {
+      k_rows_copy<<<grid_for(n, 256), 256, 0, s>>>(pstart.as<int64_t>(), tgt.as<int32_t>(), dplus.as<int32_t>(),
+                                                   g->off.as<int64_t>(), n, g->col.as<int32_t>(), (int32_t)n);
+      if ((st = launched("k_rows_copy"))) break;
+    }
+  } while (0);
+  for (Buf* b : {&pstart, &len, &tgt, &lists, &rcb, &plen}) buf_release(a, *b, s);
+  return st;
+}
+
 tc_status build_graph(tc_graph* g, cudaStream_t s) { return build_graph_pruned(g, -1, nullptr, s); }
 
 tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* ps, cudaStream_t s) {
@@ -441,7 +912,7 @@ tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* p
   const int64_t n1 = n > 0 ? n : 1;
   const uint64_t sentinel = (1ull << (2 * B)) - 1ull;
   tc_status st = TC_OK;
-  Buf alt, part, counters, odeg, ukeys, rkeys, rkeys_alt, rank, ustart, plen;
+  Buf alt, part, counters, odeg, ukeys, rkeys, rkeys_alt, rank, rcount, ustart, plen;
   int64_t m = 0;
   BinCounters hb{};
   int64_t total_padded = 0;
@@ -470,92 +941,101 @@ tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* p
       while (dbits < 32 && (1ll << dbits) <= (int64_t)maxdeg) ++dbits;
       uint64_t* rs = nullptr;
       if ((st = radix_sort_u64(a, rkeys.as<uint64_t>(), rkeys_alt.as<uint64_t>(), n, B, B + dbits, &rs, s))) break;
-      k_rank<<<grid_for(n, 256), 256, 0, s>>>(rs, n, B, rank.as<int32_t>(), g->perm.as<int32_t>());
+      if (peel_rounds < 0 && (st = buf_alloc(a, rcount, (size_t)n * 4, s))) break;
+      k_rank<<<grid_for(n, 256), 256, 0, s>>>(rs, n, B, rank.as<int32_t>(), g->perm.as<int32_t>(),
+                                              rcount.as<int32_t>());
       if ((st = launched("k_rank"))) break;
       buf_release(a, rkeys, s);
       buf_release(a, rkeys_alt, s);
     }
     buf_release(a, g->indeg, s);
 
-    // ---- relabel, sort, unique: ukeys = distinct (rank s << B) | rank d with s < d, sorted ----
-    if (M > 0) {
-      uint64_t* sorted = nullptr;
-      if ((st = buf_alloc(a, alt, (size_t)M * 8, s))) break;
-      k_relabel<<<grid_for(M, 256), 256, 0, s>>>(g->keys.as<uint64_t>(), M, B, rank.as<int32_t>(),
-                                                 alt.as<uint64_t>());
-      if ((st = launched("k_relabel"))) break;
-      if ((st = radix_sort_u64(a, alt.as<uint64_t>(), g->keys.as<uint64_t>(), M, 0, 2 * B, &sorted, s))) break;
-      const bool in_alt = sorted == alt.as<uint64_t>();
-      uint64_t* uout = in_alt ? g->keys.as<uint64_t>() : alt.as<uint64_t>();
-      const int64_t tiles = (M + kUTile - 1) / kUTile;
-      if ((st = buf_alloc(a, part, (size_t)tiles * 4, s))) break;
-      k_unique_count<<<(unsigned)tiles, kUThreads, 0, s>>>(sorted, M, sentinel, part.as<uint32_t>());
-      if ((st = launched("k_unique_count"))) break;
-      if ((st = exclusive_scan_u32(a, part.as<uint32_t>(), tiles, s))) break;
-      k_unique_scatter<<<(unsigned)tiles, kUThreads, 0, s>>>(sorted, M, sentinel, part.as<uint32_t>(), uout,
-                                                              counters.as<int64_t>());
-      if ((st = launched("k_unique_scatter"))) break;
-      if ((st = cuda_status(cudaMemcpyAsync(&m, counters.p, 8, cudaMemcpyDeviceToHost, s), "copy m"))) break;
-      if ((st = cuda_status(cudaStreamSynchronize(s), "sync m"))) break;
-      buf_release(a, part, s);
-      if (in_alt) {
-        ukeys = g->keys;
-        g->keys = Buf{};
-      } else {
-        ukeys = alt;
-        alt = Buf{};
+    if (peel_rounds < 0) {  // the default: bucketed orientation
+      if ((st = bucket_csr(g, rank.as<int32_t>(), rcount.as<int32_t>(), odeg, &m, &total_padded, s))) break;
+      buf_release(a, rank, s);
+      buf_release(a, rcount, s);
+      g->m = m;
+      g->csr_entries = total_padded;
+    } else {  // the sort path (needed by pruning, which works on the sorted distinct keys)
+      // ---- relabel, sort, unique: ukeys = distinct (rank s << B) | rank d with s < d, sorted ----
+      if (M > 0) {
+        uint64_t* sorted = nullptr;
+        if ((st = buf_alloc(a, alt, (size_t)M * 8, s))) break;
+        k_relabel<<<grid_for(M, 256), 256, 0, s>>>(g->keys.as<uint64_t>(), M, B, rank.as<int32_t>(),
+                                                   alt.as<uint64_t>());
+        if ((st = launched("k_relabel"))) break;
+        if ((st = radix_sort_u64(a, alt.as<uint64_t>(), g->keys.as<uint64_t>(), M, 0, 2 * B, &sorted, s))) break;
+        const bool in_alt = sorted == alt.as<uint64_t>();
+        uint64_t* uout = in_alt ? g->keys.as<uint64_t>() : alt.as<uint64_t>();
+        const int64_t tiles = (M + kUTile - 1) / kUTile;
+        if ((st = buf_alloc(a, part, (size_t)tiles * 4, s))) break;
+        k_unique_count<<<(unsigned)tiles, kUThreads, 0, s>>>(sorted, M, sentinel, part.as<uint32_t>());
+        if ((st = launched("k_unique_count"))) break;
+        if ((st = exclusive_scan_u32(a, part.as<uint32_t>(), tiles, s))) break;
+        k_unique_scatter<<<(unsigned)tiles, kUThreads, 0, s>>>(sorted, M, sentinel, part.as<uint32_t>(), uout,
+                                                                counters.as<int64_t>());
+        if ((st = launched("k_unique_scatter"))) break;
+        if ((st = cuda_status(cudaMemcpyAsync(&m, counters.p, 8, cudaMemcpyDeviceToHost, s), "copy m"))) break;
+        if ((st = cuda_status(cudaStreamSynchronize(s), "sync m"))) break;
+        buf_release(a, part, s);
+        if (in_alt) {
+          ukeys = g->keys;
+          g->keys = Buf{};
+        } else {
+          ukeys = alt;
+          alt = Buf{};
+        }
+        buf_release(a, alt, s);
+        buf_release(a, g->keys, s);
       }
-      buf_release(a, alt, s);
-      buf_release(a, g->keys, s);
-    }
-    buf_release(a, rank, s);
-    if (peel_rounds >= 0 && m > 0 && (st = peel_keys(a, ukeys, &m, n, B, sentinel, peel_rounds, ps, s))) break;
-    g->m = m;
+      buf_release(a, rank, s);
+      if (peel_rounds >= 0 && m > 0 && (st = peel_keys(a, ukeys, &m, n, B, sentinel, peel_rounds, ps, s))) break;
+      g->m = m;
 
-    // ---- offsets: unpadded starts (ustart) and padded offsets (off) ----
-    if ((st = buf_alloc(a, odeg, (size_t)n1 * 4, s))) break;
-    if ((st = cuda_status(cudaMemsetAsync(odeg.p, 0, (size_t)n1 * 4, s), "memset odeg"))) break;
-    if (m > 0) {
-      k_outdeg<<<grid_for(m, 256), 256, 0, s>>>(ukeys.as<uint64_t>(), m, B, odeg.as<int32_t>());
-      if ((st = launched("k_outdeg"))) break;
-    }
-    if ((st = buf_alloc(a, ustart, (size_t)(n + 1) * 8, s))) break;
-    if ((st = buf_alloc(a, g->off, (size_t)(n + 1) * 8, s))) break;
-    if ((st = buf_alloc(a, plen, (size_t)n1 * 4, s))) break;
-    if (n > 0) {
-      if ((st = exclusive_scan_i32_to_i64(a, odeg.as<int32_t>(), ustart.as<int64_t>(), n, s))) break;
-      k_padded_len<<<grid_for(n, 256), 256, 0, s>>>(odeg.as<int32_t>(), n, plen.as<int32_t>());
-      if ((st = launched("k_padded_len"))) break;
-      if ((st = exclusive_scan_i32_to_i64(a, plen.as<int32_t>(), g->off.as<int64_t>(), n, s))) break;
-    } else {
-      if ((st = cuda_status(cudaMemsetAsync(ustart.p, 0, 8, s), "memset ustart"))) break;
-      if ((st = cuda_status(cudaMemsetAsync(g->off.p, 0, 8, s), "memset off"))) break;
-    }
-    buf_release(a, plen, s);
-    buf_release(a, odeg, s);
-    if ((st = cuda_status(cudaMemcpyAsync(&total_padded, g->off.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, s),
-                          "copy entries")))
-      break;
-    if ((st = cuda_status(cudaStreamSynchronize(s), "sync entries"))) break;
-    g->csr_entries = total_padded;
+      // ---- offsets: unpadded starts (ustart) and padded offsets (off) ----
+      if ((st = buf_alloc(a, odeg, (size_t)n1 * 4, s))) break;
+      if ((st = cuda_status(cudaMemsetAsync(odeg.p, 0, (size_t)n1 * 4, s), "memset odeg"))) break;
+      if (m > 0) {
+        k_outdeg<<<grid_for(m, 256), 256, 0, s>>>(ukeys.as<uint64_t>(), m, B, odeg.as<int32_t>());
+        if ((st = launched("k_outdeg"))) break;
+      }
+      if ((st = buf_alloc(a, ustart, (size_t)(n + 1) * 8, s))) break;
+      if ((st = buf_alloc(a, g->off, (size_t)(n + 1) * 8, s))) break;
+      if ((st = buf_alloc(a, plen, (size_t)n1 * 4, s))) break;
+      if (n > 0) {
+        if ((st = exclusive_scan_i32_to_i64(a, odeg.as<int32_t>(), ustart.as<int64_t>(), n, s))) break;
+        k_padded_len<<<grid_for(n, 256), 256, 0, s>>>(odeg.as<int32_t>(), n, plen.as<int32_t>());
+        if ((st = launched("k_padded_len"))) break;
+        if ((st = exclusive_scan_i32_to_i64(a, plen.as<int32_t>(), g->off.as<int64_t>(), n, s))) break;
+      } else {
+        if ((st = cuda_status(cudaMemsetAsync(ustart.p, 0, 8, s), "memset ustart"))) break;
+        if ((st = cuda_status(cudaMemsetAsync(g->off.p, 0, 8, s), "memset off"))) break;
+      }
+      buf_release(a, plen, s);
+      if ((st = cuda_status(cudaMemcpyAsync(&total_padded, g->off.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, s),
+                            "copy entries")))
+        break;
+      if ((st = cuda_status(cudaStreamSynchronize(s), "sync entries"))) break;
+      g->csr_entries = total_padded;
 
-    // ---- columns: fill with the pad id n, then scatter ----
-    const int64_t ncol = total_padded + 4;
-    if ((st = buf_alloc(a, g->col, (size_t)ncol * 4, s))) break;
-    k_fill<<<grid_for(ncol, 256), 256, 0, s>>>(g->col.as<int32_t>(), ncol, (int32_t)n);
-    if ((st = launched("k_fill"))) break;
-    if (m > 0) {
-      k_columns<<<grid_for(m, 256), 256, 0, s>>>(ukeys.as<uint64_t>(), m, B, ustart.as<int64_t>(),
-                                                 g->off.as<int64_t>(), g->col.as<int32_t>());
-      if ((st = launched("k_columns"))) break;
+      // ---- columns: fill with the pad id n, then scatter ----
+      const int64_t ncol = total_padded + 4;
+      if ((st = buf_alloc(a, g->col, (size_t)ncol * 4, s))) break;
+      k_fill<<<grid_for(ncol, 256), 256, 0, s>>>(g->col.as<int32_t>(), ncol, (int32_t)n);
+      if ((st = launched("k_fill"))) break;
+      if (m > 0) {
+        k_columns<<<grid_for(m, 256), 256, 0, s>>>(ukeys.as<uint64_t>(), m, B, ustart.as<int64_t>(),
+                                                   g->off.as<int64_t>(), g->col.as<int32_t>());
+        if ((st = launched("k_columns"))) break;
+      }
+      buf_release(a, ukeys, s);
     }
-    buf_release(a, ukeys, s);
 
     // ---- bins ----
     if ((st = buf_alloc(a, g->list, (size_t)n1 * 4, s))) break;
     if ((st = cuda_status(cudaMemsetAsync(counters.p, 0, sizeof(BinCounters), s), "memset bins"))) break;
     if (n > 0) {
-      k_bins<<<grid_for(n, 256), 256, 0, s>>>(g->off.as<int64_t>(), g->col.as<int32_t>(), ustart.as<int64_t>(), n,
+      k_bins<<<grid_for(n, 256), 256, 0, s>>>(g->off.as<int64_t>(), g->col.as<int32_t>(), odeg.as<int32_t>(), n,
                                               block_min_work_for(m), g->list.as<int32_t>(),
                                               counters.as<BinCounters>());
       if ((st = launched("k_bins"))) break;
@@ -566,7 +1046,7 @@ tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* p
     if ((st = cuda_status(cudaStreamSynchronize(s), "sync bins"))) break;
   } while (0);
 
-  for (Buf* b : {&alt, &part, &counters, &odeg, &ukeys, &rkeys, &rkeys_alt, &rank, &ustart, &plen})
+  for (Buf* b : {&alt, &part, &counters, &odeg, &ukeys, &rkeys, &rkeys_alt, &rank, &rcount, &ustart, &plen})
     buf_release(a, *b, s);
   buf_release(a, g->keys, s);
   buf_release(a, g->indeg, s);

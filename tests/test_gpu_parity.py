@@ -202,19 +202,49 @@ def test_rmat20_full(tc):
         tc.tc_free(g)
 
 
-def test_csr_structure(tc):
-    """The oriented CSR: vertices relabelled by rank in the (degree, id) order, each undirected edge stored once
+def _repeat_heavy_pairs():
+    """Hubs whose pairs repeat thousands of times: the build's buckets then span all three sizes (up to 32 pairs,
+    up to a few thousand, and longer), with most of each long bucket being repeats."""
+    rng = np.random.default_rng(2100)
+    n = 6000
+    hubs = np.arange(12, dtype=np.int32)
+    parts_s, parts_d = [], []
+    for i in range(12):
+        for j in range(i + 1, 12):
+            k = int(rng.integers(50, 4000))
+            parts_s.append(np.full(k, hubs[i]))
+            parts_d.append(np.full(k, hubs[j]))
+    parts_s.append(np.repeat(hubs, 700))
+    parts_d.append(rng.integers(12, n, 12 * 700))
+    parts_s.append(rng.integers(12, n, 40000))
+    parts_d.append(rng.integers(12, n, 40000))
+    parts_s.append(rng.integers(12, 400, 30000))  # mid-size buckets among the next tier
+    parts_d.append(rng.integers(12, 400, 30000))
+    src = np.concatenate(parts_s).astype(np.int32)
+    dst = np.concatenate(parts_d).astype(np.int32)
+    perm = rng.permutation(src.size)
+    return src[perm], dst[perm], n
+
+
+CSR_CASES = [("rmat13", lambda: (*graphgen.rmat(13, 12, 21).edges(), 1 << 13)),
+             ("repeat_heavy", _repeat_heavy_pairs),
+             ("er_sparse", lambda: (*graphgen.er(30000, 20000, 22).edges(), 30000))]
+
+
+@pytest.mark.parametrize("name,make", CSR_CASES, ids=[c[0] for c in CSR_CASES])
+def test_csr_structure(tc, name, make):
+    """The oriented CSR: vertices relabelled by rank in the (count, id) order, each undirected edge stored once
     from its lower to its higher rank, rows ascending, 16-byte aligned and padded with the id n."""
-    spec = graphgen.rmat(13, 12, 21)
-    hs, hd = spec.edges()
-    g = tc.tc_load_edges(hs, hd, spec.n)
+    hs, hd, n = make()
+    g = tc.tc_load_edges(hs, hd, n)
     try:
         tc.tc_build(g)
         off, col, perm = tc.tc_copy_csr(g)
         info = tc.tc_graph_get_info(g)
+        T = tc.tc_count(g)
     finally:
         tc.tc_free(g)
-    n = spec.n
+    assert T == oracle.count(hs, hd, n)[0]
     lo = np.minimum(hs, hd)
     hi = np.maximum(hs, hd)
     keep = lo != hi
@@ -233,7 +263,7 @@ def test_csr_structure(tc):
     dplus = np.bincount(rows[real], minlength=n)
     assert np.all(pads_per_row < 4) and np.all(np.diff(off) == dplus + pads_per_row)
     assert np.all(col[real] > rows[real])
-    for r in np.flatnonzero(dplus > 1)[:3000]:
+    for r in np.flatnonzero(dplus > 1)[-3000:]:
         seg = col[off[r]:off[r] + dplus[r]]
         assert np.all(np.diff(seg) > 0) and np.all(col[off[r] + dplus[r]:off[r + 1]] == n)
     a, b = perm[rows[real]].astype(np.int64), perm[col[real]].astype(np.int64)
