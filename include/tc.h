@@ -345,6 +345,11 @@ typedef struct tc_tuning {
                                                           segmented-intersection kernel (tc_count_intersect) when
                                                           1000 * num_wedges <= this * num_edges, i.e. when it has
                                                           few candidate 2-paths per edge; 0: never.  >= 0 */
+  int64_t bucket_max_pairs;                            /* tc_build groups the pairs by source in per-source buckets
+                                                          sorted on chip for graphs of at most this many input pairs,
+                                                          and by a radix sort of all pairs above it (the buckets'
+                                                          random accesses stop fitting in L2); 0: always buckets.
+                                                          >= 0 */
 } tc_tuning;
 
 /* tc_set_tuning — replace the table (TC_ERR_INVALID_ARG if malformed).  Applies to graphs built afterwards. */

@@ -51,7 +51,7 @@ class tc_tuning(ctypes.Structure):
                 ("batch_warp_max_edges", ctypes.c_int64),
                 ("class_max_edges", ctypes.c_int64 * TC_TUNING_MAX_CLASSES),
                 ("block_min_work", ctypes.c_int64 * TC_TUNING_MAX_CLASSES),
-                ("isect_max_wedges_milli", ctypes.c_int64)]
+                ("isect_max_wedges_milli", ctypes.c_int64), ("bucket_max_pairs", ctypes.c_int64)]
 
 
 class tc_server_config(ctypes.Structure):
@@ -177,18 +177,23 @@ def _apply_tuning_file(lib, path: str = TUNING_FILE) -> bool:
         props = torch.cuda.get_device_properties(torch.cuda.current_device())
         if data.get("device") != props.name or int(data.get("sms", -1)) != props.multi_processor_count:
             return False
+        cur = tc_tuning()
+        lib.tc_get_tuning(ctypes.byref(cur))
         t = _tuning_struct(data["classes"], data.get("batch_warp_max_edges", 1 << 25),
-                           data.get("isect_max_wedges_milli", 0))
+                           data.get("isect_max_wedges_milli", 0),
+                           data.get("bucket_max_pairs", cur.bucket_max_pairs))
         return lib.tc_set_tuning(ctypes.byref(t)) == TC_OK
     except Exception:
         return False
 
 
-def _tuning_struct(classes, batch_warp_max_edges: int = 1 << 25, isect_max_wedges_milli: int = 0) -> "tc_tuning":
+def _tuning_struct(classes, batch_warp_max_edges: int = 1 << 25, isect_max_wedges_milli: int = 0,
+                   bucket_max_pairs: int = 1 << 29) -> "tc_tuning":
     t = tc_tuning()
     t.num_classes = len(classes)
     t.batch_warp_max_edges = int(batch_warp_max_edges)
     t.isect_max_wedges_milli = int(isect_max_wedges_milli)
+    t.bucket_max_pairs = int(bucket_max_pairs)
     for i, (max_edges, work) in enumerate(classes):
         t.class_max_edges[i] = int(max_edges)
         t.block_min_work[i] = int(work)
@@ -196,9 +201,9 @@ def _tuning_struct(classes, batch_warp_max_edges: int = 1 << 25, isect_max_wedge
 
 
 def tc_set_tuning(classes, batch_warp_max_edges: Optional[int] = None,
-                  isect_max_wedges_milli: Optional[int] = None) -> None:
-    """classes: [(max_edges, block_min_work), ...] with ascending max_edges; batch_warp_max_edges and
-    isect_max_wedges_milli: keep the current values if None."""
+                  isect_max_wedges_milli: Optional[int] = None, bucket_max_pairs: Optional[int] = None) -> None:
+    """classes: [(max_edges, block_min_work), ...] with ascending max_edges; batch_warp_max_edges,
+    isect_max_wedges_milli and bucket_max_pairs: keep the current values if None."""
     if not 1 <= len(classes) <= TC_TUNING_MAX_CLASSES:
         raise ValueError("1..16 classes")
     cur = tc_tuning()
@@ -207,7 +212,9 @@ def tc_set_tuning(classes, batch_warp_max_edges: Optional[int] = None,
         batch_warp_max_edges = cur.batch_warp_max_edges
     if isect_max_wedges_milli is None:
         isect_max_wedges_milli = cur.isect_max_wedges_milli
-    t = _tuning_struct(classes, batch_warp_max_edges, isect_max_wedges_milli)
+    if bucket_max_pairs is None:
+        bucket_max_pairs = cur.bucket_max_pairs
+    t = _tuning_struct(classes, batch_warp_max_edges, isect_max_wedges_milli, bucket_max_pairs)
     _check(load_library().tc_set_tuning(ctypes.byref(t)))
 
 
@@ -215,6 +222,12 @@ def tc_get_tuning():
     t = tc_tuning()
     _check(load_library().tc_get_tuning(ctypes.byref(t)))
     return [(int(t.class_max_edges[i]), int(t.block_min_work[i])) for i in range(t.num_classes)]
+
+
+def tc_get_bucket_max_pairs() -> int:
+    t = tc_tuning()
+    _check(load_library().tc_get_tuning(ctypes.byref(t)))
+    return int(t.bucket_max_pairs)
 
 
 def tc_get_isect_max_wedges_milli() -> int:

@@ -912,6 +912,7 @@ tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* p
   const int64_t n1 = n > 0 ? n : 1;
   const uint64_t sentinel = (1ull << (2 * B)) - 1ull;
   tc_status st = TC_OK;
+  const bool buckets = peel_rounds < 0 && use_buckets(M);
   Buf alt, part, counters, odeg, ukeys, rkeys, rkeys_alt, rank, rcount, ustart, plen;
   int64_t m = 0;
   BinCounters hb{};
@@ -941,7 +942,7 @@ tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* p
       while (dbits < 32 && (1ll << dbits) <= (int64_t)maxdeg) ++dbits;
       uint64_t* rs = nullptr;
       if ((st = radix_sort_u64(a, rkeys.as<uint64_t>(), rkeys_alt.as<uint64_t>(), n, B, B + dbits, &rs, s))) break;
-      if (peel_rounds < 0 && (st = buf_alloc(a, rcount, (size_t)n * 4, s))) break;
+      if (buckets && (st = buf_alloc(a, rcount, (size_t)n * 4, s))) break;
       k_rank<<<grid_for(n, 256), 256, 0, s>>>(rs, n, B, rank.as<int32_t>(), g->perm.as<int32_t>(),
                                               rcount.as<int32_t>());
       if ((st = launched("k_rank"))) break;
@@ -950,13 +951,13 @@ tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* p
     }
     buf_release(a, g->indeg, s);
 
-    if (peel_rounds < 0) {  // the default: bucketed orientation
+    if (buckets) {  // the default: bucketed orientation
       if ((st = bucket_csr(g, rank.as<int32_t>(), rcount.as<int32_t>(), odeg, &m, &total_padded, s))) break;
       buf_release(a, rank, s);
       buf_release(a, rcount, s);
       g->m = m;
       g->csr_entries = total_padded;
-    } else {  // the sort path (needed by pruning, which works on the sorted distinct keys)
+    } else {  // the sort path (for very large inputs, and for pruning, which works on the sorted distinct keys)
       // ---- relabel, sort, unique: ukeys = distinct (rank s << B) | rank d with s < d, sorted ----
       if (M > 0) {
         uint64_t* sorted = nullptr;

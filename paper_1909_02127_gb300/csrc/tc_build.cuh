@@ -14,4 +14,7 @@ namespace tc {
 // was removed.
 tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* ps, cudaStream_t s);
 
+// Whether tc_build groups `pairs` input pairs by per-source buckets (true) or by a radix sort (the tuning table).
+bool use_buckets(int64_t pairs);
+
 }  // namespace tc

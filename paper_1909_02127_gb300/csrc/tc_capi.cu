@@ -24,7 +24,8 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 namespace {
 std::mutex g_tuning_mutex;
 // Built-in default, measured on GB300: graphs up to ~2^25 edges run fastest with every source in the warp bin;
-// larger ones with heavy sources (w(u) > 2^15) spread over a whole block.
+// larger ones with heavy sources (w(u) > 2^15) spread over a whole block; the build groups pairs in per-source
+// buckets up to 2^29 input pairs.
 tc_tuning g_tuning = [] {
   tc_tuning t{};
   t.num_classes = 2;
@@ -33,6 +34,7 @@ tc_tuning g_tuning = [] {
   t.class_max_edges[1] = int64_t(1) << 62;
   t.block_min_work[1] = int64_t(1) << 15;
   t.batch_warp_max_edges = int64_t(1) << 25;
+  t.bucket_max_pairs = int64_t(1) << 29;  // measured: buckets faster up to R-MAT 25 (2^29 pairs), sort at 2^30
   return t;
 }();
 }  // namespace
@@ -51,6 +53,11 @@ bool use_intersection(const tc_graph* g) {
   }
   if (r <= 0 || g->m <= 0) return false;
   return (long double)g->wedges * 1000.0L <= (long double)r * (long double)g->m;
+}
+
+bool use_buckets(int64_t pairs) {
+  std::lock_guard<std::mutex> lk(g_tuning_mutex);
+  return g_tuning.bucket_max_pairs <= 0 || pairs <= g_tuning.bucket_max_pairs;
 }
 
 int64_t block_min_work_for(int64_t m) {
@@ -187,8 +194,8 @@ TC_API tc_status tc_set_tuning(const tc_tuning* t) {
     set_error("tc_set_tuning: num_classes must be in 1..TC_TUNING_MAX_CLASSES");
     return TC_ERR_INVALID_ARG;
   }
-  if (t->isect_max_wedges_milli < 0) {
-    set_error("tc_set_tuning: isect_max_wedges_milli must be >= 0");
+  if (t->isect_max_wedges_milli < 0 || t->bucket_max_pairs < 0) {
+    set_error("tc_set_tuning: isect_max_wedges_milli and bucket_max_pairs must be >= 0");
     return TC_ERR_INVALID_ARG;
   }
   for (int i = 0; i < t->num_classes; ++i) {

@@ -231,19 +231,26 @@ CSR_CASES = [("rmat13", lambda: (*graphgen.rmat(13, 12, 21).edges(), 1 << 13)),
              ("er_sparse", lambda: (*graphgen.er(30000, 20000, 22).edges(), 30000))]
 
 
+@pytest.mark.parametrize("path", ["buckets", "sort"])
 @pytest.mark.parametrize("name,make", CSR_CASES, ids=[c[0] for c in CSR_CASES])
-def test_csr_structure(tc, name, make):
+def test_csr_structure(tc, name, make, path):
     """The oriented CSR: vertices relabelled by rank in the (count, id) order, each undirected edge stored once
-    from its lower to its higher rank, rows ascending, 16-byte aligned and padded with the id n."""
+    from its lower to its higher rank, rows ascending, 16-byte aligned and padded with the id n.  Both ways of
+    grouping the pairs (per-source buckets, radix sort) give the same CSR."""
     hs, hd, n = make()
-    g = tc.tc_load_edges(hs, hd, n)
+    saved = tc.tc_get_bucket_max_pairs()
+    tc.tc_set_tuning(tc.tc_get_tuning(), bucket_max_pairs=0 if path == "buckets" else 1)
     try:
-        tc.tc_build(g)
-        off, col, perm = tc.tc_copy_csr(g)
-        info = tc.tc_graph_get_info(g)
-        T = tc.tc_count(g)
+        g = tc.tc_load_edges(hs, hd, n)
+        try:
+            tc.tc_build(g)
+            off, col, perm = tc.tc_copy_csr(g)
+            info = tc.tc_graph_get_info(g)
+            T = tc.tc_count(g)
+        finally:
+            tc.tc_free(g)
     finally:
-        tc.tc_free(g)
+        tc.tc_set_tuning(tc.tc_get_tuning(), bucket_max_pairs=saved)
     assert T == oracle.count(hs, hd, n)[0]
     lo = np.minimum(hs, hd)
     hi = np.maximum(hs, hd)
