@@ -192,9 +192,12 @@ def profiled_traffic(workload: str):
 
 def algorithmic_bytes(info: dict, grid_ctas: int) -> float:
     """Bytes the two-hop method must read once per use: offsets of every source (8(n+1)), its row N+(u) (4m), the
-    offset pair of every hop-1 target (16m), the row N+(v) of every hop-1 target (4W), one 8-byte atomic per CTA."""
+    offset pair of every hop-1 target (16m), the row N+(v) of every hop-1 target — 4 bytes per id for rows read
+    as id lists (4(W - W_dense)) and 16 bytes per 128-id quad for rows read as bitmaps (16 Q_dense) — and one
+    8-byte atomic per CTA."""
     n, m, W = info["num_vertices"], info["num_edges"], info["num_wedges"]
-    return 8.0 * (n + 1) + 4.0 * m + 16.0 * m + 4.0 * W + 8.0 * grid_ctas
+    Wd, Qd = info.get("dense_wedges", 0), info.get("dense_quads", 0)
+    return 8.0 * (n + 1) + 4.0 * m + 16.0 * m + 4.0 * (W - Wd) + 16.0 * Qd + 8.0 * grid_ctas
 
 
 def count_grid(info: dict) -> int:

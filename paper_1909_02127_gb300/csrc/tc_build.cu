@@ -622,18 +622,33 @@ struct BinCounters {
   unsigned int nw;
   int max_out;
   int pad;
+  unsigned long long dense_wedges;  // 2-paths through dense rows
+  unsigned long long dense_visits;  // quads of dense rows read per count
 };
 
-// w(u) = sum of the padded lengths of the rows of N+(u) (the entries the counting kernel reads in hop 2) and the
-// true 2-path count; sources with d+(u) >= 2 and a 2-path go to the block bin (w above the threshold) or the warp
-// bin.  Rows of up to 32 entries are summed by their own lane, longer ones by the whole warp.
+// w(u) = the hop-2 work of source u: the padded length of each id row of N+(u), and four ids' worth per quad of
+// each dense row (see k_dense_select); plus the true 2-path count.  Sources with d+(u) >= 2 and a 2-path go to
+// the block bin (w above the threshold) or the warp bin.  Rows of up to 32 entries are summed by their own lane,
+// longer ones by the whole warp.
+struct DenseInfo {
+  const int32_t* dq0;  // null: no dense rows
+  int32_t base_w;
+  int32_t wtopq;
+  int64_t n;
+  // quads of v's dense row, or 0 if v's row is an id list only
+  __device__ __forceinline__ int32_t quads(int32_t v) const {
+    if (dq0 == nullptr || v < base_w || v >= n || __ldg(&dq0[v - base_w]) < 0) return 0;
+    return wtopq - ((v + 1 - base_w) >> 7);
+  }
+};
+
 __global__ void k_bins(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                       const int32_t* __restrict__ dplus, int64_t n, int64_t block_min_work,
+                       const int32_t* __restrict__ dplus, int64_t n, int64_t block_min_work, DenseInfo di,
                        int32_t* __restrict__ list, BinCounters* __restrict__ bc) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  unsigned long long wsum = 0, act = 0;
+  unsigned long long wsum = 0, act = 0, dw = 0, dv = 0;
   int dmax = 0;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
     const int64_t u = base + threadIdx.x;
@@ -643,12 +658,18 @@ __global__ void k_bins(const int64_t* __restrict__ off, const int32_t* __restric
       d = dplus[u];
       b = off[u];
     }
-    int64_t wpad = 0, wtrue = 0;
+    int64_t wpad = 0, wtrue = 0, wdense = 0, qdense = 0;
     if (d <= 32) {
       for (int64_t j = b; j < b + d; ++j) {
-        const int32_t dv = dplus[col[j]];
-        wpad += (dv + 3) & ~3;
-        wtrue += dv;
+        const int32_t v = col[j];
+        const int32_t dv_ = dplus[v];
+        const int32_t q = di.quads(v);
+        wpad += q > 0 ? 4 * q : (dv_ + 3) & ~3;
+        wtrue += dv_;
+        if (q > 0) {
+          wdense += dv_;
+          qdense += q;
+        }
       }
     }
     unsigned longs = __ballot_sync(kFull, d > 32);
@@ -657,20 +678,32 @@ __global__ void k_bins(const int64_t* __restrict__ off, const int32_t* __restric
       longs &= longs - 1;
       const int64_t rb = __shfl_sync(kFull, b, k);
       const int32_t rd = __shfl_sync(kFull, d, k);
-      int64_t p = 0, t = 0;
+      int64_t p = 0, t = 0, wd = 0, qd = 0;
       for (int32_t j = lane; j < rd; j += 32) {
-        const int32_t dv = dplus[col[rb + j]];
-        p += (dv + 3) & ~3;
-        t += dv;
+        const int32_t v = col[rb + j];
+        const int32_t dv_ = dplus[v];
+        const int32_t q = di.quads(v);
+        p += q > 0 ? 4 * q : (dv_ + 3) & ~3;
+        t += dv_;
+        if (q > 0) {
+          wd += dv_;
+          qd += q;
+        }
       }
       p = warp_sum(p);
       t = warp_sum(t);
+      wd = warp_sum(wd);
+      qd = warp_sum(qd);
       if (lane == k) {
         wpad = p;
         wtrue = t;
+        wdense = wd;
+        qdense = qd;
       }
     }
     wsum += (unsigned long long)wtrue;
+    dw += (unsigned long long)wdense;
+    dv += (unsigned long long)qdense;
     if (d > dmax) dmax = d;
     const bool keep = d >= 2 && wtrue > 0;
     const bool blk = keep && wpad > block_min_work;
@@ -690,11 +723,61 @@ __global__ void k_bins(const int64_t* __restrict__ off, const int32_t* __restric
   }
   wsum = warp_sum(wsum);
   act = warp_sum(act);
+  dw = warp_sum(dw);
+  dv = warp_sum(dv);
   for (int o = 16; o > 0; o >>= 1) dmax = max(dmax, __shfl_xor_sync(kFull, dmax, o));
   if (lane == 0) {
     atomicAdd(&bc->wedges, wsum);
     atomicAdd(&bc->active, act);
+    if (dw) atomicAdd(&bc->dense_wedges, dw);
+    if (dv) atomicAdd(&bc->dense_visits, dv);
     atomicMax(&bc->max_out, dmax);
+  }
+}
+
+// ---- dense rows -------------------------------------------------------------------------------------------------
+// Row v (in the warp window) is kept as a bitmap too when its bitmap quads cover no more words than it has entries.
+__global__ void k_dense_select(const int32_t* __restrict__ dplus, int64_t n, int32_t base_w, int32_t wtopq,
+                               int32_t* __restrict__ nq) {
+  const int64_t wn = n - base_w;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < wn; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = base_w + i;
+    const int32_t d = dplus[v];
+    const int32_t q = wtopq - (int32_t)((v + 1 - base_w) >> 7);
+    nq[i] = (d >= kDenseMinDegree && 4 * (int64_t)q <= d) ? q : 0;
+  }
+}
+
+// dq0[i] = first quad of the dense row of base_w + i, or -1; qoff is the exclusive scan of the quad counts.
+__global__ void k_dense_index(const int32_t* __restrict__ nq, const int64_t* __restrict__ qoff, int64_t wn,
+                              int32_t* __restrict__ dq0, unsigned long long* __restrict__ rows) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < wn; i += (int64_t)gridDim.x * blockDim.x) {
+    const bool on = nq[i] > 0;
+    dq0[i] = on ? (int32_t)qoff[i] : -1;
+    const unsigned b = __ballot_sync(__activemask(), on);
+    if (on && (threadIdx.x & 31) == __ffs(b) - 1) atomicAdd(rows, (unsigned long long)__popc(b));
+  }
+}
+
+// One warp per window vertex: the bits of N+(v) into its (zeroed) dense row.
+__global__ void k_dense_fill(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                             const int32_t* __restrict__ dplus, int64_t n, int32_t base_w,
+                             const int32_t* __restrict__ dq0, uint32_t* __restrict__ words) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wn = n - base_w;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp0; i < wn; i += nwarps) {
+    const int32_t q0 = dq0[i];
+    if (q0 < 0) continue;
+    const int64_t v = base_w + i;
+    const int64_t beg = off[v];
+    const int32_t d = dplus[v];
+    const int64_t w0 = 4 * (int64_t)q0 - 4 * ((v + 1 - base_w) >> 7);  // word of window word 0, relative
+    for (int32_t j = lane; j < d; j += 32) {
+      const int32_t b = col[beg + j] - base_w;
+      atomicOr(&words[w0 + (b >> 5)], 1u << (b & 31));
+    }
   }
 }
 
@@ -913,7 +996,7 @@ tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* p
   const uint64_t sentinel = (1ull << (2 * B)) - 1ull;
   tc_status st = TC_OK;
   const bool buckets = peel_rounds < 0 && use_buckets(M);
-  Buf alt, part, counters, odeg, ukeys, rkeys, rkeys_alt, rank, rcount, ustart, plen;
+  Buf alt, part, counters, odeg, ukeys, rkeys, rkeys_alt, rank, rcount, ustart, plen, dnq, dqoff;
   int64_t m = 0;
   BinCounters hb{};
   int64_t total_padded = 0;
@@ -1032,12 +1115,39 @@ tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* p
       buf_release(a, ukeys, s);
     }
 
+    // ---- dense rows: selection and quad offsets (before the bins, which charge their cost) ----
+    const CsrView vw = g->view();
+    const int64_t wn = n - vw.base_w;
+    unsigned long long* drows = reinterpret_cast<unsigned long long*>(counters.as<char>() + 48);
+    int64_t dquads = 0;
+    unsigned long long hrows = 0;
+    DenseInfo di{nullptr, vw.base_w, vw.wtopq, n};
+    if (n > 0 && m > 0) {
+      if ((st = buf_alloc(a, dnq, (size_t)wn * 4, s))) break;
+      if ((st = buf_alloc(a, dqoff, (size_t)(wn + 1) * 8, s))) break;
+      if ((st = buf_alloc(a, g->dq0, (size_t)wn * 4, s))) break;
+      if ((st = cuda_status(cudaMemsetAsync(drows, 0, 8, s), "memset dense rows"))) break;
+      k_dense_select<<<grid_for(wn, 256), 256, 0, s>>>(odeg.as<int32_t>(), n, vw.base_w, vw.wtopq,
+                                                       dnq.as<int32_t>());
+      if ((st = launched("k_dense_select"))) break;
+      if ((st = exclusive_scan_i32_to_i64(a, dnq.as<int32_t>(), dqoff.as<int64_t>(), wn, s))) break;
+      k_dense_index<<<grid_for(wn, 256), 256, 0, s>>>(dnq.as<int32_t>(), dqoff.as<int64_t>(), wn,
+                                                      g->dq0.as<int32_t>(), drows);
+      if ((st = launched("k_dense_index"))) break;
+      if ((st = cuda_status(cudaMemcpyAsync(&dquads, dqoff.as<int64_t>() + wn, 8, cudaMemcpyDeviceToHost, s),
+                            "copy dense quads")))
+        break;
+      if ((st = cuda_status(cudaMemcpyAsync(&hrows, drows, 8, cudaMemcpyDeviceToHost, s), "copy dense rows")))
+        break;
+      di.dq0 = g->dq0.as<int32_t>();
+    }
+
     // ---- bins ----
     if ((st = buf_alloc(a, g->list, (size_t)n1 * 4, s))) break;
     if ((st = cuda_status(cudaMemsetAsync(counters.p, 0, sizeof(BinCounters), s), "memset bins"))) break;
     if (n > 0) {
       k_bins<<<grid_for(n, 256), 256, 0, s>>>(g->off.as<int64_t>(), g->col.as<int32_t>(), odeg.as<int32_t>(), n,
-                                              block_min_work_for(m), g->list.as<int32_t>(),
+                                              block_min_work_for(m), di, g->list.as<int32_t>(),
                                               counters.as<BinCounters>());
       if ((st = launched("k_bins"))) break;
     }
@@ -1045,14 +1155,29 @@ tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* p
                           "copy bins")))
       break;
     if ((st = cuda_status(cudaStreamSynchronize(s), "sync bins"))) break;
+    if (hrows > 0) {
+      if ((st = buf_alloc(a, g->dense, (size_t)dquads * 16, s))) break;
+      if ((st = cuda_status(cudaMemsetAsync(g->dense.p, 0, (size_t)dquads * 16, s), "memset dense"))) break;
+      k_dense_fill<<<grid_for(wn * 32, 256), 256, 0, s>>>(g->off.as<int64_t>(), g->col.as<int32_t>(),
+                                                           odeg.as<int32_t>(), n, vw.base_w, g->dq0.as<int32_t>(),
+                                                           g->dense.as<uint32_t>());
+      if ((st = launched("k_dense_fill"))) break;
+      g->dense_rows = (int64_t)hrows;
+      g->dense_quads = dquads;
+    } else {
+      buf_release(a, g->dq0, s);
+    }
   } while (0);
 
-  for (Buf* b : {&alt, &part, &counters, &odeg, &ukeys, &rkeys, &rkeys_alt, &rank, &rcount, &ustart, &plen})
+  for (Buf* b : {&alt, &part, &counters, &odeg, &ukeys, &rkeys, &rkeys_alt, &rank, &rcount, &ustart, &plen, &dnq,
+                 &dqoff})
     buf_release(a, *b, s);
   buf_release(a, g->keys, s);
   buf_release(a, g->indeg, s);
   if (st != TC_OK) return st;
   g->wedges = (int64_t)hb.wedges;
+  g->dense_wedges = g->dense_rows > 0 ? (int64_t)hb.dense_wedges : 0;
+  g->dense_visits = g->dense_rows > 0 ? (int64_t)hb.dense_visits : 0;
   g->active = (int64_t)hb.active;
   g->nb = hb.nb;
   g->nw = hb.nw;

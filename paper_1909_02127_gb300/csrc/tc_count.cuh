@@ -45,6 +45,7 @@ struct Closing {
   const int32_t* low;    // kLowSearch: N+(u) entries below base (sorted, global); kLowHash: open-addressing table
   int32_t nlow;          // kLowSearch: number of entries; kLowHash: table mask
   uint32_t cap;          // bitmap size in bits: bit `cap` exists and is never set
+  int32_t delta;         // quads from this bitmap's base to the warp window's base (dense rows line up there)
   __device__ __forceinline__ uint32_t bit(uint32_t t) const {
     return __funnelshift_r(bm[t >> 5], 0u, t) & 1u;  // shift amount taken mod 32
   }
@@ -218,6 +219,53 @@ __device__ __forceinline__ uint32_t walk(const Rows& r, int R, uint32_t x0, uint
   return hits;
 }
 
+// Walk quads [x0, x1) of the concatenated dense rows 0..R-1 (row k: r.q0[k] = its first quad in `dense`, r.v[k] =
+// the quad of the source bitmap its first quad lines up with) with one warp: each quad is 128 ids, and its closing
+// tests are four ANDs with the source's bitmap words and four population counts.
+__device__ __forceinline__ uint32_t dense_walk(const Rows& r, int R, uint32_t x0, uint32_t x1,
+                                               const int4* __restrict__ dense, const uint4* bm4) {
+  uint32_t hits = 0;
+  if (x0 >= x1) return 0;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  int a = 0, b = R;  // cur = last row with P <= x0
+  while (a < b) {
+    const int mid = (a + b) >> 1;
+    if (r.P[mid] <= x0)
+      a = mid + 1;
+    else
+      b = mid;
+  }
+  int cur = a - 1;
+  for (uint32_t base = x0; base < x1; base += 32) {
+    const int j = cur + (lane == 0 ? 32 : lane);
+    uint32_t bit = 0;
+    if (j < R) {
+      const uint32_t pj = r.P[j];
+      if (pj <= base + 32) bit = 1u << (pj - base - 1);
+    }
+    const uint32_t starts = __reduce_or_sync(kFull, bit);
+    const uint32_t x = base + lane;
+    if (x < x1) {
+      const int own = cur + __popc(starts & lt);
+      const uint32_t qi = x - r.P[own];
+      const int4 q = __ldg(&dense[r.q0[own] + qi]);
+      const uint4 w = bm4[r.v[own] + qi];
+      hits += (__popc((uint32_t)q.x & w.x) + __popc((uint32_t)q.y & w.y)) +
+              (__popc((uint32_t)q.z & w.z) + __popc((uint32_t)q.w & w.w));
+    }
+    cur += __popc(starts);
+  }
+  return hits;
+}
+
+// Is v's row also stored as a dense bitmap?  Returns its first quad or -1 (always -1 outside count mode).
+template <int MODE>
+__device__ __forceinline__ int32_t dense_row(const CsrView& g, int32_t v) {
+  if (MODE != kModeCount || g.dq0 == nullptr || v < g.base_w || v >= g.n) return -1;
+  return __ldg(&g.dq0[v - g.base_w]);
+}
+
 // Descriptor of row v (v = n is the pad id: no row).
 struct RowOf {
   uint32_t q0, nq;
@@ -264,7 +312,10 @@ __device__ __forceinline__ uint32_t warp_hops(const CsrView& g, int64_t beg, int
   for (int64_t vb = 0; vb < len; vb += 32) {
     const int64_t j = vb + lane;
     const int32_t v = j < len ? __ldg(&g.col[beg + j]) : (int32_t)g.n;
-    const RowOf ro = row_of(g.off, v, g.n);
+    const int32_t dq = dense_row<MODE>(g, v);
+    const bool dense = dq >= 0;
+    RowOf ro = row_of(g.off, v, g.n);
+    if (dense) ro.nq = 0;
     const bool is_long = ro.nq >= (uint32_t)kLongQuads;
     unsigned longs = __ballot_sync(kFull, is_long);
     while (longs) {
@@ -290,6 +341,24 @@ __device__ __forceinline__ uint32_t warp_hops(const CsrView& g, int64_t beg, int
       hits += walk<MODE>(r, __popc(shorts), 0, Q, col4, c, sk, (int32_t)g.n);
       __syncwarp();
     }
+    if (MODE == kModeCount) {
+      const unsigned dmask = __ballot_sync(kFull, dense);
+      if (dmask) {
+        const int32_t sq = dense ? (v + 1 - g.base_w) >> 7 : 0;
+        const uint32_t nq = dense ? (uint32_t)(g.wtopq - sq) : 0u;
+        const uint32_t incl = warp_inclusive_scan(nq);
+        const uint32_t Q = __shfl_sync(kFull, incl, 31);
+        if (dense) {
+          const int k = __popc(dmask & lt);
+          r.q0[k] = (uint32_t)dq;
+          r.P[k] = incl - nq;
+          r.v[k] = sq + c.delta;
+        }
+        __syncwarp();
+        hits += dense_walk(r, __popc(dmask), 0, Q, g.dense, reinterpret_cast<const uint4*>(c.bm));
+        __syncwarp();
+      }
+    }
   }
   return hits;
 }
@@ -309,15 +378,15 @@ __device__ __forceinline__ uint32_t warp_source(int32_t u, const CsrView& g, uin
   constexpr uint32_t cap = (uint32_t)kWarpBitmapBits, lmask = (uint32_t)kWarpLowSlots - 1;
   uint32_t hits;
   if (nlow == 0) {
-    hits = warp_hops<MODE>(g, beg, len, Closing<kLowNone>{bm, g.base_w, row, 0, cap}, r, sk);
+    hits = warp_hops<MODE>(g, beg, len, Closing<kLowNone>{bm, g.base_w, row, 0, cap, 0}, r, sk);
   } else if (nlow <= (uint32_t)kWarpLowSlots / 2) {
     low_insert(row, (int)nlow, ltab, lmask, lane, 32);
     __syncwarp();
-    hits = warp_hops<MODE>(g, beg, len, Closing<kLowHash>{bm, g.base_w, ltab, (int32_t)lmask, cap}, r, sk);
+    hits = warp_hops<MODE>(g, beg, len, Closing<kLowHash>{bm, g.base_w, ltab, (int32_t)lmask, cap, 0}, r, sk);
     __syncwarp();
     for (int i = lane; i < kWarpLowSlots; i += 32) ltab[i] = -1;
   } else {
-    hits = warp_hops<MODE>(g, beg, len, Closing<kLowSearch>{bm, g.base_w, row, (int32_t)nlow, cap}, r, sk);
+    hits = warp_hops<MODE>(g, beg, len, Closing<kLowSearch>{bm, g.base_w, row, (int32_t)nlow, cap, 0}, r, sk);
   }
   __syncwarp();
   mark_row(row, len, g.n, g.base_w, bm, false, lane, 32);
@@ -335,6 +404,7 @@ struct BlockRows {
   uint32_t* lnq;
   int32_t* lv;
   Rows sr;
+  Rows dr;  // dense rows (count mode)
   uint32_t* next;
   int32_t* ltab;
 };
@@ -348,13 +418,27 @@ __device__ __forceinline__ uint32_t block_hops(const CsrView& g, int64_t beg, in
   for (int64_t cb = 0; cb < len; cb += kBlockRows) {
     const int64_t j = cb + tid;
     const int32_t v = j < len ? __ldg(&g.col[beg + j]) : (int32_t)g.n;
-    const RowOf ro = row_of(g.off, v, g.n);
+    const int32_t dq = dense_row<MODE>(g, v);
+    const bool dense = dq >= 0;
+    RowOf ro = row_of(g.off, v, g.n);
+    if (dense) ro.nq = 0;
     const bool is_long = ro.nq >= (uint32_t)kLongQuads;
     const bool is_short = ro.nq > 0 && !is_long;
-    uint32_t NL, R, Q;
+    uint32_t NL, R, Q, ND = 0, QD = 0;
     const uint32_t lrank = block_exclusive_scan<uint32_t>(is_long ? 1u : 0u, ws, &NL);
     const uint32_t srank = block_exclusive_scan<uint32_t>(is_short ? 1u : 0u, ws, &R);
     const uint32_t pre = block_exclusive_scan<uint32_t>(is_short ? ro.nq : 0u, ws, &Q);
+    if (MODE == kModeCount) {
+      const int32_t sq = dense ? (v + 1 - g.base_w) >> 7 : 0;
+      const uint32_t nqd = dense ? (uint32_t)(g.wtopq - sq) : 0u;
+      const uint32_t drank = block_exclusive_scan<uint32_t>(dense ? 1u : 0u, ws, &ND);
+      const uint32_t dpre = block_exclusive_scan<uint32_t>(nqd, ws, &QD);
+      if (dense) {
+        br.dr.q0[drank] = (uint32_t)dq;
+        br.dr.P[drank] = dpre;
+        br.dr.v[drank] = sq + c.delta;
+      }
+    }
     if (is_long) {
       br.lq0[lrank] = ro.q0;
       br.lnq[lrank] = ro.nq;
@@ -379,6 +463,11 @@ __device__ __forceinline__ uint32_t block_hops(const CsrView& g, int64_t beg, in
     const uint32_t per = (Q + kWarpsPerCTA - 1) / kWarpsPerCTA;
     const uint32_t x0 = min(Q, (uint32_t)warp * per), x1 = min(Q, x0 + per);
     hits += walk<MODE>(br.sr, (int)R, x0, x1, col4, c, sk, (int32_t)g.n);
+    if (MODE == kModeCount && QD > 0) {  // dense rows: equal shares of their quads
+      const uint32_t dper = (QD + kWarpsPerCTA - 1) / kWarpsPerCTA;
+      const uint32_t d0 = min(QD, (uint32_t)warp * dper), d1 = min(QD, d0 + dper);
+      hits += dense_walk(br.dr, (int)ND, d0, d1, g.dense, reinterpret_cast<const uint4*>(c.bm));
+    }
     __syncthreads();
   }
   return hits;
@@ -400,14 +489,14 @@ __device__ __forceinline__ uint32_t block_source(int32_t u, const CsrView& g, ui
   constexpr uint32_t cap = (uint32_t)kBlockBitmapBits, lmask = (uint32_t)kBlockLowSlots - 1;
   uint32_t hits;
   if (nlow == 0) {
-    hits = block_hops<MODE>(g, beg, len, Closing<kLowNone>{bm, g.base_b, row, 0, cap}, br, ws, sk);
+    hits = block_hops<MODE>(g, beg, len, Closing<kLowNone>{bm, g.base_b, row, 0, cap, g.dq_delta}, br, ws, sk);
   } else if (nlow <= (uint32_t)kBlockLowSlots / 2) {
     low_insert(row, (int)nlow, br.ltab, lmask, tid, kCountThreads);
     __syncthreads();
-    hits = block_hops<MODE>(g, beg, len, Closing<kLowHash>{bm, g.base_b, br.ltab, (int32_t)lmask, cap}, br, ws, sk);
+    hits = block_hops<MODE>(g, beg, len, Closing<kLowHash>{bm, g.base_b, br.ltab, (int32_t)lmask, cap, g.dq_delta}, br, ws, sk);
     for (int i = tid; i < kBlockLowSlots; i += kCountThreads) br.ltab[i] = -1;  // block_hops ended with a barrier
   } else {
-    hits = block_hops<MODE>(g, beg, len, Closing<kLowSearch>{bm, g.base_b, row, (int32_t)nlow, cap}, br, ws, sk);
+    hits = block_hops<MODE>(g, beg, len, Closing<kLowSearch>{bm, g.base_b, row, (int32_t)nlow, cap, g.dq_delta}, br, ws, sk);
   }
   mark_row(row, len, g.n, g.base_b, bm, false, tid, kCountThreads);
   if (MODE == kModeVertex) {
@@ -422,9 +511,10 @@ __device__ __forceinline__ uint32_t block_source(int32_t u, const CsrView& g, ui
 constexpr int kWarpBitmapWords = kWarpBitmapBits / 32 + kBitmapSlackWords;
 constexpr int kBlockBitmapWords = kBlockBitmapBits / 32 + kBitmapSlackWords;
 constexpr int kWarpRowWords = 32 + 33 + 32;                        // q0, P, v
-constexpr int kWarpRegionWords = kWarpBitmapWords + kWarpRowWords + kWarpLowSlots;
+constexpr int kWarpRegionWords = (kWarpBitmapWords + kWarpRowWords + kWarpLowSlots + 3) & ~3;  // 16-byte aligned
 constexpr int kWarpSmem = kWarpsPerCTA * kWarpRegionWords * 4;
-constexpr int kBlockRowWords = 3 * kBlockRows + 2 * kBlockRows + (kBlockRows + 1) + 1;  // long, short, counter
+constexpr int kBlockRowWords = 3 * kBlockRows + 2 * kBlockRows + (kBlockRows + 1) + 1 + 3 * kBlockRows;
+// (long, short, counter, dense)
 constexpr int kBlockSmem = (kBlockBitmapWords + kBlockRowWords + kBlockLowSlots) * 4;
 constexpr int kCountSmem = kBlockSmem > kWarpSmem ? kBlockSmem : kWarpSmem;
 
@@ -450,6 +540,9 @@ __device__ __forceinline__ BlockRows block_rows(uint32_t* smem) {
   b.sr.v = reinterpret_cast<int32_t*>(p + 4 * kBlockRows);
   b.sr.P = p + 5 * kBlockRows;
   b.next = p + 6 * kBlockRows + 1;
+  b.dr.q0 = p + 6 * kBlockRows + 2;
+  b.dr.v = reinterpret_cast<int32_t*>(p + 7 * kBlockRows + 2);
+  b.dr.P = p + 8 * kBlockRows + 2;
   b.ltab = reinterpret_cast<int32_t*>(p + kBlockRowWords);
   return b;
 }

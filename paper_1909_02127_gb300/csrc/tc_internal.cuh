@@ -71,9 +71,14 @@ constexpr int kLongQuads = 16;                     // rows of >= 16 quads (64 id
 int64_t block_min_work_for(int64_t m);
 int64_t batch_warp_max_edges();
 
-// Per-graph view used by the counting kernels.  Vertices are relabelled by rank in the (degree, id) order, so
-// every oriented edge goes from a lower to a higher id and rows hold ascending ids.  Rows start on 16-byte
-// boundaries and are padded to a multiple of 4 entries with the id n, which no bitmap ever marks.
+// Per-graph view used by the counting kernels.  Vertices are relabelled by rank in the (input-pair count, id)
+// order, so every oriented edge goes from a lower to a higher id and rows hold ascending ids.  Rows start on
+// 16-byte boundaries and are padded to a multiple of 4 entries with the id n, which no bitmap ever marks.
+// Dense rows: a row N+(v) with v in the warp window [base_w, n) whose bitmap over its range (v, n) takes no more
+// words than it has entries is also stored as that bitmap, aligned to the windows (both bases are multiples of
+// 128, so bitmap quad q of the row lines up with quad (v + 1 - base_w) / 128 + q of a source's warp bitmap and
+// dq_delta quads further on in its block bitmap).  Counting (not per-vertex counts or listing) tests such a row by
+// ANDing words instead of looking up ids.
 struct CsrView {
   const int64_t* off;   // n+1 padded row offsets (multiples of 4)
   const int32_t* col;   // off[n] column ids (+ one spare quad)
@@ -84,8 +89,13 @@ struct CsrView {
   int32_t base_w;       // per-warp bitmap covers ids [base_w, n]
   int32_t base_b;       // per-CTA bitmap covers ids [base_b, n]
   int32_t nbw;          // batches only: block-bin sources that are run one warp each (0 or nb)
+  int32_t wtopq;        // dense rows end at window quad wtopq (the quad holding id n - 1)
+  const int32_t* dq0;   // n - base_w entries: first quad of v's dense row in `dense`, or -1; null if none
+  const int4* dense;    // dense row bitmaps, 128 ids per quad
+  int32_t dq_delta;     // (base_w - base_b) / 128
   int32_t pad;
 };
+constexpr int kDenseMinDegree = 16;  // rows with fewer entries stay id lists
 
 // ------------------------------------------------------------------------------------------------------------
 // Primitives (tc_prims.cu)
@@ -127,7 +137,13 @@ struct tc_graph {
   tc::Buf list;              // int32[n]: block bin at the front, warp bin at the back
   tc::Buf perm;              // int32[n]: perm[r] = original id of the vertex of rank r
   tc::Buf acc;               // uint64 scratch word(s) for counting: [0] total, [1..2] work cursors
+  tc::Buf dq0;               // int32[n - base_w]: dense row start (quads) or -1
+  tc::Buf dense;             // int4[dense_quads]: dense row bitmaps
+  int64_t dense_rows = 0, dense_quads = 0;       // rows stored dense; quads of storage
+  int64_t dense_wedges = 0, dense_visits = 0;    // 2-paths through dense rows; quads read for them per count
   uint64_t* host_total = nullptr;  // pinned 8-byte landing slot
+  // The bitmap windows start at a multiple of 128 ids at or above n - (bitmap bits), so they end at id n.
+  static int64_t window_base(int64_t n, int64_t bits) { return n > bits ? ((n - bits + 127) & ~int64_t(127)) : 0; }
   tc::CsrView view() const {
     tc::CsrView v;
     v.off = off.as<int64_t>();
@@ -136,9 +152,13 @@ struct tc_graph {
     v.n = n;
     v.nb = (int32_t)nb;
     v.nw = (int32_t)nw;
-    v.base_w = (int32_t)(n > tc::kWarpBitmapBits ? n - tc::kWarpBitmapBits : 0);
-    v.base_b = (int32_t)(n > tc::kBlockBitmapBits ? n - tc::kBlockBitmapBits : 0);
+    v.base_w = (int32_t)window_base(n, tc::kWarpBitmapBits);
+    v.base_b = (int32_t)window_base(n, tc::kBlockBitmapBits);
     v.nbw = 0;
+    v.wtopq = n > v.base_w ? (int32_t)(((n - 1 - v.base_w) >> 7) + 1) : 0;
+    v.dq0 = dense_rows > 0 ? dq0.as<int32_t>() : nullptr;
+    v.dense = dense.as<int4>();
+    v.dq_delta = (v.base_w - v.base_b) >> 7;
     v.pad = 0;
     return v;
   }

@@ -227,6 +227,7 @@ def _repeat_heavy_pairs():
 
 
 CSR_CASES = [("rmat13", lambda: (*graphgen.rmat(13, 12, 21).edges(), 1 << 13)),
+             ("rmat16p", lambda: (*graphgen.rmat(16, 8, 23, n=60000, permute=True).edges(), 60000)),
              ("repeat_heavy", _repeat_heavy_pairs),
              ("er_sparse", lambda: (*graphgen.er(30000, 20000, 22).edges(), 30000))]
 
@@ -277,6 +278,19 @@ def test_csr_structure(tc, name, make, path):
     np.testing.assert_array_equal(np.sort(np.minimum(a, b) * n + np.maximum(a, b)), und)
     assert info["max_out_degree"] == dplus.max()
     assert info["num_wedges"] == int(dplus[col[real]].sum())
+    # dense rows: v in the warp window (its base a multiple of 128 at or above n - 2^15) whose bitmap quads over
+    # (v, n) hold no more words than v has out-neighbours (and at least 16 of them)
+    base = ((n - (1 << 15) + 127) & ~127) if n > (1 << 15) else 0
+    wtopq = ((n - 1 - base) >> 7) + 1
+    v = np.arange(n)
+    quads = np.where(v >= base, wtopq - ((v + 1 - base) >> 7), 0)
+    dense = (v >= base) & (dplus >= 16) & (4 * quads <= dplus)
+    targets = col[real]
+    assert info["dense_rows"] == int(dense.sum())
+    assert info["dense_wedges"] == int(dplus[targets][dense[targets]].sum())
+    assert info["dense_quads"] == int(quads[targets][dense[targets]].sum())
+    if name.startswith("rmat"):
+        assert info["dense_rows"] > 0
 
 
 def test_host_and_device_inputs_and_allocators_agree(tc):
