@@ -43,8 +43,7 @@ constexpr int kPackTile = kPackThreads * kPackItems;  // 1024 pairs, <= 2048 dis
 constexpr int kPackSlots = 4096;
 constexpr int kPackProbe = 8;
 
-__device__ __forceinline__ void pack_count(int32_t* skey, int32_t* scnt, int32_t* used, int32_t* nused,
-                                           int32_t* indeg, int32_t x) {
+__device__ __forceinline__ void pack_count(int32_t* skey, int32_t* scnt, int32_t* indeg, int32_t x) {
   uint32_t s = ((uint32_t)x * 2654435761u) >> 20;  // 12 bits
   for (int p = 0; p < kPackProbe; ++p) {
     const int32_t k = skey[s];
@@ -55,7 +54,6 @@ __device__ __forceinline__ void pack_count(int32_t* skey, int32_t* scnt, int32_t
     if (k < 0) {
       const int32_t prev = atomicCAS(&skey[s], -1, x);
       if (prev == -1) {
-        used[atomicAdd(nused, 1)] = (int32_t)s;
         atomicAdd(&scnt[s], 1);
         return;
       }
@@ -74,14 +72,11 @@ __global__ void __launch_bounds__(kPackThreads) k_pack(const int32_t* __restrict
                                                        int32_t* __restrict__ indeg, uint32_t* __restrict__ err) {
   __shared__ int32_t skey[kPackSlots];
   __shared__ int32_t scnt[kPackSlots];
-  __shared__ int32_t used[2 * kPackTile];
-  __shared__ int32_t nused;
   const uint64_t sentinel = (1ull << (2 * B)) - 1ull;
   for (int i = threadIdx.x; i < kPackSlots; i += kPackThreads) {
     skey[i] = -1;
     scnt[i] = 0;
   }
-  if (threadIdx.x == 0) nused = 0;
   __syncthreads();
   bool bad = false;
   for (int64_t tile = (int64_t)blockIdx.x * kPackTile; tile < len; tile += (int64_t)gridDim.x * kPackTile) {
@@ -94,21 +89,21 @@ __global__ void __launch_bounds__(kPackThreads) k_pack(const int32_t* __restrict
         bad = true;
       } else if (a != b) {
         key = ((uint64_t)(a < b ? a : b) << B) | (uint64_t)(a < b ? b : a);
-        pack_count(skey, scnt, used, &nused, indeg, a);
-        pack_count(skey, scnt, used, &nused, indeg, b);
+        pack_count(skey, scnt, indeg, a);
+        pack_count(skey, scnt, indeg, b);
       }
       keys[i] = key;
     }
     __syncthreads();
-    const int nu = nused;
-    for (int t = threadIdx.x; t < nu; t += kPackThreads) {
-      const int32_t slot = used[t];
-      atomicAdd(&indeg[skey[slot]], scnt[slot]);
-      skey[slot] = -1;
-      scnt[slot] = 0;
+    // flush: every occupied slot once (a scan of the table, no shared counter)
+    for (int slot = threadIdx.x; slot < kPackSlots; slot += kPackThreads) {
+      const int32_t k = skey[slot];
+      if (k >= 0) {
+        atomicAdd(&indeg[k], scnt[slot]);
+        skey[slot] = -1;
+        scnt[slot] = 0;
+      }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) nused = 0;
     __syncthreads();
   }
   if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(err, 1u);
@@ -629,21 +624,23 @@ struct BinCounters {
 // w(u) = the hop-2 work of source u: the padded length of each id row of N+(u), and four ids' worth per quad of
 // each dense row (see k_dense_select); plus the true 2-path count.  Sources with d+(u) >= 2 and a 2-path go to
 // the block bin (w above the threshold) or the warp bin.  Rows of up to 32 entries are summed by their own lane,
-// longer ones by the whole warp.
-struct DenseInfo {
-  const int32_t* dq0;  // null: no dense rows
-  int32_t base_w;
-  int32_t wtopq;
-  int64_t n;
-  // quads of v's dense row, or 0 if v's row is an id list only
-  __device__ __forceinline__ int32_t quads(int32_t v) const {
-    if (dq0 == nullptr || v < base_w || v >= n || __ldg(&dq0[v - base_w]) < 0) return 0;
-    return wtopq - ((v + 1 - base_w) >> 7);
+// longer ones by the whole warp.  rowinfo[v] = {d+(v), padded length or minus dense quads}.
+struct RowWork {
+  int64_t pad = 0, wtrue = 0, wdense = 0, qdense = 0;
+  __device__ __forceinline__ void add(int2 ri) {
+    wtrue += ri.x;
+    if (ri.y >= 0) {
+      pad += ri.y;
+    } else {
+      pad += -4 * (int64_t)ri.y;
+      wdense += ri.x;
+      qdense += -ri.y;
+    }
   }
 };
 
 __global__ void k_bins(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                       const int32_t* __restrict__ dplus, int64_t n, int64_t block_min_work, DenseInfo di,
+                       const int2* __restrict__ rowinfo, int64_t n, int64_t block_min_work,
                        int32_t* __restrict__ list, BinCounters* __restrict__ bc) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
@@ -655,55 +652,30 @@ __global__ void k_bins(const int64_t* __restrict__ off, const int32_t* __restric
     int64_t b = 0;
     int32_t d = 0;
     if (u < n) {
-      d = dplus[u];
+      d = rowinfo[u].x;
       b = off[u];
     }
-    int64_t wpad = 0, wtrue = 0, wdense = 0, qdense = 0;
-    if (d <= 32) {
-      for (int64_t j = b; j < b + d; ++j) {
-        const int32_t v = col[j];
-        const int32_t dv_ = dplus[v];
-        const int32_t q = di.quads(v);
-        wpad += q > 0 ? 4 * q : (dv_ + 3) & ~3;
-        wtrue += dv_;
-        if (q > 0) {
-          wdense += dv_;
-          qdense += q;
-        }
-      }
-    }
+    RowWork w;
+    if (d <= 32)
+      for (int64_t j = b; j < b + d; ++j) w.add(rowinfo[col[j]]);
     unsigned longs = __ballot_sync(kFull, d > 32);
     while (longs) {
       const int k = __ffs(longs) - 1;
       longs &= longs - 1;
       const int64_t rb = __shfl_sync(kFull, b, k);
       const int32_t rd = __shfl_sync(kFull, d, k);
-      int64_t p = 0, t = 0, wd = 0, qd = 0;
-      for (int32_t j = lane; j < rd; j += 32) {
-        const int32_t v = col[rb + j];
-        const int32_t dv_ = dplus[v];
-        const int32_t q = di.quads(v);
-        p += q > 0 ? 4 * q : (dv_ + 3) & ~3;
-        t += dv_;
-        if (q > 0) {
-          wd += dv_;
-          qd += q;
-        }
-      }
-      p = warp_sum(p);
-      t = warp_sum(t);
-      wd = warp_sum(wd);
-      qd = warp_sum(qd);
-      if (lane == k) {
-        wpad = p;
-        wtrue = t;
-        wdense = wd;
-        qdense = qd;
-      }
+      RowWork p;
+      for (int32_t j = lane; j < rd; j += 32) p.add(rowinfo[col[rb + j]]);
+      p.pad = warp_sum(p.pad);
+      p.wtrue = warp_sum(p.wtrue);
+      p.wdense = warp_sum(p.wdense);
+      p.qdense = warp_sum(p.qdense);
+      if (lane == k) w = p;
     }
+    const int64_t wpad = w.pad, wtrue = w.wtrue;
     wsum += (unsigned long long)wtrue;
-    dw += (unsigned long long)wdense;
-    dv += (unsigned long long)qdense;
+    dw += (unsigned long long)w.wdense;
+    dv += (unsigned long long)w.qdense;
     if (d > dmax) dmax = d;
     const bool keep = d >= 2 && wtrue > 0;
     const bool blk = keep && wpad > block_min_work;
@@ -737,14 +709,20 @@ __global__ void k_bins(const int64_t* __restrict__ off, const int32_t* __restric
 
 // ---- dense rows -------------------------------------------------------------------------------------------------
 // Row v (in the warp window) is kept as a bitmap too when its bitmap quads cover no more words than it has entries.
+// For every vertex, rowinfo[v] = {d+(v), its hop-2 cost code}: the padded row length, or minus the quads of its
+// dense row; nq[v - base_w] = those quads (0: id list only) for the window.
 __global__ void k_dense_select(const int32_t* __restrict__ dplus, int64_t n, int32_t base_w, int32_t wtopq,
-                               int32_t* __restrict__ nq) {
-  const int64_t wn = n - base_w;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < wn; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t v = base_w + i;
+                               int32_t* __restrict__ nq, int2* __restrict__ rowinfo) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const int32_t d = dplus[v];
-    const int32_t q = wtopq - (int32_t)((v + 1 - base_w) >> 7);
-    nq[i] = (d >= kDenseMinDegree && 4 * (int64_t)q <= d) ? q : 0;
+    int32_t code = (d + 3) & ~3;
+    if (v >= base_w) {
+      const int32_t q = wtopq - (int32_t)((v + 1 - base_w) >> 7);
+      const bool dense = d >= kDenseMinDegree && 4 * (int64_t)q <= d;
+      nq[v - base_w] = dense ? q : 0;
+      if (dense) code = -q;
+    }
+    rowinfo[v] = make_int2(d, code);
   }
 }
 
@@ -996,7 +974,7 @@ tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* p
   const uint64_t sentinel = (1ull << (2 * B)) - 1ull;
   tc_status st = TC_OK;
   const bool buckets = peel_rounds < 0 && use_buckets(M);
-  Buf alt, part, counters, odeg, ukeys, rkeys, rkeys_alt, rank, rcount, ustart, plen, dnq, dqoff;
+  Buf alt, part, counters, odeg, ukeys, rkeys, rkeys_alt, rank, rcount, ustart, plen, dnq, dqoff, rowinfo;
   int64_t m = 0;
   BinCounters hb{};
   int64_t total_padded = 0;
@@ -1121,14 +1099,14 @@ tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* p
     unsigned long long* drows = reinterpret_cast<unsigned long long*>(counters.as<char>() + 48);
     int64_t dquads = 0;
     unsigned long long hrows = 0;
-    DenseInfo di{nullptr, vw.base_w, vw.wtopq, n};
-    if (n > 0 && m > 0) {
-      if ((st = buf_alloc(a, dnq, (size_t)wn * 4, s))) break;
+    if ((st = buf_alloc(a, rowinfo, (size_t)n1 * 8, s))) break;
+    if (n > 0) {
+      if ((st = buf_alloc(a, dnq, (size_t)(wn > 0 ? wn : 1) * 4, s))) break;
       if ((st = buf_alloc(a, dqoff, (size_t)(wn + 1) * 8, s))) break;
       if ((st = buf_alloc(a, g->dq0, (size_t)wn * 4, s))) break;
       if ((st = cuda_status(cudaMemsetAsync(drows, 0, 8, s), "memset dense rows"))) break;
-      k_dense_select<<<grid_for(wn, 256), 256, 0, s>>>(odeg.as<int32_t>(), n, vw.base_w, vw.wtopq,
-                                                       dnq.as<int32_t>());
+      k_dense_select<<<grid_for(n, 256), 256, 0, s>>>(odeg.as<int32_t>(), n, vw.base_w, vw.wtopq,
+                                                      dnq.as<int32_t>(), rowinfo.as<int2>());
       if ((st = launched("k_dense_select"))) break;
       if ((st = exclusive_scan_i32_to_i64(a, dnq.as<int32_t>(), dqoff.as<int64_t>(), wn, s))) break;
       k_dense_index<<<grid_for(wn, 256), 256, 0, s>>>(dnq.as<int32_t>(), dqoff.as<int64_t>(), wn,
@@ -1139,15 +1117,14 @@ tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* p
         break;
       if ((st = cuda_status(cudaMemcpyAsync(&hrows, drows, 8, cudaMemcpyDeviceToHost, s), "copy dense rows")))
         break;
-      di.dq0 = g->dq0.as<int32_t>();
     }
 
     // ---- bins ----
     if ((st = buf_alloc(a, g->list, (size_t)n1 * 4, s))) break;
     if ((st = cuda_status(cudaMemsetAsync(counters.p, 0, sizeof(BinCounters), s), "memset bins"))) break;
     if (n > 0) {
-      k_bins<<<grid_for(n, 256), 256, 0, s>>>(g->off.as<int64_t>(), g->col.as<int32_t>(), odeg.as<int32_t>(), n,
-                                              block_min_work_for(m), di, g->list.as<int32_t>(),
+      k_bins<<<grid_for(n, 256), 256, 0, s>>>(g->off.as<int64_t>(), g->col.as<int32_t>(), rowinfo.as<int2>(), n,
+                                              block_min_work_for(m), g->list.as<int32_t>(),
                                               counters.as<BinCounters>());
       if ((st = launched("k_bins"))) break;
     }
@@ -1170,7 +1147,7 @@ tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* p
   } while (0);
 
   for (Buf* b : {&alt, &part, &counters, &odeg, &ukeys, &rkeys, &rkeys_alt, &rank, &rcount, &ustart, &plen, &dnq,
-                 &dqoff})
+                 &dqoff, &rowinfo})
     buf_release(a, *b, s);
   buf_release(a, g->keys, s);
   buf_release(a, g->indeg, s);

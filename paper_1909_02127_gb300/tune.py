@@ -167,7 +167,7 @@ def main():
     out = {"device": props.name, "sms": props.multi_processor_count, "cc": f"{props.major}.{props.minor}",
            "classes": classes, "batch_warp_max_edges": batch_warp, "batch_times_ms": batch_times,
            "isect_max_wedges_milli": isect_ratio, "method_measurements": method_rows,
-           "measurements": results}
+           "bucket_max_pairs": tc.tc_get_bucket_max_pairs(), "measurements": results}
     with open(args.out, "w") as f:
         json.dump(out, f, indent=1)
     tc.tc_set_tuning([tuple(c) for c in classes], batch_warp_max_edges=batch_warp,
