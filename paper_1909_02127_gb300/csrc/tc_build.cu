@@ -287,10 +287,10 @@ struct RowCounters {
 };
 
 // Each pair {a, b} goes to the bucket of its lower-ranked endpoint as the higher rank.  Bucket s has room for the
-// input-pair count of s (an upper bound on its size) starting at pstart[s]; len[s] counts its pairs (the order in a
-// bucket is free).
+// input-pair count of s (an upper bound on its size) starting at pstart[s]; its cursor cur[s] starts there and ends
+// one past its last pair (the order in a bucket is free).
 __global__ void k_bucket(const uint64_t* __restrict__ keys, int64_t npairs, int B, const int32_t* __restrict__ rank,
-                         const int64_t* __restrict__ pstart, int32_t* __restrict__ len, int32_t* __restrict__ tgt) {
+                         unsigned long long* __restrict__ cur, int32_t* __restrict__ tgt) {
   const uint64_t mask = (1ull << B) - 1ull;
   const uint64_t sentinel = (1ull << (2 * B)) - 1ull;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npairs;
@@ -299,15 +299,14 @@ __global__ void k_bucket(const uint64_t* __restrict__ keys, int64_t npairs, int 
     if (k == sentinel) continue;
     const int32_t ra = rank[k >> B], rb = rank[k & mask];
     const int32_t lo = ra < rb ? ra : rb, hi = ra < rb ? rb : ra;
-    const int32_t slot = atomicAdd(&len[lo], 1);
-    tgt[pstart[lo] + slot] = hi;
+    tgt[atomicAdd(&cur[lo], 1ull)] = hi;
   }
 }
 
 // Buckets of up to kSmallRow pairs, sorted and de-duplicated in place by one warp each (32 consecutive sources per
 // warp).  Longer buckets are listed for k_rows_warp (front of `lists`) when their target range fits a warp's bitmap
 // or they fit a warp's registers, and for k_rows_block (back of `lists`) otherwise.  d[s] = distinct targets of s.
-__global__ void k_rows_small(const int64_t* __restrict__ pstart, const int32_t* __restrict__ len, int64_t n,
+__global__ void k_rows_small(const int64_t* __restrict__ pstart, const int64_t* __restrict__ cur, int64_t n,
                              int32_t* __restrict__ tgt, int32_t* __restrict__ d, int32_t* __restrict__ lists,
                              RowCounters* __restrict__ rc) {
   const int lane = threadIdx.x & 31;
@@ -321,7 +320,7 @@ __global__ void k_rows_small(const int64_t* __restrict__ pstart, const int32_t* 
     int32_t L = 0;
     if (sidx < n) {
       ps = pstart[sidx];
-      L = len[sidx];
+      L = (int32_t)(cur[sidx] - ps);
     }
     const int64_t range = n - 1 - sidx;
     const bool to_warp = L > kSmallRow && (range <= kWarpBits || L <= kWarpRow);
@@ -441,7 +440,7 @@ __device__ __forceinline__ uint32_t warp_sort_unique(int32_t (&x)[T], int32_t* _
 // Buckets listed for one warp each: a bitmap over the target range (s, n) in the warp's shared memory when the range
 // has at most kWarpBits ids, else (at most kWarpRow pairs) a bitonic sort in registers.
 __global__ void __launch_bounds__(kRowThreads) k_rows_warp(const int64_t* __restrict__ pstart,
-                                                           const int32_t* __restrict__ len, int64_t n,
+                                                           const int64_t* __restrict__ cur, int64_t n,
                                                            int32_t* __restrict__ tgt, int32_t* __restrict__ d,
                                                            const int32_t* __restrict__ list,
                                                            RowCounters* __restrict__ rc) {
@@ -454,7 +453,7 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_warp(const int64_t* __rest
   for (unsigned r = gw; r < rows; r += nw) {
     const int32_t sidx = list[r];
     const int64_t ps = pstart[sidx];
-    const int32_t L = len[sidx];
+    const int32_t L = (int32_t)(cur[sidx] - ps);
     const int64_t range = n - 1 - sidx;
     uint32_t run;
     if (range <= kWarpBits) {
@@ -509,7 +508,7 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_warp(const int64_t* __rest
 // range when it has at most kBigBits ids, else a bitonic sort in shared memory (such a bucket has fewer than
 // 2M / kBigBits <= mid_max pairs).
 __global__ void __launch_bounds__(kBigThreads) k_rows_block(const int64_t* __restrict__ pstart,
-                                                            const int32_t* __restrict__ len, int64_t n,
+                                                            const int64_t* __restrict__ cur, int64_t n,
                                                             int32_t mid_max, int32_t* __restrict__ tgt,
                                                             int32_t* __restrict__ d,
                                                             const int32_t* __restrict__ lists,
@@ -521,7 +520,7 @@ __global__ void __launch_bounds__(kBigThreads) k_rows_block(const int64_t* __res
   for (unsigned r = blockIdx.x; r < rows; r += gridDim.x) {
     const int32_t sidx = lists[n - 1 - r];
     const int64_t ps = pstart[sidx];
-    const int64_t L = len[sidx];
+    const int64_t L = cur[sidx] - ps;
     const int64_t range = n - 1 - sidx;
     uint32_t total = 0;
     if (range <= kBigBits) {
@@ -876,7 +875,7 @@ tc_status bucket_csr(tc_graph* g, const int32_t* rank, const int32_t* rcount, Bu
   const int64_t M = g->num_pairs;
   const int64_t n = g->n;
   const int64_t n1 = n > 0 ? n : 1;
-  Buf pstart, len, tgt, lists, rcb, plen;
+  Buf pstart, cur, tgt, lists, rcb, plen;
   tc_status st = TC_OK;
   auto launched = [&](const char* what) {
     note_launch();
@@ -889,42 +888,44 @@ tc_status bucket_csr(tc_graph* g, const int32_t* rank, const int32_t* rcount, Bu
   do {
     // bucket s has room for the input-pair count of s: 2 slots per pair in all
     if ((st = buf_alloc(a, pstart, (size_t)(n + 1) * 8, s))) break;
-    if ((st = buf_alloc(a, len, (size_t)n1 * 4, s))) break;
+    if ((st = buf_alloc(a, cur, (size_t)n1 * 8, s))) break;
     if ((st = buf_alloc(a, tgt, (size_t)(M > 0 ? 2 * M : 1) * 4, s))) break;
     if ((st = buf_alloc(a, dplus, (size_t)n1 * 4, s))) break;
     if ((st = buf_alloc(a, lists, (size_t)n1 * 4, s))) break;
     if ((st = buf_alloc(a, rcb, sizeof(RowCounters), s))) break;
-    if ((st = cuda_status(cudaMemsetAsync(len.p, 0, (size_t)n1 * 4, s), "memset len"))) break;
     if ((st = cuda_status(cudaMemsetAsync(rcb.p, 0, sizeof(RowCounters), s), "memset rows"))) break;
     if (n > 0) {
       if ((st = exclusive_scan_i32_to_i64(a, rcount, pstart.as<int64_t>(), n, s))) break;
     } else if ((st = cuda_status(cudaMemsetAsync(pstart.p, 0, 8, s), "memset pstart"))) {
       break;
     }
+    if ((st = cuda_status(cudaMemcpyAsync(cur.p, pstart.p, (size_t)n1 * 8, cudaMemcpyDeviceToDevice, s),
+                          "copy cursors")))
+      break;
     if (M > 0) {
-      k_bucket<<<grid_for(M, 256), 256, 0, s>>>(g->keys.as<uint64_t>(), M, B, rank, pstart.as<int64_t>(),
-                                                len.as<int32_t>(), tgt.as<int32_t>());
+      k_bucket<<<grid_for(M, 256), 256, 0, s>>>(g->keys.as<uint64_t>(), M, B, rank,
+                                                cur.as<unsigned long long>(), tgt.as<int32_t>());
       if ((st = launched("k_bucket"))) break;
     }
     buf_release(a, g->keys, s);
     RowCounters* rc = rcb.as<RowCounters>();
     int32_t* rlist = lists.as<int32_t>();
     if (n > 0) {
-      k_rows_small<<<grid_for(n, 256), 256, 0, s>>>(pstart.as<int64_t>(), len.as<int32_t>(), n, tgt.as<int32_t>(),
+      k_rows_small<<<grid_for(n, 256), 256, 0, s>>>(pstart.as<int64_t>(), cur.as<int64_t>(), n, tgt.as<int32_t>(),
                                                     dplus.as<int32_t>(), rlist, rc);
       if ((st = launched("k_rows_small"))) break;
-      k_rows_warp<<<4 * kNumSMs, kRowThreads, 0, s>>>(pstart.as<int64_t>(), len.as<int32_t>(), n,
+      k_rows_warp<<<4 * kNumSMs, kRowThreads, 0, s>>>(pstart.as<int64_t>(), cur.as<int64_t>(), n,
                                                       tgt.as<int32_t>(), dplus.as<int32_t>(), rlist, rc);
       if ((st = launched("k_rows_warp"))) break;
       const size_t blk_smem = (size_t)kBigBits / 8;
       if ((st = cuda_status(cudaFuncSetAttribute(k_rows_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)blk_smem), "k_rows_block attribute")))
         break;
-      k_rows_block<<<kNumSMs, kBigThreads, blk_smem, s>>>(pstart.as<int64_t>(), len.as<int32_t>(), n, mid_max,
+      k_rows_block<<<kNumSMs, kBigThreads, blk_smem, s>>>(pstart.as<int64_t>(), cur.as<int64_t>(), n, mid_max,
                                                           tgt.as<int32_t>(), dplus.as<int32_t>(), rlist, rc);
       if ((st = launched("k_rows_block"))) break;
     }
-    buf_release(a, len, s);
+    buf_release(a, cur, s);
     // padded offsets
     if ((st = buf_alloc(a, g->off, (size_t)(n + 1) * 8, s))) break;
     if ((st = buf_alloc(a, plen, (size_t)n1 * 4, s))) break;
@@ -959,7 +960,7 @@ tc_status bucket_csr(tc_graph* g, const int32_t* rank, const int32_t* rcount, Bu
       if ((st = launched("k_rows_copy"))) break;
     }
   } while (0);
-  for (Buf* b : {&pstart, &len, &tgt, &lists, &rcb, &plen}) buf_release(a, *b, s);
+  for (Buf* b : {&pstart, &cur, &tgt, &lists, &rcb, &plen}) buf_release(a, *b, s);
   return st;
 }
 
