@@ -1140,6 +1140,8 @@ tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* p
                                                            odeg.as<int32_t>(), n, vw.base_w, g->dq0.as<int32_t>(),
                                                            g->dense.as<uint32_t>());
       if ((st = launched("k_dense_fill"))) break;
+      // the graph is complete when tc_build returns: another stream may count it next
+      if ((st = cuda_status(cudaStreamSynchronize(s), "sync dense rows"))) break;
       g->dense_rows = (int64_t)hrows;
       g->dense_quads = dquads;
     } else {

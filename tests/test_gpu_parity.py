@@ -374,3 +374,25 @@ def test_counts_do_not_depend_on_tuning(tc):
                 assert info["bin_block"] == 0
     finally:
         tc.tc_set_tuning(saved)
+
+
+@pytest.mark.parametrize("scale", [16, 18])
+def test_build_then_count_on_another_stream(tc, scale):
+    """tc_build synchronises its stream before returning, so a graph built on one stream can be counted on another
+    at once (the serving loop does exactly that) — including the dense row bitmaps written last."""
+    import torch
+    src, dst = graphgen.rmat(scale, 16, 2200 + scale).edges()
+    n = 1 << scale
+    T = oracle.count(src, dst, n)[0]
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for _ in range(3):
+        g = tc.tc_load_edges(src, dst, n, stream=s1)
+        try:
+            tc.tc_build(g, s1)
+            assert tc.tc_graph_get_info(g)["dense_rows"] > 0
+            tc.tc_count_device(g, out, s2)
+            s2.synchronize()
+            assert int(out.item()) == T
+        finally:
+            tc.tc_free(g)
