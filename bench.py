@@ -41,8 +41,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="rmat20",
-                   help="rmat20 | rmat26 | er4096 | batch | serve | unfused | prune | rmat<scale> (R-MAT, edge factor 16)")
-    p.add_argument("--graph", default="rmat20", help="unfused: the graph the two counting paths are compared on")
+                   help="rmat20 | rmat26 | er4096 | batch | serve | unfused | prune | list | rmat<scale> (R-MAT, edge factor 16)")
+    p.add_argument("--graph", default="rmat20", help="unfused, list: the graph")
     p.add_argument("--unfused-chunk-bytes", type=int, default=0,
                    help="unfused: bytes one round-2 pass may hold (0: the largest pass)")
     p.add_argument("--batch-graphs", type=int, default=4096)
@@ -467,6 +467,108 @@ def run_unfused(args, dist: Dist):
     }
 
 
+def run_list(args, dist: Dist):
+    """Triangle listing: every triangle of the graph written as ascending original-id triples into device memory
+    (tc_list_triangles), timed with CUDA events; the count kernel on the same graph beside it."""
+    import ctypes
+
+    import torch
+
+    import graphgen
+    import paper_1909_02127_gb300 as tc
+
+    dev = torch.device("cuda", dist.local)
+    torch.cuda.set_device(dev)
+    base = graphgen.config(args.graph)
+    spec = graphgen.GraphSpec(base.kind, base.n, base.num_edges, base.seed + dist.rank, base.scale, base.permute,
+                              base.name)
+    stream = torch.cuda.current_stream()
+    ds, dd = spec.edges(device=dev)
+    g = tc.tc_load_edges(ds, dd, spec.n, stream=stream)
+    tc.tc_build(g, stream)
+    info = tc.tc_graph_get_info(g)
+    T = tc.tc_count(g, stream)
+    out = torch.empty((max(T, 1), 3), dtype=torch.int32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+    lib = tc.load_library()
+    found = ctypes.c_uint64()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+
+    def list_all():
+        st = lib.tc_list_triangles(g, 0, spec.n, out.data_ptr(), T, ctypes.byref(found), tc.TC_PTR_DEVICE, sp)
+        if st != tc.TC_OK or found.value != T:
+            raise RuntimeError(f"listing: status {st}, found {found.value} of {T}")
+
+    for _ in range(max(1, args.warmup)):
+        list_all()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(dist.local)
+    launches0 = tc.tc_kernel_launches()
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.fill_(k)
+        ev[k][0].record(stream)
+        list_all()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clock_info = clocks.stop()
+    dist.barrier()
+    launches = tc.tc_kernel_launches() - launches0
+    # spot check: a sample of the listed triples are triangles of the input (sorted, distinct, adjacent)
+    sample = out[torch.randint(0, max(T, 1), (4096,), device=dev)].cpu().numpy() if T else None
+    if sample is not None:
+        import numpy as np
+        hs, hd = ds.cpu().numpy().astype(np.int64), dd.cpu().numpy().astype(np.int64)
+        edges = np.unique(np.minimum(hs, hd) * spec.n + np.maximum(hs, hd))
+        t = sample.astype(np.int64)
+
+        def present(x):
+            i = np.minimum(np.searchsorted(edges, x), edges.size - 1)
+            return edges[i] == x
+
+        ok = (t[:, 0] < t[:, 1]) & (t[:, 1] < t[:, 2])
+        ok &= present(t[:, 0] * spec.n + t[:, 1]) & present(t[:, 1] * spec.n + t[:, 2])
+        ok &= present(t[:, 0] * spec.n + t[:, 2])
+        if not ok.all():
+            raise RuntimeError(f"listing: {int((~ok).sum())} sampled triples are not triangles")
+    count_ms = []
+    d_total = torch.zeros(1, dtype=torch.int64, device=dev)
+    for k in range(args.steps):
+        flush.fill_(k)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tc.tc_count_device(g, d_total, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        count_ms.append(e0.elapsed_time(e1))
+    tc.tc_free(g)
+    list_ms = [a.elapsed_time(b) for a, b in ev]
+    units, secs = aggregate(T * args.steps, sum(list_ms) / 1e3, dist)
+    out_bytes = 12 * T
+    t_list = statistics.mean(list_ms) / 1e3
+    peak, peak_kind = measured_peaks()
+    # both passes: the counting pass (dense rows as bitmaps), the listing pass (every hop-2 row as ids), and per
+    # triangle its 12-byte triple and the 4-byte rank -> id lookup of its third vertex
+    n_, m_, W_ = info["num_vertices"], info["num_edges"], info["num_wedges"]
+    list_bytes = (algorithmic_bytes(info, 2 * 152) + 8.0 * (n_ + 1) + 20.0 * m_ + 4.0 * W_ + 16.0 * T)
+    return {
+        "metric": "triangles listed per second (ascending original-id triples into device memory)",
+        "value": round(units / secs, 1), "unit": "triangles/s", "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(statistics.mean(list_ms), 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32/uint64 (exact integer)", "data": "synthetic",
+        "config": workload_config(spec, "2x L2 buffer written before each timed listing", dist.world),
+        "m": info["num_edges"], "triangles": T, "output_bytes": out_bytes,
+        "count_ms": round(statistics.mean(count_ms), 4),
+        "roofline": {"bound": "hbm", "kernel": "k_list (counting and listing passes)",
+                     "achieved": round(list_bytes / t_list / 1e9, 1), "peak": peak, "peak_kind": peak_kind,
+                     "unit": "GB/s", "frac": round(list_bytes / t_list / 1e9 / peak, 4), "traffic": None,
+                     "algorithmic_bytes": list_bytes},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clock_info,
+    }
+
+
 def run_batch(args, dist: Dist):
     import numpy as np
     import torch
@@ -722,7 +824,7 @@ def run_reference(args, dist: Dist):
     import oracle
     if dist.rank != 0:
         return None
-    if args.workload in ("batch", "serve", "unfused", "prune"):
+    if args.workload in ("batch", "serve", "unfused", "prune", "list"):
         return {"impl": "reference", "unavailable": "the oracle arm is defined for the single-graph workloads"}
     spec = graphgen.config(args.workload)
     sample, what = cpu_sample(spec, 21)
@@ -772,6 +874,8 @@ def main():
         out = run_unfused(args, dist)
     elif args.workload == "prune":
         out = run_prune(args, dist)
+    elif args.workload == "list":
+        out = run_list(args, dist)
     else:
         out = run_single(args, dist)
     dist.close()

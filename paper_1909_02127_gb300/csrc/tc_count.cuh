@@ -91,22 +91,25 @@ enum Mode { kModeCount = 0, kModeVertex = 1, kModeList = 2 };
 struct Sink {
   unsigned long long* pv = nullptr;      // kModeVertex: t(x) in rank space
   int32_t* tri = nullptr;                // kModeList: triples of original ids, 3 per triangle
-  unsigned long long* cursor = nullptr;  // kModeList: triangles found so far (also past `capacity`)
+  unsigned long long* slot = nullptr;    // kModeList: the warp's next output position (shared memory)
   unsigned long long capacity = 0;       // kModeList: triples that fit in `tri`
   const int32_t* perm = nullptr;         // kModeList: rank -> original id
   int32_t u = 0;                         // kModeList: the current source
 };
 
-// Append the closed 2-paths u->v->w of this lane (h_i marks w_i) to the list.  Warp-collective: every lane calls it.
+// Append the closed 2-paths u->v->w of this lane (h_i marks w_i) to the list at the warp's output position (the
+// source's own range of the output, known from a counting pass), which advances past them.  Warp-collective:
+// every lane calls it.
 __device__ __forceinline__ void list_hits(const int4 q, uint32_t h0, uint32_t h1, uint32_t h2, uint32_t h3,
                                           const Sink& sk, int32_t v) {
   const uint32_t cnt = h0 + h1 + h2 + h3;
   const uint32_t incl = warp_inclusive_scan(cnt);
   const uint32_t total = __shfl_sync(kFull, incl, 31);
   if (total == 0) return;
-  unsigned long long base = 0;
-  if ((threadIdx.x & 31) == 31) base = atomicAdd(sk.cursor, (unsigned long long)total);
-  base = __shfl_sync(kFull, base, 31);
+  const unsigned long long base = *sk.slot;
+  __syncwarp();
+  if ((threadIdx.x & 31) == 31) *sk.slot = base + total;
+  __syncwarp();
   unsigned long long pos = base + incl - cnt;
   const int32_t ws[4] = {q.x, q.y, q.z, q.w};
   const uint32_t hs[4] = {h0, h1, h2, h3};
