@@ -44,11 +44,14 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     """Build libtc.so if any source is newer than it (or force).  Returns the library path."""
     if not force and not stale():
         return LIB
-    os.makedirs(BUILD_DIR, exist_ok=True)
+    # objects in a directory of this process's own, so that processes building at once (ranks of one job) never
+    # link each other's half-written objects; the library itself is replaced atomically
+    obj_dir = os.path.join(BUILD_DIR, str(os.getpid()))
+    os.makedirs(obj_dir, exist_ok=True)
     nvcc = _nvcc()
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(obj_dir, src.replace(".cu", ".o"))
         cmd = [nvcc, *NVCC_FLAGS, *extra_flags, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -64,6 +67,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    shutil.rmtree(obj_dir, ignore_errors=True)
     return LIB
 
 
