@@ -201,7 +201,7 @@ def algorithmic_bytes(info: dict, grid_ctas: int) -> float:
 
 
 def count_grid(info: dict) -> int:
-    want = info["bin_block"] + (info["bin_warp"] + 15) // 16
+    want = info["bin_block"] + (info["bin_warp"] + 15) // 16 + (info.get("bin_thread", 0) + 511) // 512
     return int(max(1, min(want, 2 * 152)))
 
 

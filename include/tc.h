@@ -77,6 +77,7 @@ typedef struct tc_graph_info {
   int64_t dense_rows;      /* rows N+(v) also stored as bitmaps over (v, n) (no more words than entries) */
   int64_t dense_wedges;    /* the part of num_wedges through dense rows (tested 128 ids per 16-byte word load) */
   int64_t dense_quads;     /* 16-byte bitmap words that tc_count reads for them: sum of d-(v) * quads(v) */
+  int64_t bin_thread;      /* sources handled one lane each (few out-neighbours: each pair tested by a lookup) */
 } tc_graph_info;
 
 /*

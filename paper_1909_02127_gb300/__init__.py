@@ -41,7 +41,7 @@ class tc_graph_info(ctypes.Structure):
                 ("csr_entries", ctypes.c_int64), ("max_out_degree", ctypes.c_int64), ("num_wedges", ctypes.c_int64),
                 ("active_sources", ctypes.c_int64), ("bin_warp", ctypes.c_int64), ("bin_block", ctypes.c_int64),
                 ("built", ctypes.c_int32), ("reserved", ctypes.c_int32), ("dense_rows", ctypes.c_int64),
-                ("dense_wedges", ctypes.c_int64), ("dense_quads", ctypes.c_int64)]
+                ("dense_wedges", ctypes.c_int64), ("dense_quads", ctypes.c_int64), ("bin_thread", ctypes.c_int64)]
 
 
 TC_TUNING_MAX_CLASSES = 16

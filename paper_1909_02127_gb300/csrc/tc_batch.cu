@@ -1,9 +1,10 @@
 // tc_batch.cu — count many graphs in one persistent launch.
 //
 // The work queue is the concatenation, over the graphs of the batch, of their block-bin sources and (separately)
-// of their warp-bin sources.  pb[g] / pw[g] are exclusive prefixes of the per-graph bin sizes, so a global source
-// index maps to its graph by binary search.  CTAs first drain the block-bin space one source at a time; then each
-// warp drains the warp-bin space four sources at a time.  Per-source counts are added to counts[g] (one atomic per
+// of their warp-bin sources and of their thread-bin sources in tasks of 32.  pb[g] / pw[g] / pt[g] are exclusive
+// prefixes of the per-graph sizes, so a global index maps to its graph by binary search.  CTAs first drain the
+// block-bin space one source at a time; then each warp drains the warp-bin space sixteen sources at a time, and the
+// thread-bin space one task (one source per lane) at a time.  Per-source counts are added to counts[g] (one atomic per
 // warp per run of consecutive sources of the same graph).  The loops end when the cursors pass the totals: there
 // is no waiting on other CTAs.
 #include <string.h>
@@ -21,6 +22,7 @@ struct BatchTable {
   const CsrView* views;
   const int64_t* pb;  // num_graphs + 1
   const int64_t* pw;  // num_graphs + 1
+  const int64_t* pt;  // num_graphs + 1: thread-bin tasks of 32 sources
   int32_t num_graphs;
 };
 
@@ -112,12 +114,38 @@ __global__ void __launch_bounds__(kCountThreads, 2)
     acc = warp_sum(acc);
     if (lane == 0 && acc && cur_g >= 0) atomicAdd(&counts[cur_g], acc);
   }
+  const int64_t NT = __ldg(&t.pt[G]);
+  if (NT > 0) {  // thread-bin sources: one task of 32 per warp, one source per lane
+    int cur_g = -1;
+    unsigned long long acc = 0;
+    CsrView v{};
+    int64_t gbeg = 0, gend = 0;  // [pt[cur_g], pt[cur_g + 1])
+    while (true) {
+      long long idx = 0;
+      if (lane == 0) idx = (long long)atomicAdd(&cursors[2], 1ull);
+      idx = __shfl_sync(kFull, idx, 0);
+      if (idx >= NT) break;
+      if (idx < gbeg || idx >= gend) {
+        acc = warp_sum(acc);
+        if (lane == 0 && acc && cur_g >= 0) atomicAdd(&counts[cur_g], acc);
+        acc = 0;
+        cur_g = find_graph(t.pt, G, idx);
+        v = t.views[cur_g];
+        gbeg = __ldg(&t.pt[cur_g]);
+        gend = __ldg(&t.pt[cur_g + 1]);
+      }
+      const int64_t k = (idx - gbeg) * 32 + lane;
+      if (k < v.nt) acc += dev::tiny_source<dev::kModeCount>(v.tlist[k], v, dev::Sink{});
+    }
+    acc = warp_sum(acc);
+    if (lane == 0 && acc && cur_g >= 0) atomicAdd(&counts[cur_g], acc);
+  }
 }
 
 // Device layout of a batch: views | pb | pw | counts | cursors, built from host handles.
 struct BatchLayout {
   size_t views_bytes, pre_bytes, table_bytes, counts_bytes, total_bytes;
-  int64_t nb_total, nw_total;
+  int64_t nb_total, nw_total, nt_total;
 };
 
 tc_status check_batch(tc_graph* const* gs, int32_t num_graphs, const char* who) {
@@ -139,23 +167,26 @@ BatchLayout batch_table(tc_graph* const* gs, int32_t num_graphs, std::vector<uns
   BatchLayout L{};
   L.views_bytes = ((G * sizeof(CsrView)) + 255) / 256 * 256;
   L.pre_bytes = ((G + 1) * 8 + 255) / 256 * 256;
-  L.table_bytes = L.views_bytes + 2 * L.pre_bytes;
+  L.table_bytes = L.views_bytes + 3 * L.pre_bytes;
   L.counts_bytes = (G * 8 + 255) / 256 * 256;
   L.total_bytes = L.table_bytes + L.counts_bytes + 64;
   host.assign(L.table_bytes, 0);
   CsrView* hv = reinterpret_cast<CsrView*>(host.data());
   int64_t* hpb = reinterpret_cast<int64_t*>(host.data() + L.views_bytes);
   int64_t* hpw = reinterpret_cast<int64_t*>(host.data() + L.views_bytes + L.pre_bytes);
-  hpb[0] = hpw[0] = 0;
+  int64_t* hpt = reinterpret_cast<int64_t*>(host.data() + L.views_bytes + 2 * L.pre_bytes);
+  hpb[0] = hpw[0] = hpt[0] = 0;
   const int64_t warp_max = batch_warp_max_edges();
   for (size_t i = 0; i < G; ++i) {
     hv[i] = gs[i]->view();
     if (gs[i]->m <= warp_max) hv[i].nbw = hv[i].nb;  // this graph's block-bin sources run one warp each
     hpb[i + 1] = hpb[i] + (hv[i].nb - hv[i].nbw);
     hpw[i + 1] = hpw[i] + hv[i].nw + hv[i].nbw;
+    hpt[i + 1] = hpt[i] + (hv[i].nt + 31) / 32;
   }
   L.nb_total = hpb[G];
   L.nw_total = hpw[G];
+  L.nt_total = hpt[G];
   return L;
 }
 
@@ -165,13 +196,14 @@ tc_status batch_launch(unsigned char* base, const BatchLayout& L, int32_t num_gr
   unsigned long long* counts = reinterpret_cast<unsigned long long*>(base + L.table_bytes);
   unsigned long long* cursors = reinterpret_cast<unsigned long long*>(base + L.table_bytes + L.counts_bytes);
   TC_CUDA(cudaMemsetAsync(counts, 0, L.counts_bytes + 64, s));
-  if (L.nb_total + L.nw_total > 0) {
+  if (L.nb_total + L.nw_total + L.nt_total > 0) {
     BatchTable t;
     t.views = reinterpret_cast<const CsrView*>(base);
     t.pb = reinterpret_cast<const int64_t*>(base + L.views_bytes);
     t.pw = reinterpret_cast<const int64_t*>(base + L.views_bytes + L.pre_bytes);
+    t.pt = reinterpret_cast<const int64_t*>(base + L.views_bytes + 2 * L.pre_bytes);
     t.num_graphs = num_graphs;
-    const int64_t want = L.nb_total + (L.nw_total + kWarpsPerCTA - 1) / kWarpsPerCTA;
+    const int64_t want = L.nb_total + (L.nw_total + L.nt_total + kWarpsPerCTA - 1) / kWarpsPerCTA;
     const int grid = (int)(want < 2 * kNumSMs ? want : 2 * kNumSMs);
     k_count_batch<<<grid, kCountThreads, dev::kCountSmem, s>>>(t, counts, cursors);
     TC_CUDA(cudaGetLastError());
@@ -203,7 +235,7 @@ extern "C" TC_API tc_status tc_count_batch(tc_graph* const* gs, int32_t num_grap
   tc_status st = cuda_status(cudaMemcpyAsync(dev.p, host.data(), L.table_bytes, cudaMemcpyHostToDevice, s), "H2D");
   if (st == TC_OK) st = batch_launch(dev.as<unsigned char>(), L, num_graphs, out_counts, s);
   if (st == TC_OK) {
-    if (L.nb_total + L.nw_total > 0) note_launch();
+    if (L.nb_total + L.nw_total + L.nt_total > 0) note_launch();
     st = cuda_status(cudaStreamSynchronize(s), "tc_count_batch sync");
   }
   buf_release(a, dev, s);
@@ -249,7 +281,7 @@ extern "C" TC_API tc_status tc_batch_plan_create(tc_graph* const* gs, int32_t nu
   p->alloc = gs[0]->alloc;
   std::vector<unsigned char> host;
   const BatchLayout L = batch_table(gs, num_graphs, host);
-  p->launches_kernel = L.nb_total + L.nw_total > 0;
+  p->launches_kernel = L.nb_total + L.nw_total + L.nt_total > 0;
   tc_status st = TC_OK;
   do {
     if ((st = cuda_status(cudaFuncSetAttribute(k_count_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,

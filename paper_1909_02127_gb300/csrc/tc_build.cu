@@ -615,7 +615,7 @@ struct BinCounters {
   unsigned int nb;
   unsigned int nw;
   int max_out;
-  int pad;
+  unsigned int nt;
   unsigned long long dense_wedges;  // 2-paths through dense rows
   unsigned long long dense_visits;  // quads of dense rows read per count
 };
@@ -640,7 +640,7 @@ struct RowWork {
 
 __global__ void k_bins(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
                        const int2* __restrict__ rowinfo, int64_t n, int64_t block_min_work,
-                       int32_t* __restrict__ list, BinCounters* __restrict__ bc) {
+                       int32_t* __restrict__ list, int32_t* __restrict__ tlist, BinCounters* __restrict__ bc) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -677,20 +677,27 @@ __global__ void k_bins(const int64_t* __restrict__ off, const int32_t* __restric
     dv += (unsigned long long)w.qdense;
     if (d > dmax) dmax = d;
     const bool keep = d >= 2 && wtrue > 0;
-    const bool blk = keep && wpad > block_min_work;
-    const bool wrp = keep && !blk;
+    // thread bin: few out-neighbours whose pairs cost far less to look up than the hop-2 rows cost to walk
+    // (4 C(d, 2) lookups' worth of entries or more; measured on GB300 against factors 2, 8 and 16 of C(d, 2))
+    const bool tny = keep && d <= kTinyMaxDegree && 8 * (int64_t)d * (d - 1) <= wpad;
+    const bool blk = keep && !tny && wpad > block_min_work;
+    const bool wrp = keep && !tny && !blk;
     act += keep ? 1 : 0;
     const unsigned mb = __ballot_sync(kFull, blk);
     const unsigned mw = __ballot_sync(kFull, wrp);
-    unsigned pb = 0, pw = 0;
+    const unsigned mt = __ballot_sync(kFull, tny);
+    unsigned pb = 0, pw = 0, pt = 0;
     if (lane == 0) {
       if (mb) pb = atomicAdd(&bc->nb, (unsigned)__popc(mb));
       if (mw) pw = atomicAdd(&bc->nw, (unsigned)__popc(mw));
+      if (mt) pt = atomicAdd(&bc->nt, (unsigned)__popc(mt));
     }
     pb = __shfl_sync(kFull, pb, 0);
     pw = __shfl_sync(kFull, pw, 0);
+    pt = __shfl_sync(kFull, pt, 0);
     if (blk) list[pb + __popc(mb & lt)] = (int32_t)u;
     if (wrp) list[n - 1 - (pw + __popc(mw & lt))] = (int32_t)u;
+    if (tny) tlist[pt + __popc(mt & lt)] = (int32_t)u;
   }
   wsum = warp_sum(wsum);
   act = warp_sum(act);
@@ -1122,10 +1129,11 @@ tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* p
 
     // ---- bins ----
     if ((st = buf_alloc(a, g->list, (size_t)n1 * 4, s))) break;
+    if ((st = buf_alloc(a, g->tlist, (size_t)n1 * 4, s))) break;
     if ((st = cuda_status(cudaMemsetAsync(counters.p, 0, sizeof(BinCounters), s), "memset bins"))) break;
     if (n > 0) {
       k_bins<<<grid_for(n, 256), 256, 0, s>>>(g->off.as<int64_t>(), g->col.as<int32_t>(), rowinfo.as<int2>(), n,
-                                              block_min_work_for(m), g->list.as<int32_t>(),
+                                              block_min_work_for(m), g->list.as<int32_t>(), g->tlist.as<int32_t>(),
                                               counters.as<BinCounters>());
       if ((st = launched("k_bins"))) break;
     }
@@ -1161,6 +1169,7 @@ tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* p
   g->active = (int64_t)hb.active;
   g->nb = hb.nb;
   g->nw = hb.nw;
+  g->nt = hb.nt;
   g->max_out_degree = hb.max_out;
   return TC_OK;
 }

@@ -163,6 +163,7 @@ void release_all(tc_graph* g, cudaStream_t s) {
   buf_release(g->alloc, g->off, s);
   buf_release(g->alloc, g->col, s);
   buf_release(g->alloc, g->list, s);
+  buf_release(g->alloc, g->tlist, s);
   buf_release(g->alloc, g->perm, s);
   buf_release(g->alloc, g->acc, s);
   buf_release(g->alloc, g->dq0, s);
@@ -501,6 +502,7 @@ TC_API tc_status tc_graph_get_info(const tc_graph* g, tc_graph_info* info) {
     info->active_sources = g->active;
     info->bin_warp = g->nw;
     info->bin_block = g->nb;
+    info->bin_thread = g->nt;
     info->dense_rows = g->dense_rows;
     info->dense_wedges = g->dense_wedges;
     info->dense_quads = g->dense_visits;

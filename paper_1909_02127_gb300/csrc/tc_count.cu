@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(kCountThreads, 2)
 }  // namespace
 
 int count_grid(const tc_graph* g) {
-  const int64_t want = g->nb + (g->nw + kWarpsPerCTA - 1) / kWarpsPerCTA;
+  const int64_t want = g->nb + (g->nw + kWarpsPerCTA - 1) / kWarpsPerCTA + (g->nt + kCountThreads - 1) / kCountThreads;
   return (int)(want < 2 * kNumSMs ? (want < 1 ? 1 : want) : 2 * kNumSMs);
 }
 
@@ -38,8 +38,8 @@ tc_status launch_count(const tc_graph* g, uint64_t* d_total, uint64_t* d_per_ver
                        cudaStream_t s) {
   TC_CUDA(cudaMemsetAsync(d_total, 0, sizeof(uint64_t), s));
   if (d_per_vertex && g->n > 0) TC_CUDA(cudaMemsetAsync(d_per_vertex, 0, (size_t)g->n * sizeof(uint64_t), s));
-  if (g->nb + g->nw == 0) return TC_OK;
-  TC_CUDA(cudaMemsetAsync(d_cursors, 0, 2 * sizeof(uint32_t), s));
+  if (g->nb + g->nw + g->nt == 0) return TC_OK;
+  TC_CUDA(cudaMemsetAsync(d_cursors, 0, 3 * sizeof(uint32_t), s));
   const int grid = count_grid(g);
   dev::Sink sk;
   if (d_per_vertex) {

@@ -510,6 +510,64 @@ __device__ __forceinline__ uint32_t block_source(int32_t u, const CsrView& g, ui
   return hits;
 }
 
+// One thread-bin source u, one lane: N+(u) has at most kTinyMaxDegree entries (one or two padded quads), and the
+// triangles u < a < b are the pairs a < b of N+(u) with b in N+(a).  For each a the lane reads its row once: a dense
+// row answers each b with one bit; an id row by binary search, whose lower bound only moves forward because the
+// b's ascend.  (The per-pair form of the closing test: C(d, 2) lookups instead of walking every N+(a).)
+template <int MODE>
+__device__ __forceinline__ uint32_t tiny_source(int32_t u, const CsrView& g, const Sink& sk) {
+  const int32_t n = (int32_t)g.n;
+  const int64_t beg = __ldg(&g.off[u]);
+  const int64_t plen = __ldg(&g.off[u + 1]) - beg;
+  const int4* r4 = reinterpret_cast<const int4*>(g.col + beg);
+  const int4 q0 = __ldg(&r4[0]);
+  const int4 q1 = plen > 4 ? __ldg(&r4[1]) : make_int4(n, n, n, n);
+  const int32_t x[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+  const uint32_t* dense_words = reinterpret_cast<const uint32_t*>(g.dense);
+  uint32_t hits = 0;
+#pragma unroll
+  for (int i = 0; i < kTinyMaxDegree - 1; ++i) {
+    const int32_t a = x[i];
+    if (a >= n) break;  // pad ids end the row
+    int64_t wbase = -1;  // dense row: its word 0 relative to window word 0
+    if (g.dq0 != nullptr && a >= g.base_w) {
+      const int32_t dq = __ldg(&g.dq0[a - g.base_w]);
+      if (dq >= 0) wbase = 4 * ((int64_t)dq - ((a + 1 - g.base_w) >> 7));
+    }
+    int64_t lo = __ldg(&g.off[a]);
+    const int64_t end = __ldg(&g.off[a + 1]);
+#pragma unroll
+    for (int j = i + 1; j < kTinyMaxDegree; ++j) {
+      const int32_t b = x[j];
+      if (b >= n) break;
+      bool hit;
+      if (wbase >= 0) {
+        const int32_t t = b - g.base_w;
+        hit = (__ldg(&dense_words[wbase + (t >> 5)]) >> (t & 31)) & 1u;
+      } else {
+        int64_t hi = end;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi) >> 1;
+          if (__ldg(&g.col[mid]) < b)
+            lo = mid + 1;
+          else
+            hi = mid;
+        }
+        hit = lo < end && __ldg(&g.col[lo]) == b;
+      }
+      if (hit) {
+        ++hits;
+        if (MODE == kModeVertex) {
+          atomicAdd(&sk.pv[u], 1ull);
+          atomicAdd(&sk.pv[a], 1ull);
+          atomicAdd(&sk.pv[b], 1ull);
+        }
+      }
+    }
+  }
+  return hits;
+}
+
 // Shared-memory layout of the counting kernels.
 constexpr int kWarpBitmapWords = kWarpBitmapBits / 32 + kBitmapSlackWords;
 constexpr int kBlockBitmapWords = kBlockBitmapBits / 32 + kBitmapSlackWords;
@@ -554,8 +612,8 @@ __device__ __forceinline__ void zero_words(uint32_t* p, int nwords, int t, int s
   for (int i = t; i < nwords; i += stride) p[i] = 0u;
 }
 
-// Count the triangles of one graph: block-bin sources first (one CTA each), then warp-bin sources.
-// cursors[0], cursors[1]: zeroed work counters of this graph.  Returns this thread's count.
+// Count the triangles of one graph: block-bin sources first (one CTA each), then warp-bin sources, then thread-bin
+// sources (one lane each).  cursors[0..2]: zeroed work counters of this graph.  Returns this thread's count.
 template <int MODE>
 __device__ __forceinline__ unsigned long long count_graph(const CsrView& g, const Sink& sk,
                                                           uint32_t* cursors, uint32_t* smem, uint32_t* ws,
@@ -592,6 +650,15 @@ __device__ __forceinline__ unsigned long long count_graph(const CsrView& g, cons
       if (idx >= g.nw) break;
       const int e = min(idx + kChunk, g.nw);
       for (int k = idx; k < e; ++k) acc += warp_source<MODE>(wlist[k], g, region, ltab, r, sk);
+    }
+  }
+  if (g.nt > 0) {  // thread bin: 32 sources per warp, one per lane
+    while (true) {
+      int idx = 0;
+      if (lane == 0) idx = (int)atomicAdd(&cursors[2], 32u);
+      idx = __shfl_sync(kFull, idx, 0);
+      if (idx >= g.nt) break;
+      if (idx + lane < g.nt) acc += tiny_source<MODE>(g.tlist[idx + lane], g, sk);
     }
   }
   return acc;

@@ -93,9 +93,11 @@ struct CsrView {
   const int32_t* dq0;   // n - base_w entries: first quad of v's dense row in `dense`, or -1; null if none
   const int4* dense;    // dense row bitmaps, 128 ids per quad
   int32_t dq_delta;     // (base_w - base_b) / 128
-  int32_t pad;
+  int32_t nt;           // thread-bin sources
+  const int32_t* tlist; // thread-bin sources: few out-neighbours, each pair tested by one lookup
 };
 constexpr int kDenseMinDegree = 16;  // rows with fewer entries stay id lists
+constexpr int kTinyMaxDegree = 8;    // thread-bin sources have at most this many out-neighbours
 
 // ------------------------------------------------------------------------------------------------------------
 // Primitives (tc_prims.cu)
@@ -135,6 +137,8 @@ struct tc_graph {
   tc::Buf off;               // int64[n+1], padded row offsets
   tc::Buf col;               // int32[csr_entries + 4]
   tc::Buf list;              // int32[n]: block bin at the front, warp bin at the back
+  tc::Buf tlist;             // int32[n]: thread bin
+  int64_t nt = 0;
   tc::Buf perm;              // int32[n]: perm[r] = original id of the vertex of rank r
   tc::Buf acc;               // uint64 scratch word(s) for counting: [0] total, [1..2] work cursors
   tc::Buf dq0;               // int32[n - base_w]: dense row start (quads) or -1
@@ -159,7 +163,8 @@ struct tc_graph {
     v.dq0 = dense_rows > 0 ? dq0.as<int32_t>() : nullptr;
     v.dense = dense.as<int4>();
     v.dq_delta = (v.base_w - v.base_b) >> 7;
-    v.pad = 0;
+    v.nt = (int32_t)nt;
+    v.tlist = tlist.as<int32_t>();
     return v;
   }
 };

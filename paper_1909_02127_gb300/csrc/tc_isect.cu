@@ -6,7 +6,7 @@
 // the part of N+(u) above v can meet N+(v) (rows hold ascending ranks and every w in N+(v) is above v), so the
 // lane that owns the edge at position i of N+(u) intersects N+(v) with N+(u)[i+1 ..].
 //
-// Layout of the work: a warp takes sources four at a time from an atomic cursor over the active sources (both bins
+// Layout of the work: a warp takes sources four at a time from an atomic cursor over the active sources (all bins
 // of tc_build), stages N+(u) in shared memory when it fits (1024 ranks per warp), and its lanes take the edges
 // u -> v of that source one each.  A lane walks the shorter of its two lists and finds each entry in the longer by
 // galloping from the previous hit (both lists ascend), so an edge costs about min(a, b) * log(max(a, b) / min(a, b))
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kIsThreads, 2)
   unsigned long long* part = reinterpret_cast<unsigned long long*>(is_smem + kIsWarps * kIsStage);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int32_t pad = (int32_t)g.n;
-  const int64_t sources = (int64_t)g.nb + g.nw;
+  const int64_t sources = (int64_t)g.nb + g.nw + g.nt;
   uint64_t mine = 0;
   for (;;) {
     uint32_t first = 0;
@@ -101,7 +101,9 @@ __global__ void __launch_bounds__(kIsThreads, 2)
     if ((int64_t)first >= sources) break;
     const int64_t last = (int64_t)first + kIsChunk < sources ? (int64_t)first + kIsChunk : sources;
     for (int64_t k = first; k < last; ++k) {
-      const int32_t u = k < g.nb ? g.list[k] : g.list[g.n - g.nw + (k - g.nb)];
+      const int32_t u = k < g.nb ? g.list[k]
+                        : k < (int64_t)g.nb + g.nw ? g.list[g.n - g.nw + (k - g.nb)]
+                                                   : g.tlist[k - g.nb - g.nw];
       const int64_t base = g.off[u];
       const int32_t du = true_len(g.off, g.col, pad, u);
       const bool staged = du <= kIsStage;
@@ -134,9 +136,9 @@ __global__ void __launch_bounds__(kIsThreads, 2)
 
 tc_status launch_count_isect(const tc_graph* g, uint64_t* d_total, uint32_t* d_cursor, cudaStream_t s) {
   TC_CUDA(cudaMemsetAsync(d_total, 0, sizeof(uint64_t), s));
-  if (g->nb + g->nw == 0) return TC_OK;
+  if (g->nb + g->nw + g->nt == 0) return TC_OK;
   TC_CUDA(cudaMemsetAsync(d_cursor, 0, sizeof(uint32_t), s));
-  const int64_t want = (g->nb + g->nw + kIsChunk * kIsWarps - 1) / (kIsChunk * kIsWarps);
+  const int64_t want = (g->nb + g->nw + g->nt + kIsChunk * kIsWarps - 1) / (kIsChunk * kIsWarps);
   const int grid = (int)(want < 2 * kNumSMs ? (want < 1 ? 1 : want) : 2 * kNumSMs);
   TC_CUDA(cudaFuncSetAttribute(k_count_isect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIsSmem));
   k_count_isect<<<grid, kIsThreads, kIsSmem, s>>>(g->view(), (unsigned long long*)d_total, d_cursor);

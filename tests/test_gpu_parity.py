@@ -396,3 +396,26 @@ def test_build_then_count_on_another_stream(tc, scale):
             assert int(out.item()) == T
         finally:
             tc.tc_free(g)
+
+
+@pytest.mark.parametrize("scale,ef", [(14, 4), (16, 8), (18, 16)])
+def test_thread_bin_sources(tc, scale, ef):
+    """Sparse R-MAT graphs put many sources in the thread bin (a handful of out-neighbours next to heavy rows): one
+    lane tests each pair of their out-neighbours by a lookup.  Totals, per-vertex counts and batches stay exact."""
+    src, dst = graphgen.rmat(scale, ef, 2300 + scale).edges()
+    n = 1 << scale
+    T, m, t = oracle.count(src, dst, n, per_vertex=True)
+    g = tc.tc_load_edges(src, dst, n)
+    try:
+        tc.tc_build(g)
+        info = tc.tc_graph_get_info(g)
+        assert info["bin_thread"] > 0
+        assert info["bin_thread"] + info["bin_warp"] + info["bin_block"] == info["active_sources"]
+        assert tc.tc_count(g) == T
+        T2, t2 = tc.tc_count_per_vertex(g)
+        assert T2 == T
+        np.testing.assert_array_equal(t2, t)
+        assert tc.tc_count_intersect(g) == T
+        assert int(tc.tc_count_batch([g, g])[1]) == T
+    finally:
+        tc.tc_free(g)
