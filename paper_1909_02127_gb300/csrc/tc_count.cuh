@@ -520,9 +520,15 @@ __device__ __forceinline__ uint32_t tiny_source(int32_t u, const CsrView& g, con
   const int64_t beg = __ldg(&g.off[u]);
   const int64_t plen = __ldg(&g.off[u + 1]) - beg;
   const int4* r4 = reinterpret_cast<const int4*>(g.col + beg);
-  const int4 q0 = __ldg(&r4[0]);
-  const int4 q1 = plen > 4 ? __ldg(&r4[1]) : make_int4(n, n, n, n);
-  const int32_t x[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+  int32_t x[kTinyMaxDegree];
+#pragma unroll
+  for (int q = 0; q < kTinyMaxDegree / 4; ++q) {
+    const int4 v4 = 4 * q < plen ? __ldg(&r4[q]) : make_int4(n, n, n, n);
+    x[4 * q] = v4.x;
+    x[4 * q + 1] = v4.y;
+    x[4 * q + 2] = v4.z;
+    x[4 * q + 3] = v4.w;
+  }
   const uint32_t* dense_words = reinterpret_cast<const uint32_t*>(g.dense);
   uint32_t hits = 0;
 #pragma unroll
