@@ -92,6 +92,8 @@ typedef struct tc_graph_info {
  *                struct is copied; its functions must stay valid until tc_free.
  *   out          receives the new graph handle (set to NULL on failure).
  * Self-loops and repeated pairs are accepted and removed by tc_build (the simple-graph reading of Def. 1).
+ * Host arrays that are page-locked and mapped into the device's address space (cudaHostAlloc / pinned tensors)
+ * are read by the device directly; other host arrays are copied through a device staging buffer.
  * Synchronises `stream` once (to report out-of-range ids).
  */
 TC_API tc_status tc_load_edges(const int32_t* src, const int32_t* dst, int64_t num_edges, int64_t num_vertices,

@@ -174,6 +174,38 @@ void release_all(tc_graph* g, cudaStream_t s) {
   }
 }
 
+// The device address of the host array p[0, len) when all of it is page-locked memory mapped into the device's
+// address space (as cudaHostAlloc gives under unified addressing), else null.  Both ends are checked, so an array
+// that runs past a registered range is never read by the device.
+const int32_t* mapped_for_device(const int32_t* p, int64_t len) {
+  cudaPointerAttributes a{}, b{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess || cudaPointerGetAttributes(&b, p + (len - 1)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer || !b.devicePointer)
+    return nullptr;
+  const int32_t* da = static_cast<const int32_t*>(a.devicePointer);
+  if (static_cast<const int32_t*>(b.devicePointer) != da + (len - 1)) return nullptr;
+  return da;
+}
+
+// Host arrays streamed through a device staging buffer (`stage`, allocated here) in chunks.
+tc_status pack_staged(tc_graph* g, const int32_t* src, const int32_t* dst, int64_t num_edges, uint32_t* d_err,
+                      Buf& stage, cudaStream_t s) {
+  const int64_t chunk = num_edges < (int64_t)(1 << 24) ? num_edges : (int64_t)(1 << 24);
+  TC_TRY(buf_alloc(g->alloc, stage, (size_t)chunk * 8, s));
+  int32_t* ds = stage.as<int32_t>();
+  int32_t* dd = ds + chunk;
+  for (int64_t o = 0; o < num_edges; o += chunk) {
+    const int64_t len = num_edges - o < chunk ? num_edges - o : chunk;
+    TC_CUDA(cudaMemcpyAsync(ds, src + o, (size_t)len * 4, cudaMemcpyHostToDevice, s));
+    TC_CUDA(cudaMemcpyAsync(dd, dst + o, (size_t)len * 4, cudaMemcpyHostToDevice, s));
+    TC_TRY(pack_edges(g, ds, dd, len, o, d_err, s));
+  }
+  return TC_OK;
+}
+
 tc_status check_built(const tc_graph* g) {
   if (!g) {
     set_error("graph handle is NULL");
@@ -297,19 +329,15 @@ TC_API tc_status tc_load_edges(const int32_t* src, const int32_t* dst, int64_t n
     if (flags == TC_PTR_DEVICE) {
       if ((st = pack_edges(g, src, dst, num_edges, 0, err.as<uint32_t>(), s))) break;
     } else {
-      // host arrays: stream them through a device staging buffer in chunks
-      const int64_t chunk = num_edges < (int64_t)(1 << 24) ? num_edges : (int64_t)(1 << 24);
-      if ((st = buf_alloc(g->alloc, stage, (size_t)chunk * 8, s))) break;
-      int32_t* ds = stage.as<int32_t>();
-      int32_t* dd = ds + chunk;
-      for (int64_t o = 0; o < num_edges && st == TC_OK; o += chunk) {
-        const int64_t len = num_edges - o < chunk ? num_edges - o : chunk;
-        st = cuda_status(cudaMemcpyAsync(ds, src + o, (size_t)len * 4, cudaMemcpyHostToDevice, s), "H2D src");
-        if (st == TC_OK)
-          st = cuda_status(cudaMemcpyAsync(dd, dst + o, (size_t)len * 4, cudaMemcpyHostToDevice, s), "H2D dst");
-        if (st == TC_OK) st = pack_edges(g, ds, dd, len, o, err.as<uint32_t>(), s);
+      const int32_t* msrc = mapped_for_device(src, num_edges);
+      const int32_t* mdst = msrc ? mapped_for_device(dst, num_edges) : nullptr;
+      if (msrc && mdst) {
+        // page-locked host arrays mapped into the device's address space: the ingest kernel reads them over the
+        // host link directly, with no staging copy
+        if ((st = pack_edges(g, msrc, mdst, num_edges, 0, err.as<uint32_t>(), s))) break;
+      } else if ((st = pack_staged(g, src, dst, num_edges, err.as<uint32_t>(), stage, s))) {
+        break;
       }
-      if (st) break;
     }
     if ((st = cuda_status(cudaMemcpyAsync(&h_err, err.p, 4, cudaMemcpyDeviceToHost, s), "copy err"))) break;
     if ((st = cuda_status(cudaStreamSynchronize(s), "tc_load_edges sync"))) break;

@@ -302,6 +302,32 @@ def test_host_and_device_inputs_and_allocators_agree(tc):
             assert gpu_counts(tc, hs, hd, spec.n, device=device, per_vertex=False, allocator=allocator)[0] == ref
 
 
+def test_pinned_host_inputs(tc):
+    """Page-locked host arrays are read by the device in place; a slice inside a larger pinned buffer, and a pinned
+    array paired with a pageable one (staged), give the same count; ids out of range are still reported."""
+    import torch
+    spec = graphgen.rmat(15, 12, 32)
+    hs, hd = spec.edges()
+    ref = oracle.count(hs, hd, spec.n)[0]
+    ps = torch.from_numpy(hs).pin_memory()
+    pd = torch.from_numpy(hd).pin_memory()
+    big = torch.zeros(2 * hs.size + 64, dtype=torch.int32).pin_memory()
+    big[32:32 + hs.size] = ps
+    big[hs.size + 48:hs.size + 48 + hd.size] = pd
+    cases = [(ps, pd), (big[32:32 + hs.size], big[hs.size + 48:hs.size + 48 + hd.size]), (ps, torch.from_numpy(hd))]
+    for s_, d_ in cases:
+        g = tc.tc_load_edges(s_, d_, spec.n)
+        try:
+            tc.tc_build(g)
+            assert tc.tc_count(g) == ref
+        finally:
+            tc.tc_free(g)
+    bad = ps.clone().pin_memory()
+    bad[7] = spec.n + 3
+    with pytest.raises(tc.TCError):
+        tc.tc_load_edges(bad, pd, spec.n)
+
+
 def test_errors(tc):
     import torch
     s = torch.tensor([0, 1, 5], dtype=torch.int32, device="cuda")
