@@ -44,7 +44,7 @@ def parse():
                    help="rmat20 | rmat26 | er4096 | batch | serve | unfused | prune | list | rmat<scale> (R-MAT, edge factor 16)")
     p.add_argument("--graph", default="rmat20", help="unfused, list: the graph")
     p.add_argument("--unfused-chunk-bytes", type=int, default=0,
-                   help="unfused: bytes one round-2 pass may hold (0: the largest pass)")
+                   help="unfused: bytes one hop-2 pass may hold (0: the largest pass)")
     p.add_argument("--batch-graphs", type=int, default=4096)
     p.add_argument("--rate", type=float, default=2000.0, help="serve: mean request arrivals per second")
     p.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
@@ -444,7 +444,7 @@ def run_unfused(args, dist: Dist):
     units, secs = aggregate(m * args.steps, sum(unf_ms) / 1e3, dist)
     t_unf = statistics.mean(unf_ms) / 1e3
     peak, peak_kind = measured_peaks()
-    # round-2 frontier bytes: per slot the column read, the keep-flag write, the scan's read and write of it and
+    # hop-2 frontier bytes: per slot the column read, the keep-flag write, the scan's read and write of it and
     # the compaction's read (5 x 4 B)
     frontier_bytes = 20 * stats["frontier2"]
     return {

@@ -201,11 +201,11 @@ TC_API tc_status tc_list_triangles(tc_graph* g, int64_t first_source, int64_t nu
 /* Frontier sizes of one tc_count_unfused call (all counts of slots or matches). */
 typedef struct tc_unfused_stats {
   int64_t candidates; /* |c_set|: sources u with d+(u) >= 2 after the NE filter */
-  int64_t frontier1;  /* round-1 advance slots: sum over c_set of d+(u) */
-  int64_t partials;   /* round-1 survivors (u, v) with d+(v) > 0 (the 1-look-ahead) */
-  int64_t frontier2;  /* round-2 advance slots: sum over the partials of d+(v) (the candidate 2-paths) */
-  int64_t matches;    /* round-2 survivors (u, v, w) with u -> w an edge: the triangle count */
-  int64_t chunks;     /* round-2 passes that the byte budget required */
+  int64_t frontier1;  /* hop-1 advance slots: sum over c_set of d+(u) */
+  int64_t partials;   /* hop-1 survivors (u, v) with d+(v) > 0 (the 1-look-ahead) */
+  int64_t frontier2;  /* hop-2 advance slots: sum over the partials of d+(v) (the candidate 2-paths) */
+  int64_t matches;    /* hop-2 survivors (u, v, w) with u -> w an edge: the triangle count */
+  int64_t chunks;     /* hop-2 passes that the byte budget required */
   int64_t peak_bytes; /* largest total of intermediate device buffers held at one time */
   int64_t reserved;
 } tc_unfused_stats;
@@ -214,15 +214,15 @@ typedef struct tc_unfused_stats {
  * tc_count_unfused — the same count by the paper's unfused verification loop (Algorithm 1, Sec. III-A/III-B):
  * a filter of candidate sources by NE, then two rounds of advance (one 32-bit frontier slot per traversed edge,
  * marked kept or masked by the constraint check), compaction of the kept slots (Compute) and their write to the
- * partial results.  Round 1 extends each source u by its out-neighbours v and keeps those with an out-neighbour
- * (1-look-ahead); round 2 extends each (u, v) by w in N+(v) and keeps those closed by the edge u -> w.  The result
+ * partial results.  Hop 1 extends each source u by its out-neighbours v and keeps those with an out-neighbour
+ * (1-look-ahead); hop 2 extends each (u, v) by w in N+(v) and keeps those closed by the edge u -> w.  The result
  * equals tc_count.  It exists to measure what fusion saves: its frontiers hold W slots where tc_count writes none.
  *   out_total        host pointer: T.
- *   max_chunk_bytes  bytes that one round-2 pass may hold (4 per slot plus 12 per surviving match); the round-2
+ *   max_chunk_bytes  bytes that one hop-2 pass may hold (4 per slot plus 12 per surviving match); the hop-2
  *                    frontier is cut into passes accordingly (at least 4096 and at most 2^31 - 1 slots per pass).
  *                    0: the largest pass.  Negative: TC_ERR_INVALID_ARG.
  *   stats            host pointer or NULL: frontier sizes and the peak bytes held.
- * Memory comes from the graph's allocator (TC_ERR_NO_MEMORY when a frontier does not fit).  Graphs whose round-1
+ * Memory comes from the graph's allocator (TC_ERR_NO_MEMORY when a frontier does not fit).  Graphs whose hop-1
  * frontier reaches 2^31 - 1 slots are rejected with TC_ERR_INVALID_ARG.  Blocks until the outputs are valid.
  */
 TC_API tc_status tc_count_unfused(tc_graph* g, uint64_t* out_total, int64_t max_chunk_bytes,

@@ -10,10 +10,10 @@ order that orients every edge towards the later vertex, the sizes of those front
 alone:
 
 * candidates  |{u : d+(u) >= 2}|                                    (NE filter, 2-look-ahead)
-* frontier1   sum of d+(u) over the candidates                       (round-1 advance: one slot per (u, v))
+* frontier1   sum of d+(u) over the candidates                       (hop-1 advance: one slot per (u, v))
 * partials    |{(u, v) : u a candidate, u -> v, d+(v) > 0}|          (1-look-ahead, compacted)
-* frontier2   sum of d+(v) over the partials                         (round-2 advance: one slot per (u, v, w))
-* matches     the triangle count (round-2 slots closed by u -> w)
+* frontier2   sum of d+(v) over the partials                         (hop-2 advance: one slot per (u, v, w))
+* matches     the triangle count (hop-2 slots closed by u -> w)
 
 The visiting order is the one the library documents for tc_build (a reading of Sec. III-C, which only needs a total
 order): vertices ascending by the number of input pairs at the vertex (self-loops excluded, repeated pairs counted

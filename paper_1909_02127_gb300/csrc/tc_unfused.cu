@@ -6,12 +6,12 @@
 // survivors (Compute), their write to the partial results and a mask of the incomplete ones (Sec. III-A/III-B).
 // On the oriented CSR of tc_build (the visiting order stands in for the UMO id constraint) the rounds are:
 //   filter    c_set = {u : d+(u) >= 2}                          NE filter with the 2-look-ahead (Sec. III-C)
-//   round 1   advance c_set over N+(u): one slot per (u, v), kept if d+(v) > 0 (the 1-look-ahead);
+//   hop 1   advance c_set over N+(u): one slot per (u, v), kept if d+(v) > 0 (the 1-look-ahead);
 //             compact the kept slots to the partial matches M2 = [(u, v)]
-//   round 2   advance M2 over N+(v): one slot per (u, v, w), kept if u -> w is an edge (the stored non-tree
+//   hop 2   advance M2 over N+(v): one slot per (u, v, w), kept if u -> w is an edge (the stored non-tree
 //             connection); compact the kept slots to the complete matches M3 = [(u, v, w)]
 //   result    |M3| triangles (|M|/|Q| with M counted in nodes)
-// Each frontier holds one 32-bit slot per traversed edge: the memory the fused kernel never writes.  Round 2 has
+// Each frontier holds one 32-bit slot per traversed edge: the memory the fused kernel never writes.  Hop 2 has
 // W = sum over M2 of d+(v) slots; it runs in chunks whose slots and survivors fit the caller's budget (the paper
 // keeps the frontier whole), at most 2^31 - 1 slots per chunk because positions come from a 32-bit scan.
 #include <cstring>
@@ -47,7 +47,7 @@ __device__ __forceinline__ int64_t row_of(const int64_t* __restrict__ o, int64_t
   return lo;
 }
 
-// Filter: the sizes of the round-1 frontier rows (0 for u outside c_set) and |c_set|.
+// Filter: the sizes of the hop-1 frontier rows (0 for u outside c_set) and |c_set|.
 __global__ void k_uf_filter(const int64_t* __restrict__ off, const int32_t* __restrict__ col, int64_t n,
                             int32_t* __restrict__ sz, unsigned long long* __restrict__ candidates) {
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
@@ -75,7 +75,7 @@ __device__ __forceinline__ TileRange tile_rows(const int64_t* o, int64_t rows, i
   return r;
 }
 
-// Round 1 advance: slot e is (u, v) with v the (e - o1[u])-th out-neighbour of u; kept if v has out-neighbours.
+// Hop 1 advance: slot e is (u, v) with v the (e - o1[u])-th out-neighbour of u; kept if v has out-neighbours.
 __global__ void __launch_bounds__(kUfThreads) k_uf_advance1(const int64_t* __restrict__ o1, int64_t n,
                                                             const int64_t* __restrict__ off,
                                                             const int32_t* __restrict__ col, int64_t E1,
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kUfThreads) k_uf_advance1(const int64_t* __res
   }
 }
 
-// Round 1 compaction: kept slots to M2 at their scanned positions.
+// Hop 1 compaction: kept slots to M2 at their scanned positions.
 __global__ void __launch_bounds__(kUfThreads) k_uf_compact1(const int64_t* __restrict__ o1, int64_t n,
                                                             const int64_t* __restrict__ off,
                                                             const int32_t* __restrict__ col, int64_t E1,
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kUfThreads) k_uf_compact1(const int64_t* __res
   }
 }
 
-// Sizes of the round-2 frontier rows: d+(v) for each partial match (u, v).
+// Sizes of the hop-2 frontier rows: d+(v) for each partial match (u, v).
 __global__ void k_uf_sizes2(const int32_t* __restrict__ m2v, int64_t P2, const int64_t* __restrict__ off,
                             const int32_t* __restrict__ col, int32_t pad, int32_t* __restrict__ sz) {
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < P2; j += (int64_t)gridDim.x * blockDim.x)
@@ -136,7 +136,7 @@ __device__ __forceinline__ bool has_edge(const int64_t* __restrict__ off, const 
   return lo < end && col[lo] == w;
 }
 
-// Round 2 advance over slots [c0, c0 + cnt): slot e is (u, v, w) with w the (e - o2[j])-th out-neighbour of v for
+// Hop 2 advance over slots [c0, c0 + cnt): slot e is (u, v, w) with w the (e - o2[j])-th out-neighbour of v for
 // the partial match j = (u, v); kept if the closing edge u -> w exists.
 __global__ void __launch_bounds__(kUfThreads) k_uf_advance2(const int64_t* __restrict__ o2, int64_t P2,
                                                             const int32_t* __restrict__ m2u,
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kUfThreads) k_uf_advance2(const int64_t* __res
   }
 }
 
-// Round 2 compaction: kept slots to M3 as (u, v, w) rank triples.
+// Hop 2 compaction: kept slots to M3 as (u, v, w) rank triples.
 __global__ void __launch_bounds__(kUfThreads) k_uf_compact2(const int64_t* __restrict__ o2, int64_t P2,
                                                             const int32_t* __restrict__ m2u,
                                                             const int32_t* __restrict__ m2v,
@@ -249,11 +249,11 @@ tc_status run_unfused(tc_graph* g, int64_t max_chunk_bytes, tc_unfused_stats* st
     const int64_t E1 = st->frontier1;
     if (E1 == 0) break;
     if (E1 >= kUfMaxChunk) {
-      set_error("tc_count_unfused: the round-1 frontier exceeds 2^31 - 1 slots");
+      set_error("tc_count_unfused: the hop-1 frontier exceeds 2^31 - 1 slots");
       rc = TC_ERR_INVALID_ARG;
       break;
     }
-    // round 1: advance, compact
+    // hop 1: advance, compact
     if (fail(h.take(keep1, (size_t)(E1 + 1) * 4)) != TC_OK) break;
     if (fail(cuda_status(cudaMemsetAsync(keep1.as<uint32_t>() + E1, 0, 4, s), "memset")) != TC_OK) break;
     k_uf_advance1<<<tiles_grid(E1), kUfThreads, 0, s>>>(o1.as<int64_t>(), n, off, col, E1, keep1.as<uint32_t>());
@@ -270,7 +270,7 @@ tc_status run_unfused(tc_graph* g, int64_t max_chunk_bytes, tc_unfused_stats* st
     if (fail(cuda_status(cudaGetLastError(), "k_uf_compact1")) != TC_OK) break;
     h.drop(keep1);
     h.drop(o1);
-    // round 2: row sizes, then advance + compaction per chunk
+    // hop 2: row sizes, then advance + compaction per chunk
     if (fail(h.take(sz2, (size_t)P2 * 4)) != TC_OK || fail(h.take(o2, (size_t)(P2 + 1) * 8)) != TC_OK) break;
     k_uf_sizes2<<<grid_for(P2, 256), 256, 0, s>>>(m2v.as<int32_t>(), P2, off, col, pad, sz2.as<int32_t>());
     note_launch();

@@ -2,7 +2,7 @@
 
 CPU: the frontier-size definitions in oracle/frontiers.py against closed forms (K_n, stars, disjoint unions) and a
 loop enumeration on random tiny graphs.  GPU: tc_count_unfused through the C ABI against the oracle's count and the
-frontier sizes, whole and cut into many round-2 passes, and its argument errors.
+frontier sizes, whole and cut into many hop-2 passes, and its argument errors.
 """
 import math
 
@@ -21,7 +21,7 @@ from tests import graphs
 @pytest.mark.parametrize("n", [3, 4, 5, 9, 30])
 def test_frontiers_of_a_clique(n):
     """K_n: every vertex has the same count, so the order is by id and d+(i) = n-1-i.  Candidates are i <= n-3;
-    round 1 has sum_{d=2}^{n-1} d slots; the partials are i < j <= n-2; round 2 reaches every i < j < k, all
+    hop 1 has sum_{d=2}^{n-1} d slots; the partials are i < j <= n-2; hop 2 reaches every i < j < k, all
     closed: C(n,3) slots."""
     src, dst, n, T, _ = graphs.complete(n)
     f = frontiers.unfused_frontiers(src, dst, n)
@@ -55,7 +55,7 @@ def test_frontiers_against_enumeration(seed):
     f = frontiers.unfused_frontiers(src, dst, n)
     assert f == frontiers.unfused_frontiers_brute(src, dst, n)
     T, _ = oracle.count(src, dst, n)
-    assert f["frontier2"] >= T  # every triangle is one closed round-2 slot
+    assert f["frontier2"] >= T  # every triangle is one closed hop-2 slot
 
 
 # ---------------------------------------------------------------------------------------------------------------
@@ -100,12 +100,12 @@ def test_gpu_unfused_matches_oracle(tc, name, make):
     src, dst, n = make()
     st = _check(tc, src, dst, n)
     assert st["chunks"] == (1 if st["frontier2"] > 0 else 0)
-    assert st["peak_bytes"] >= 4 * st["frontier2"]  # the round-2 frontier is held whole
+    assert st["peak_bytes"] >= 4 * st["frontier2"]  # the hop-2 frontier is held whole
 
 
 @pytest.mark.gpu
 def test_gpu_unfused_in_many_passes(tc):
-    """A small budget cuts round 2 into passes of 4096 slots; rows of the frontier straddle the cuts."""
+    """A small budget cuts hop 2 into passes of 4096 slots; rows of the frontier straddle the cuts."""
     src, dst = graphgen.rmat(13, 16, 74).edges()
     n = 1 << 13
     st = _check(tc, src, dst, n, budget=16 * 4096)
