@@ -7,8 +7,8 @@
 // Nothing is materialised: the 2-paths live in registers only, so Algorithm 1's Compute / Write_to_Partial /
 // Mask steps, which exist to store and compact intermediate matches, have no counterpart here.
 //
-// Closing test.  Vertices are numbered by rank in the (degree, id) order, so the ids that occur most often as w
-// (targets of hub rows) are the highest ones.  N+(u) is marked in a shared-memory bitmap over the top ids
+// Closing test.  Vertices are numbered by rank in the (input-pair count, id) order, so the ids that occur most
+// often as w (targets of hub rows) are the highest ones.  N+(u) is marked in a shared-memory bitmap over the top ids
 // [base, n] (4 KB per warp, or 64 KB per CTA for heavy sources); a test is one shared load and a bit extract.
 // The entries of N+(u) below base (a prefix of the sorted row) go into a small shared-memory hash (128 slots per
 // warp, 2048 per CTA), or, if they do not fit, are found by binary search in the row.  Pad entries (id n) fall
@@ -21,6 +21,8 @@
 // window, and a lane's owner is the current row plus the number of starts below it (a popcount).  In block mode
 // the long rows of a 512-row chunk are handed to warps one at a time from a shared-memory counter, so no warp
 // waits at the chunk barrier behind another's long rows, and the short rows' stream is cut into equal shares.
+// Dense hub rows are tested 128 ids at a time against the bitmap (dense_walk), and sources with few out-neighbours
+// are counted one per lane by pairwise lookups (tiny_source).
 #pragma once
 
 #include "tc_internal.cuh"
