@@ -200,6 +200,25 @@ def test_rmat20_full(tc):
         np.testing.assert_array_equal(gt, t)
     finally:
         tc.tc_free(g)
+    # the same graph with heavy sources in the block bin: n > 2^19, so the block bitmap starts above 0 and dense
+    # rows are addressed through the offset between the two windows
+    saved = tc.tc_get_tuning()
+    try:
+        tc.tc_set_tuning([(1 << 62, 1 << 13)])
+        g = tc.tc_load_edges(ds, dd, spec.n)
+        try:
+            tc.tc_build(g)
+            info = tc.tc_graph_get_info(g)
+            assert info["bin_block"] > 0 and info["dense_rows"] > 0
+            assert tc.tc_count(g) == T
+            T2, gt = tc.tc_count_per_vertex(g)
+            assert T2 == T
+            np.testing.assert_array_equal(gt, t)
+            assert int(tc.tc_count_batch([g])[0]) == T
+        finally:
+            tc.tc_free(g)
+    finally:
+        tc.tc_set_tuning(saved)
 
 
 def _repeat_heavy_pairs():
