@@ -16,6 +16,14 @@ __global__ void __launch_bounds__(kCountThreads, 2)
   __shared__ uint32_t ws[32];
   __shared__ unsigned long long red[kWarpsPerCTA];
   __shared__ int s_idx;
+  int nhub = 0;
+  if (MODE == dev::kModeVertex) {  // zeroed hub counters after the counting layout
+    sk.hub = smem + dev::kCountSmem / 4;
+    sk.hub0 = g.n > dev::kHubRanks ? (int32_t)(g.n - dev::kHubRanks) : 0;
+    nhub = (int)(g.n - sk.hub0);
+    for (int i = threadIdx.x; i < nhub; i += kCountThreads) sk.hub[i] = 0u;
+    __syncthreads();
+  }
   unsigned long long acc = dev::count_graph<MODE>(g, sk, cursors, smem, ws, &s_idx);
   acc = warp_sum(acc);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -24,6 +32,12 @@ __global__ void __launch_bounds__(kCountThreads, 2)
     unsigned long long s = 0;
     for (int w = 0; w < kWarpsPerCTA; ++w) s += red[w];
     if (s) atomicAdd(total, s);
+  }
+  if (MODE == dev::kModeVertex) {  // every add of this CTA is in (the barrier above)
+    for (int i = threadIdx.x; i < nhub; i += kCountThreads) {
+      const uint32_t c = sk.hub[i];
+      if (c) atomicAdd(&sk.pv[sk.hub0 + i], (unsigned long long)c);
+    }
   }
 }
 
@@ -45,9 +59,9 @@ tc_status launch_count(const tc_graph* g, uint64_t* d_total, uint64_t* d_per_ver
   if (d_per_vertex) {
     sk.pv = (unsigned long long*)d_per_vertex;
     TC_CUDA(cudaFuncSetAttribute(k_count<dev::kModeVertex>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 dev::kCountSmem));
-    k_count<dev::kModeVertex><<<grid, kCountThreads, dev::kCountSmem, s>>>(g->view(), (unsigned long long*)d_total,
-                                                                           sk, d_cursors);
+                                 dev::kVertexSmem));
+    k_count<dev::kModeVertex><<<grid, kCountThreads, dev::kVertexSmem, s>>>(g->view(), (unsigned long long*)d_total,
+                                                                            sk, d_cursors);
   } else {
     TC_CUDA(cudaFuncSetAttribute(k_count<dev::kModeCount>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  dev::kCountSmem));

@@ -97,7 +97,30 @@ struct Sink {
   unsigned long long capacity = 0;       // kModeList: triples that fit in `tri`
   const int32_t* perm = nullptr;         // kModeList: rank -> original id
   int32_t u = 0;                         // kModeList: the current source
+  uint32_t* hub = nullptr;               // kModeVertex: this CTA's counters of t(x), x in [hub0, n) (shared memory)
+  int32_t hub0 = 0;
 };
+
+// kModeVertex: per-CTA shared-memory counters for the top kHubRanks ranks.  Ranks follow the input-pair count, so
+// these are the vertices in the most triangles, whose global counters would otherwise take most of the atomics
+// (on R-MAT 20 the top 5120 ranks take 81% of all t(x) increments).  20 KB per CTA keeps two CTAs on an SM.
+constexpr int kHubRanks = 5120;
+constexpr uint32_t kHubSpill = 1u << 31;
+
+// t(x) += k.  A top rank counts in the CTA's shared counter, which the kernel adds to pv when it ends; the add that
+// takes a counter to 2^31 moves 2^31 of it to pv at once, so no counter wraps.  Any other x adds to pv directly.
+__device__ __forceinline__ void vertex_add(const Sink& sk, int32_t x, uint32_t k) {
+  const int32_t h = x - sk.hub0;
+  if (h >= 0) {
+    const uint32_t old = atomicAdd(&sk.hub[h], k);
+    if (old < kHubSpill && old + k >= kHubSpill) {
+      atomicSub(&sk.hub[h], kHubSpill);
+      atomicAdd(&sk.pv[x], (unsigned long long)kHubSpill);
+    }
+  } else {
+    atomicAdd(&sk.pv[x], (unsigned long long)k);
+  }
+}
 
 // Append the closed 2-paths u->v->w of this lane (h_i marks w_i) to the list at the warp's output position (the
 // source's own range of the output, known from a counting pass), which advances past them.  Warp-collective:
@@ -134,15 +157,12 @@ __device__ __forceinline__ void list_hits(const int4 q, uint32_t h0, uint32_t h1
 template <int MODE, class C>
 __device__ __forceinline__ uint32_t test_quad(const int4 q, const C& c, const Sink& sk, int32_t v) {
   const uint32_t h0 = c(q.x), h1 = c(q.y), h2 = c(q.z), h3 = c(q.w);
-  if (MODE == kModeVertex) {
-    unsigned long long* pv = sk.pv;
-    if (h0) atomicAdd(&pv[q.x], 1ull);
-    if (h1) atomicAdd(&pv[q.y], 1ull);
-    if (h2) atomicAdd(&pv[q.z], 1ull);
-    if (h3) atomicAdd(&pv[q.w], 1ull);
-    const uint32_t s = h0 + h1 + h2 + h3;
-    if (s) atomicAdd(&pv[v], (unsigned long long)s);
-    return s;
+  if (MODE == kModeVertex) {  // t(w) here; the caller adds the row's hits to t(v)
+    if (h0) vertex_add(sk, q.x, 1u);
+    if (h1) vertex_add(sk, q.y, 1u);
+    if (h2) vertex_add(sk, q.z, 1u);
+    if (h3) vertex_add(sk, q.w, 1u);
+    return (h0 + h1) + (h2 + h3);
   }
   if (MODE == kModeList) list_hits(q, h0, h1, h2, h3, sk, v);
   return (h0 + h1) + (h2 + h3);
@@ -172,6 +192,10 @@ __device__ __forceinline__ uint32_t long_row(const int4* __restrict__ col4, uint
     } else {
       hits += test_quad<MODE>(a, c, sk, v);
     }
+  }
+  if (MODE == kModeVertex) {
+    const uint32_t s = warp_sum(hits);
+    if (lane == 0 && s) vertex_add(sk, v, s);
   }
   return hits;
 }
@@ -217,7 +241,9 @@ __device__ __forceinline__ uint32_t walk(const Rows& r, int R, uint32_t x0, uint
     } else if (x < x1) {
       const int own = cur + __popc(starts & lt);
       const int4 q = __ldg(&col4[r.q0[own] + (x - r.P[own])]);
-      hits += test_quad<MODE>(q, c, sk, MODE != kModeCount ? r.v[own] : 0);
+      const uint32_t h = test_quad<MODE>(q, c, sk, MODE != kModeCount ? r.v[own] : 0);
+      if (MODE == kModeVertex && h) vertex_add(sk, r.v[own], h);
+      hits += h;
     }
     cur += __popc(starts);
   }
@@ -398,7 +424,7 @@ __device__ __forceinline__ uint32_t warp_source(int32_t u, const CsrView& g, uin
   __syncwarp();
   if (MODE == kModeVertex) {
     const uint32_t s = warp_sum(hits);
-    if (lane == 0 && s) atomicAdd(&sk.pv[u], (unsigned long long)s);
+    if (lane == 0 && s) vertex_add(sk, u, s);
   }
   return hits;
 }
@@ -506,7 +532,7 @@ __device__ __forceinline__ uint32_t block_source(int32_t u, const CsrView& g, ui
   mark_row(row, len, g.n, g.base_b, bm, false, tid, kCountThreads);
   if (MODE == kModeVertex) {
     const uint32_t s = warp_sum(hits);
-    if (lane == 0 && s) atomicAdd(&sk.pv[u], (unsigned long long)s);
+    if (lane == 0 && s) vertex_add(sk, u, s);
   }
   __syncthreads();
   return hits;
@@ -566,13 +592,13 @@ __device__ __forceinline__ uint32_t tiny_source(int32_t u, const CsrView& g, con
       if (hit) {
         ++hits;
         if (MODE == kModeVertex) {
-          atomicAdd(&sk.pv[u], 1ull);
-          atomicAdd(&sk.pv[a], 1ull);
-          atomicAdd(&sk.pv[b], 1ull);
+          vertex_add(sk, a, 1u);
+          vertex_add(sk, b, 1u);
         }
       }
     }
   }
+  if (MODE == kModeVertex && hits) vertex_add(sk, u, hits);
   return hits;
 }
 
@@ -586,6 +612,9 @@ constexpr int kBlockRowWords = 3 * kBlockRows + 2 * kBlockRows + (kBlockRows + 1
 // (long, short, counter, dense)
 constexpr int kBlockSmem = (kBlockBitmapWords + kBlockRowWords + kBlockLowSlots) * 4;
 constexpr int kCountSmem = kBlockSmem > kWarpSmem ? kBlockSmem : kWarpSmem;
+constexpr int kVertexSmem = kCountSmem + kHubRanks * 4;  // kModeVertex: the hub counters follow
+// two CTAs per SM: dynamic + static (< 1 KB) + the 1 KB the runtime reserves per CTA, within 228 KB
+static_assert(2 * (kVertexSmem + 2048) <= 228 * 1024, "vertex-mode counting must keep two CTAs per SM");
 
 __device__ __forceinline__ Rows warp_rows(uint32_t* region) {
   Rows r;
