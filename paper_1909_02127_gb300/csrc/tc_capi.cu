@@ -499,8 +499,9 @@ TC_API tc_status tc_list_triangles(tc_graph* g, int64_t first_source, int64_t nu
     TC_TRY(buf_alloc(g->alloc, tmp, (size_t)capacity * 12, s));
     d_tri = tmp.as<int32_t>();
   }
-  uint64_t* words = g->acc.as<uint64_t>();  // [0]: found, [1]: work cursor
-  tc_status st = launch_list(g, first_source, num_sources, d_tri, capacity, words, words + 1, s);
+  uint64_t* words = g->acc.as<uint64_t>();  // [0]: found, [1..2]: four scratch words (work cursors)
+  tc_status st = launch_list(g, first_source, num_sources, d_tri, capacity, words,
+                             reinterpret_cast<uint32_t*>(words + 1), s);
   if (st == TC_OK) st = cuda_status(cudaMemcpyAsync(g->host_total, words, 8, cudaMemcpyDeviceToHost, s), "D2H found");
   if (st == TC_OK) st = cuda_status(cudaStreamSynchronize(s), "tc_list_triangles sync");
   if (st == TC_OK && host && capacity > 0) {

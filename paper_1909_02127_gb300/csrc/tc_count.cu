@@ -79,74 +79,148 @@ tc_status launch_count(const tc_graph* g, uint64_t* d_total, uint64_t* d_per_ver
 namespace tc {
 namespace {
 
-// Triangles whose first vertex in the visiting order lies in ranks [first, first + count), one source per warp,
-// four at a time from a cursor.  MODE kModeCount writes each source's number of triangles to cnt[k]; kModeList
-// writes them as triples starting at offs[k] (the exclusive scan of those counts), so each source fills its own
-// range of the output and no global cursor is contended.  A source with fewer than two out-neighbours closes no
-// 2-path.
+// A warp-bin source closing at least this many triangles is listed by a whole CTA: listing costs per triangle,
+// and the bins were cut by 2-paths, which dense rows make cheap to test but not to write out.
+constexpr uint32_t kListBlockMin = 16384;
+
+// Triangles whose first vertex in the visiting order lies in ranks [first, first + count), taken by the counting
+// kernel's bins: CTAs take the sources of blist one at a time, then warps take warp-bin sources four at a time,
+// then lanes take thread-bin sources; a source outside the range is skipped.  MODE kModeCount (blist: the block
+// bin) writes each source's number of triangles to cnt[u - first] (zeroed beforehand: a source in no bin closes no
+// 2-path).  kModeList (blist: k_list_heavy's list) writes them as triples from offs[u - first] on (the exclusive
+// scan of those counts), so each source fills its own range of the output and no global cursor is contended; it
+// skips sources with no triangle and leaves warp-bin sources with kListBlockMin or more to the CTAs.  The output
+// position of a source lives in shared memory (one per warp; one per CTA for a source of blist, whose warps
+// reserve runs of it with shared atomics).
 template <int MODE>
 __global__ void __launch_bounds__(kCountThreads, 2)
-    k_list(CsrView g, int64_t first, int64_t count, dev::Sink sk, unsigned long long* __restrict__ cursor,
-           uint32_t* __restrict__ cnt, const int64_t* __restrict__ offs) {
+    k_list(CsrView g, int64_t first, int64_t count, dev::Sink sk, uint32_t* __restrict__ cursors,
+           uint32_t* __restrict__ cnt, const int64_t* __restrict__ offs, const int32_t* __restrict__ blist,
+           const uint32_t* __restrict__ nblist) {
   extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ unsigned long long wpos[kWarpsPerCTA];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint32_t* region = smem + warp * dev::kWarpRegionWords;
-  const dev::Rows r = dev::warp_rows(region);
-  int32_t* ltab = dev::warp_low(region);
-  dev::zero_words(region, dev::kWarpBitmapWords, lane, 32);
-  for (int i = lane; i < kWarpLowSlots; i += 32) ltab[i] = -1;
-  sk.slot = &wpos[warp];
-  __syncwarp();
-  constexpr int kChunk = 4;
-  while (true) {
-    long long idx = 0;
-    if (lane == 0) idx = (long long)atomicAdd(cursor, (unsigned long long)kChunk);
-    idx = __shfl_sync(kFull, idx, 0);
-    if (idx >= count) break;
-    const int64_t e = idx + kChunk < count ? idx + kChunk : count;
-    for (int64_t k = idx; k < e; ++k) {
-      const int32_t u = (int32_t)(first + k);
-      const int64_t beg = __ldg(&g.off[u]);
-      if (__ldg(&g.off[u + 1]) - beg < 4 || __ldg(&g.col[beg + 1]) >= g.n) {  // d+(u) < 2
-        if (MODE == dev::kModeCount && lane == 0) cnt[k] = 0u;
-        continue;
-      }
+  __shared__ uint32_t ws[32];
+  __shared__ unsigned long long pos[kWarpsPerCTA + 1];  // [warp]: warp-bin sources; [kWarpsPerCTA]: block bin
+  __shared__ int s_idx;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t last = first + count;
+  const int nb = nblist ? (int)*nblist : g.nb;
+  if (nb > 0) {
+    const dev::BlockRows br = dev::block_rows(smem);
+    dev::zero_words(smem, dev::kBlockBitmapWords, tid, kCountThreads);
+    for (int i = tid; i < kBlockLowSlots; i += kCountThreads) br.ltab[i] = -1;
+    __syncthreads();
+    dev::Sink bsk = sk;
+    bsk.slot = &pos[kWarpsPerCTA];
+    while (true) {
+      if (tid == 0) s_idx = (int)atomicAdd(&cursors[0], 1u);
+      __syncthreads();
+      const int idx = s_idx;
+      __syncthreads();
+      if (idx >= nb) break;
+      const int32_t u = __ldg(&blist[idx]);
+      if (u < first || u >= last) continue;  // uniform over the CTA
       if (MODE == dev::kModeList) {
-        if (lane == 0) wpos[warp] = (unsigned long long)offs[k];
-        __syncwarp();
+        if (tid == 0) pos[kWarpsPerCTA] = (unsigned long long)offs[u - first];
+        __syncthreads();
       }
-      const uint32_t h = dev::warp_source<MODE>(u, g, region, ltab, r, sk);
+      const uint32_t h = dev::block_source<MODE>(u, g, smem, br, ws, bsk);
       if (MODE == dev::kModeCount) {
-        const uint32_t t = warp_sum(h);
-        if (lane == 0) cnt[k] = t;
+        uint32_t total;
+        block_exclusive_scan<uint32_t>(h, ws, &total);
+        if (tid == 0) cnt[u - first] = total;
       }
     }
+  }
+  if (g.nw > 0) {
+    uint32_t* region = smem + warp * dev::kWarpRegionWords;
+    const dev::Rows r = dev::warp_rows(region);
+    int32_t* ltab = dev::warp_low(region);
+    dev::zero_words(region, dev::kWarpBitmapWords, lane, 32);
+    for (int i = lane; i < kWarpLowSlots; i += 32) ltab[i] = -1;
+    __syncwarp();
+    dev::Sink wsk = sk;
+    wsk.slot = &pos[warp];
+    const int32_t* wlist = g.list + (g.n - g.nw);
+    constexpr int kChunk = 4;
+    while (true) {
+      int idx = 0;
+      if (lane == 0) idx = (int)atomicAdd(&cursors[1], (unsigned)kChunk);
+      idx = __shfl_sync(kFull, idx, 0);
+      if (idx >= g.nw) break;
+      const int e = min(idx + kChunk, g.nw);
+      for (int k = idx; k < e; ++k) {
+        const int32_t u = __ldg(&wlist[k]);
+        if (u < first || u >= last) continue;
+        if (MODE == dev::kModeList) {
+          const uint32_t c = __ldg(&cnt[u - first]);
+          if (c == 0 || c >= kListBlockMin) continue;
+          if (lane == 0) pos[warp] = (unsigned long long)offs[u - first];
+          __syncwarp();
+        }
+        const uint32_t h = dev::warp_source<MODE>(u, g, region, ltab, r, wsk);
+        if (MODE == dev::kModeCount) {
+          const uint32_t t = warp_sum(h);
+          if (lane == 0) cnt[u - first] = t;
+        }
+      }
+    }
+  }
+  if (g.nt > 0) {  // thread bin: one source per lane, its triangles written in order from its own offset
+    while (true) {
+      int idx = 0;
+      if (lane == 0) idx = (int)atomicAdd(&cursors[2], 32u);
+      idx = __shfl_sync(kFull, idx, 0);
+      if (idx >= g.nt) break;
+      if (idx + lane < g.nt) {
+        const int32_t u = __ldg(&g.tlist[idx + lane]);
+        if (u >= first && u < last) {
+          if (MODE == dev::kModeCount)
+            cnt[u - first] = dev::tiny_source<MODE>(u, g, sk);
+          else if (__ldg(&cnt[u - first]) > 0)
+            dev::tiny_source<MODE>(u, g, sk, (unsigned long long)offs[u - first]);
+        }
+      }
+    }
+  }
+}
+
+// The CTA work of the listing pass: the block-bin sources of the range that close a triangle and the warp-bin
+// sources that close at least kListBlockMin, appended to heavy in no particular order (*nheavy: zeroed count).
+__global__ void k_list_heavy(CsrView g, int64_t first, int64_t count, const uint32_t* __restrict__ cnt,
+                             int32_t* __restrict__ heavy, uint32_t* __restrict__ nheavy) {
+  const int64_t total = (int64_t)g.nb + g.nw;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const bool blk = i < g.nb;
+    const int32_t u = __ldg(&g.list[blk ? i : g.n - g.nw + (i - g.nb)]);
+    if (u < first || u >= first + count) continue;
+    const uint32_t c = __ldg(&cnt[u - first]);
+    if (blk ? c > 0 : c >= kListBlockMin) heavy[atomicAdd(nheavy, 1u)] = u;
   }
 }
 
 }  // namespace
 
 tc_status launch_list(const tc_graph* g, int64_t first, int64_t count, int32_t* d_triples, int64_t capacity,
-                      uint64_t* d_found, uint64_t* d_cursor, cudaStream_t s) {
+                      uint64_t* d_found, uint32_t* d_cursors, cudaStream_t s) {
   TC_CUDA(cudaMemsetAsync(d_found, 0, sizeof(uint64_t), s));
-  if (count <= 0) return TC_OK;
-  const int64_t want = (count + kWarpsPerCTA - 1) / kWarpsPerCTA;
-  const int grid = (int)(want < 2 * kNumSMs ? want : 2 * kNumSMs);
-  Buf cnt, offs;
+  if (count <= 0 || g->nb + g->nw + g->nt == 0) return TC_OK;
+  const int grid = count_grid(g);
+  Buf cnt, offs, heavy;
   tc_status st = TC_OK;
   do {
     // pass 1: triangles per source (the counting kernel's tests, dense rows included)
     if ((st = buf_alloc(g->alloc, cnt, (size_t)count * 4, s))) break;
     if ((st = buf_alloc(g->alloc, offs, (size_t)(count + 1) * 8, s))) break;
-    if ((st = cuda_status(cudaMemsetAsync(d_cursor, 0, sizeof(uint64_t), s), "memset cursor"))) break;
+    if ((st = buf_alloc(g->alloc, heavy, (size_t)(g->nb + g->nw + 1) * 4, s))) break;
+    if ((st = cuda_status(cudaMemsetAsync(cnt.p, 0, (size_t)count * 4, s), "memset counts"))) break;
+    if ((st = cuda_status(cudaMemsetAsync(d_cursors, 0, 3 * sizeof(uint32_t), s), "memset cursors"))) break;
     dev::Sink none;
     if ((st = cuda_status(cudaFuncSetAttribute(k_list<dev::kModeCount>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, dev::kWarpSmem),
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, dev::kCountSmem),
                           "k_list attribute")))
       break;
-    k_list<dev::kModeCount><<<grid, kCountThreads, dev::kWarpSmem, s>>>(
-        g->view(), first, count, none, (unsigned long long*)d_cursor, cnt.as<uint32_t>(), nullptr);
+    k_list<dev::kModeCount><<<grid, kCountThreads, dev::kCountSmem, s>>>(
+        g->view(), first, count, none, d_cursors, cnt.as<uint32_t>(), nullptr, g->list.as<int32_t>(), nullptr);
     note_launch();
     if ((st = cuda_status(cudaGetLastError(), "k_list count"))) break;
     // per-source output offsets; their total is the number found (per-source counts are below 2^31: C(d+, 2)
@@ -155,23 +229,31 @@ tc_status launch_list(const tc_graph* g, int64_t first, int64_t count, int32_t* 
     if ((st = cuda_status(cudaMemcpyAsync(d_found, offs.as<int64_t>() + count, 8, cudaMemcpyDeviceToDevice, s),
                           "copy found")))
       break;
+    // the CTAs' sources for pass 2 (their number in d_cursors[3])
+    if ((st = cuda_status(cudaMemsetAsync(d_cursors + 3, 0, sizeof(uint32_t), s), "memset heavy"))) break;
+    k_list_heavy<<<2 * kNumSMs, 256, 0, s>>>(g->view(), first, count, cnt.as<uint32_t>(), heavy.as<int32_t>(),
+                                            d_cursors + 3);
+    note_launch();
+    if ((st = cuda_status(cudaGetLastError(), "k_list_heavy"))) break;
     // pass 2: the triples, each source into its own range
     dev::Sink sk;
     sk.tri = d_triples;
     sk.capacity = (unsigned long long)(capacity > 0 ? capacity : 0);
     sk.perm = g->perm.as<int32_t>();
-    if ((st = cuda_status(cudaMemsetAsync(d_cursor, 0, sizeof(uint64_t), s), "memset cursor"))) break;
+    if ((st = cuda_status(cudaMemsetAsync(d_cursors, 0, 3 * sizeof(uint32_t), s), "memset cursors"))) break;
     if ((st = cuda_status(cudaFuncSetAttribute(k_list<dev::kModeList>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, dev::kWarpSmem),
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, dev::kCountSmem),
                           "k_list attribute")))
       break;
-    k_list<dev::kModeList><<<grid, kCountThreads, dev::kWarpSmem, s>>>(
-        g->view(), first, count, sk, (unsigned long long*)d_cursor, nullptr, offs.as<int64_t>());
+    k_list<dev::kModeList><<<grid, kCountThreads, dev::kCountSmem, s>>>(
+        g->view(), first, count, sk, d_cursors, cnt.as<uint32_t>(), offs.as<int64_t>(), heavy.as<int32_t>(),
+        d_cursors + 3);
     note_launch();
     st = cuda_status(cudaGetLastError(), "k_list");
   } while (0);
   buf_release(g->alloc, cnt, s);
   buf_release(g->alloc, offs, s);
+  buf_release(g->alloc, heavy, s);
   return st;
 }
 

@@ -93,10 +93,12 @@ enum Mode { kModeCount = 0, kModeVertex = 1, kModeList = 2 };
 struct Sink {
   unsigned long long* pv = nullptr;      // kModeVertex: t(x) in rank space
   int32_t* tri = nullptr;                // kModeList: triples of original ids, 3 per triangle
-  unsigned long long* slot = nullptr;    // kModeList: the warp's next output position (shared memory)
+  unsigned long long* slot = nullptr;    // kModeList: the next output position of this source (shared memory;
+                                         // one per warp, or one per CTA in block mode), advanced atomically
   unsigned long long capacity = 0;       // kModeList: triples that fit in `tri`
   const int32_t* perm = nullptr;         // kModeList: rank -> original id
   int32_t u = 0;                         // kModeList: the current source
+  int32_t pu = 0;                        // kModeList: its original id
   uint32_t* hub = nullptr;               // kModeVertex: this CTA's counters of t(x), x in [hub0, n) (shared memory)
   int32_t hub0 = 0;
 };
@@ -122,36 +124,99 @@ __device__ __forceinline__ void vertex_add(const Sink& sk, int32_t x, uint32_t k
   }
 }
 
-// Append the closed 2-paths u->v->w of this lane (h_i marks w_i) to the list at the warp's output position (the
-// source's own range of the output, known from a counting pass), which advances past them.  Warp-collective:
-// every lane calls it.
+// kModeList: triangle (u, v, w) as its sorted original ids at output position pos (nothing past the capacity).
+__device__ __forceinline__ void write_triple(const Sink& sk, unsigned long long pos, int32_t a, int32_t b,
+                                             int32_t w) {
+  if (pos >= sk.capacity) return;
+  const int32_t c = __ldg(&sk.perm[w]);
+  const int32_t lo = min(a, min(b, c)), hi = max(a, max(b, c));
+  int32_t* t = sk.tri + 3 * pos;
+  t[0] = lo;
+  t[1] = a + b + c - lo - hi;
+  t[2] = hi;
+}
+
+// Append the closed 2-paths u->v->w of this lane (h_i marks w_i) to the source's own range of the output (known
+// from a counting pass): one shared-memory atomic on the source's position reserves the warp's run, and the i-th
+// hits of all lanes go to consecutive positions in it (a ballot and a popcount each), so each round of stores
+// covers one contiguous run.  Warp-collective: every lane calls it.
 __device__ __forceinline__ void list_hits(const int4 q, uint32_t h0, uint32_t h1, uint32_t h2, uint32_t h3,
                                           const Sink& sk, int32_t v) {
-  const uint32_t cnt = h0 + h1 + h2 + h3;
+  const unsigned b0 = __ballot_sync(kFull, h0), b1 = __ballot_sync(kFull, h1);
+  const unsigned b2 = __ballot_sync(kFull, h2), b3 = __ballot_sync(kFull, h3);
+  const uint32_t n0 = __popc(b0), n01 = n0 + __popc(b1), n012 = n01 + __popc(b2);
+  const uint32_t total = n012 + __popc(b3);
+  if (total == 0) return;
+  unsigned long long base = 0;
+  if ((threadIdx.x & 31) == 0) base = atomicAdd(sk.slot, (unsigned long long)total);
+  base = __shfl_sync(kFull, base, 0);
+  if (!(h0 | h1 | h2 | h3)) return;
+  const unsigned lt = lanemask_lt();
+  const int32_t b = __ldg(&sk.perm[v]);
+  if (h0) write_triple(sk, base + __popc(b0 & lt), sk.pu, b, q.x);
+  if (h1) write_triple(sk, base + n0 + __popc(b1 & lt), sk.pu, b, q.y);
+  if (h2) write_triple(sk, base + n01 + __popc(b2 & lt), sk.pu, b, q.z);
+  if (h3) write_triple(sk, base + n012 + __popc(b3 & lt), sk.pu, b, q.w);
+}
+
+// Position of the k-th (from 0) set bit of x, which has more than k set bits: halve the window five times by the
+// population count of its lower half.
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t x, uint32_t k) {
+  uint32_t pos = 0;
+#pragma unroll
+  for (int w = 16; w > 0; w >>= 1) {
+    const uint32_t low = __popc(x & ((1u << w) - 1u));
+    if (k >= low) {
+      k -= low;
+      x >>= w;
+      pos += w;
+    }
+  }
+  return pos;
+}
+
+// Append the closed 2-paths u->v->w whose w are the set bits of this lane's m0..m3 (bit j of m_i is w = w0 + 32i + j)
+// as one run of the source's output, reserved with one shared-memory atomic.  The run is written 32 positions at a
+// time, one per lane: lane l takes position t = t0 + l, finds the lane owning it by binary search over the lanes'
+// inclusive prefix of bit counts, and the bit within that lane's 128 by population counts, so every pass stores 32
+// consecutive triples however unevenly the bits fall across lanes.  Warp-collective.  Returns this lane's number of
+// bits.
+__device__ __forceinline__ uint32_t list_bits(uint32_t m0, uint32_t m1, uint32_t m2, uint32_t m3, int32_t w0,
+                                              const Sink& sk, int32_t v) {
+  const uint32_t cnt = (__popc(m0) + __popc(m1)) + (__popc(m2) + __popc(m3));
   const uint32_t incl = warp_inclusive_scan(cnt);
   const uint32_t total = __shfl_sync(kFull, incl, 31);
-  if (total == 0) return;
-  const unsigned long long base = *sk.slot;
-  __syncwarp();
-  if ((threadIdx.x & 31) == 31) *sk.slot = base + total;
-  __syncwarp();
-  unsigned long long pos = base + incl - cnt;
-  const int32_t ws[4] = {q.x, q.y, q.z, q.w};
-  const uint32_t hs[4] = {h0, h1, h2, h3};
-  const int32_t a = __ldg(&sk.perm[sk.u]), b = __ldg(&sk.perm[v]);
+  if (total == 0) return 0;
+  const int lane = threadIdx.x & 31;
+  const int32_t pv = cnt ? __ldg(&sk.perm[v]) : 0;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(sk.slot, (unsigned long long)total);
+  base = __shfl_sync(kFull, base, 0);
+  for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+    const uint32_t t = t0 + lane;
+    int o = 0;  // the owner: the number of lanes whose inclusive prefix is <= t (at most 31, as t < incl[31] or unused)
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    if (!hs[i]) continue;
-    if (pos < sk.capacity) {  // the triangle as its sorted original ids
-      const int32_t c = __ldg(&sk.perm[ws[i]]);
-      const int32_t lo = min(a, min(b, c)), hi = max(a, max(b, c));
-      int32_t* t = sk.tri + 3 * pos;
-      t[0] = lo;
-      t[1] = a + b + c - lo - hi;
-      t[2] = hi;
+    for (int step = 16; step > 0; step >>= 1)
+      if (__shfl_sync(kFull, incl, o + step - 1) <= t) o += step;
+    const uint32_t k = t - (__shfl_sync(kFull, incl, o) - __shfl_sync(kFull, cnt, o));
+    const uint32_t a0 = __shfl_sync(kFull, m0, o), a1 = __shfl_sync(kFull, m1, o);
+    const uint32_t a2 = __shfl_sync(kFull, m2, o), a3 = __shfl_sync(kFull, m3, o);
+    const int32_t ow0 = __shfl_sync(kFull, w0, o), opv = __shfl_sync(kFull, pv, o);
+    if (t < total) {
+      const uint32_t p0 = __popc(a0), p1 = p0 + __popc(a1), p2 = p1 + __popc(a2);
+      int32_t w;
+      if (k < p0)
+        w = ow0 + (int32_t)nth_set_bit(a0, k);
+      else if (k < p1)
+        w = ow0 + 32 + (int32_t)nth_set_bit(a1, k - p0);
+      else if (k < p2)
+        w = ow0 + 64 + (int32_t)nth_set_bit(a2, k - p1);
+      else
+        w = ow0 + 96 + (int32_t)nth_set_bit(a3, k - p2);
+      write_triple(sk, base + t, sk.pu, opv, w);
     }
-    ++pos;
   }
+  return cnt;
 }
 
 template <int MODE, class C>
@@ -290,10 +355,60 @@ __device__ __forceinline__ uint32_t dense_walk(const Rows& r, int R, uint32_t x0
   return hits;
 }
 
-// Is v's row also stored as a dense bitmap?  Returns its first quad or -1 (always -1 outside count mode).
+// kModeList: dense_walk over rows whose r.v[k] holds v itself; each closed 2-path is appended with list_bits.  Quad
+// qi of v's row covers ids base_w + 128 * (sq + qi) + [0, 128), sq the warp-window quad of v + 1, and lines up with
+// quad sq + qi + delta of the source's bitmap.
+__device__ __forceinline__ uint32_t dense_list_walk(const Rows& r, int R, uint32_t x0, uint32_t x1,
+                                                    const int4* __restrict__ dense, const uint4* bm4, int32_t base_w,
+                                                    int32_t delta, const Sink& sk) {
+  uint32_t hits = 0;
+  if (x0 >= x1) return 0;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  int a = 0, b = R;
+  while (a < b) {
+    const int mid = (a + b) >> 1;
+    if (r.P[mid] <= x0)
+      a = mid + 1;
+    else
+      b = mid;
+  }
+  int cur = a - 1;
+  for (uint32_t xb = x0; xb < x1; xb += 32) {
+    const int j = cur + (lane == 0 ? 32 : lane);
+    uint32_t bit = 0;
+    if (j < R) {
+      const uint32_t pj = r.P[j];
+      if (pj <= xb + 32) bit = 1u << (pj - xb - 1);
+    }
+    const uint32_t starts = __reduce_or_sync(kFull, bit);
+    const uint32_t x = xb + lane;
+    uint32_t m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+    int32_t v = 0, w0 = 0;
+    if (x < x1) {
+      const int own = cur + __popc(starts & lt);
+      const uint32_t qi = x - r.P[own];
+      v = r.v[own];
+      const int32_t bq = ((v + 1 - base_w) >> 7) + (int32_t)qi;
+      const int4 q = __ldg(&dense[r.q0[own] + qi]);
+      const uint4 w = bm4[bq + delta];
+      m0 = (uint32_t)q.x & w.x;
+      m1 = (uint32_t)q.y & w.y;
+      m2 = (uint32_t)q.z & w.z;
+      m3 = (uint32_t)q.w & w.w;
+      w0 = base_w + 128 * bq;
+    }
+    hits += list_bits(m0, m1, m2, m3, w0, sk, v);
+    cur += __popc(starts);
+  }
+  return hits;
+}
+
+// Is v's row also stored as a dense bitmap?  Returns its first quad or -1 (always -1 in per-vertex mode, which
+// walks the id rows).
 template <int MODE>
 __device__ __forceinline__ int32_t dense_row(const CsrView& g, int32_t v) {
-  if (MODE != kModeCount || g.dq0 == nullptr || v < g.base_w || v >= g.n) return -1;
+  if (MODE == kModeVertex || g.dq0 == nullptr || v < g.base_w || v >= g.n) return -1;
   return __ldg(&g.dq0[v - g.base_w]);
 }
 
@@ -389,6 +504,24 @@ __device__ __forceinline__ uint32_t warp_hops(const CsrView& g, int64_t beg, int
         hits += dense_walk(r, __popc(dmask), 0, Q, g.dense, reinterpret_cast<const uint4*>(c.bm));
         __syncwarp();
       }
+    } else if (MODE == kModeList) {  // the same rows, r.v = v
+      const unsigned dmask = __ballot_sync(kFull, dense);
+      if (dmask) {
+        const int32_t sq = dense ? (v + 1 - g.base_w) >> 7 : 0;
+        const uint32_t nq = dense ? (uint32_t)(g.wtopq - sq) : 0u;
+        const uint32_t incl = warp_inclusive_scan(nq);
+        const uint32_t Q = __shfl_sync(kFull, incl, 31);
+        if (dense) {
+          const int k = __popc(dmask & lt);
+          r.q0[k] = (uint32_t)dq;
+          r.P[k] = incl - nq;
+          r.v[k] = v;
+        }
+        __syncwarp();
+        hits += dense_list_walk(r, __popc(dmask), 0, Q, g.dense, reinterpret_cast<const uint4*>(c.bm), g.base_w,
+                                c.delta, sk);
+        __syncwarp();
+      }
     }
   }
   return hits;
@@ -402,6 +535,7 @@ __device__ __forceinline__ uint32_t warp_source(int32_t u, const CsrView& g, uin
   const int lane = threadIdx.x & 31;
   Sink sk = sk_in;
   sk.u = u;
+  if (MODE == kModeList) sk.pu = __ldg(&sk.perm[u]);
   const int64_t beg = __ldg(&g.off[u]), len = __ldg(&g.off[u + 1]) - beg;
   const int32_t* row = g.col + beg;
   const uint32_t nlow = warp_sum(mark_row(row, len, g.n, g.base_w, bm, true, lane, 32));
@@ -459,7 +593,7 @@ __device__ __forceinline__ uint32_t block_hops(const CsrView& g, int64_t beg, in
     const uint32_t lrank = block_exclusive_scan<uint32_t>(is_long ? 1u : 0u, ws, &NL);
     const uint32_t srank = block_exclusive_scan<uint32_t>(is_short ? 1u : 0u, ws, &R);
     const uint32_t pre = block_exclusive_scan<uint32_t>(is_short ? ro.nq : 0u, ws, &Q);
-    if (MODE == kModeCount) {
+    if (MODE != kModeVertex) {
       const int32_t sq = dense ? (v + 1 - g.base_w) >> 7 : 0;
       const uint32_t nqd = dense ? (uint32_t)(g.wtopq - sq) : 0u;
       const uint32_t drank = block_exclusive_scan<uint32_t>(dense ? 1u : 0u, ws, &ND);
@@ -467,7 +601,7 @@ __device__ __forceinline__ uint32_t block_hops(const CsrView& g, int64_t beg, in
       if (dense) {
         br.dr.q0[drank] = (uint32_t)dq;
         br.dr.P[drank] = dpre;
-        br.dr.v[drank] = sq + c.delta;
+        br.dr.v[drank] = MODE == kModeList ? v : sq + c.delta;
       }
     }
     if (is_long) {
@@ -494,10 +628,14 @@ __device__ __forceinline__ uint32_t block_hops(const CsrView& g, int64_t beg, in
     const uint32_t per = (Q + kWarpsPerCTA - 1) / kWarpsPerCTA;
     const uint32_t x0 = min(Q, (uint32_t)warp * per), x1 = min(Q, x0 + per);
     hits += walk<MODE>(br.sr, (int)R, x0, x1, col4, c, sk, (int32_t)g.n);
-    if (MODE == kModeCount && QD > 0) {  // dense rows: equal shares of their quads
+    if (MODE != kModeVertex && QD > 0) {  // dense rows: equal shares of their quads
       const uint32_t dper = (QD + kWarpsPerCTA - 1) / kWarpsPerCTA;
       const uint32_t d0 = min(QD, (uint32_t)warp * dper), d1 = min(QD, d0 + dper);
-      hits += dense_walk(br.dr, (int)ND, d0, d1, g.dense, reinterpret_cast<const uint4*>(c.bm));
+      if (MODE == kModeCount)
+        hits += dense_walk(br.dr, (int)ND, d0, d1, g.dense, reinterpret_cast<const uint4*>(c.bm));
+      else
+        hits += dense_list_walk(br.dr, (int)ND, d0, d1, g.dense, reinterpret_cast<const uint4*>(c.bm), g.base_w,
+                                c.delta, sk);
     }
     __syncthreads();
   }
@@ -512,6 +650,7 @@ __device__ __forceinline__ uint32_t block_source(int32_t u, const CsrView& g, ui
   const int tid = threadIdx.x, lane = tid & 31;
   Sink sk = sk_in;
   sk.u = u;
+  if (MODE == kModeList) sk.pu = __ldg(&sk.perm[u]);
   const int64_t beg = __ldg(&g.off[u]), len = __ldg(&g.off[u + 1]) - beg;
   const int32_t* row = g.col + beg;
   uint32_t nlow;
@@ -541,9 +680,11 @@ __device__ __forceinline__ uint32_t block_source(int32_t u, const CsrView& g, ui
 // One thread-bin source u, one lane: N+(u) has at most kTinyMaxDegree entries (one or two padded quads), and the
 // triangles u < a < b are the pairs a < b of N+(u) with b in N+(a).  For each a the lane reads its row once: a dense
 // row answers each b with one bit; an id row by binary search, whose lower bound only moves forward because the
-// b's ascend.  (The per-pair form of the closing test: C(d, 2) lookups instead of walking every N+(a).)
+// b's ascend.  (The per-pair form of the closing test: C(d, 2) lookups instead of walking every N+(a).)  In list
+// mode the lane writes u's triangles to consecutive output positions from pos on.
 template <int MODE>
-__device__ __forceinline__ uint32_t tiny_source(int32_t u, const CsrView& g, const Sink& sk) {
+__device__ __forceinline__ uint32_t tiny_source(int32_t u, const CsrView& g, const Sink& sk,
+                                                unsigned long long pos = 0) {
   const int32_t n = (int32_t)g.n;
   const int64_t beg = __ldg(&g.off[u]);
   const int64_t plen = __ldg(&g.off[u + 1]) - beg;
@@ -559,10 +700,12 @@ __device__ __forceinline__ uint32_t tiny_source(int32_t u, const CsrView& g, con
   }
   const uint32_t* dense_words = reinterpret_cast<const uint32_t*>(g.dense);
   uint32_t hits = 0;
+  const int32_t pu = MODE == kModeList ? __ldg(&sk.perm[u]) : 0;
 #pragma unroll
   for (int i = 0; i < kTinyMaxDegree - 1; ++i) {
     const int32_t a = x[i];
     if (a >= n) break;  // pad ids end the row
+    const int32_t pa = MODE == kModeList ? __ldg(&sk.perm[a]) : 0;
     int64_t wbase = -1;  // dense row: its word 0 relative to window word 0
     if (g.dq0 != nullptr && a >= g.base_w) {
       const int32_t dq = __ldg(&g.dq0[a - g.base_w]);
@@ -595,6 +738,7 @@ __device__ __forceinline__ uint32_t tiny_source(int32_t u, const CsrView& g, con
           vertex_add(sk, a, 1u);
           vertex_add(sk, b, 1u);
         }
+        if (MODE == kModeList) write_triple(sk, pos++, pu, pa, b);
       }
     }
   }

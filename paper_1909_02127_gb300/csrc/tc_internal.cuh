@@ -182,7 +182,7 @@ tc_status launch_count(const tc_graph* g, uint64_t* d_total, uint64_t* d_per_ver
                        cudaStream_t s);
 int count_grid(const tc_graph* g);
 // Lists into d_triples (capacity triples) the triangles whose first vertex has rank in [first, first + count);
-// *d_found receives how many there are (also past capacity).  d_cursor: one scratch word.
+// *d_found receives how many there are (also past capacity).  d_cursors: four scratch words.
 tc_status launch_list(const tc_graph* g, int64_t first, int64_t count, int32_t* d_triples, int64_t capacity,
-                      uint64_t* d_found, uint64_t* d_cursor, cudaStream_t s);
+                      uint64_t* d_found, uint32_t* d_cursors, cudaStream_t s);
 }  // namespace tc

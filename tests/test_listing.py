@@ -20,6 +20,12 @@ def _as_set(tri):
     return set(map(tuple, np.asarray(tri).tolist()))
 
 
+def _sorted_rows(tri):
+    """The triples as one sorted int64 key each (ids < 2^21), for comparing millions of them."""
+    t = np.asarray(tri, dtype=np.int64)
+    return np.sort((t[:, 0] << 42) | (t[:, 1] << 21) | t[:, 2])
+
+
 @pytest.mark.parametrize("n", [3, 4, 7, 12])
 def test_oracle_lists_every_triple_of_a_clique(n):
     src, dst, n, T, _ = graphs.complete(n)
@@ -75,6 +81,8 @@ def test_gpu_listing_matches_oracle(tc, name, make):
     g = tc.tc_load_edges(src, dst, n)
     try:
         tc.tc_build(g)
+        if name == "rmat14":  # hub rows stored as bitmaps: listing expands their ANDs bit by bit
+            assert tc.tc_graph_get_info(g)["dense_rows"] > 0
         tri, found = tc.tc_list_triangles(g)
         assert found == T == len(tri)
         assert _as_set(tri) == _as_set(ref) and len(_as_set(tri)) == T
@@ -88,6 +96,28 @@ def test_gpu_listing_matches_oracle(tc, name, make):
         if T > 1:  # past its capacity the call writes what fits and still reports the total
             part, f = tc.tc_list_triangles(g, capacity=T // 2)
             assert f == T and len(part) == T // 2 and _as_set(part) <= _as_set(ref)
+    finally:
+        tc.tc_free(g)
+
+
+@pytest.mark.gpu
+def test_gpu_listing_rmat16_with_dense_rows(tc):
+    """Millions of triangles, most of them closed in dense hub rows; compared as sorted keys, each triple
+    ascending and listed once."""
+    src, dst = graphgen.rmat(16, 16, 65).edges()
+    n = 1 << 16
+    ref, T = oracle.list_triangles(src, dst, n)
+    g = tc.tc_load_edges(src, dst, n)
+    try:
+        tc.tc_build(g)
+        info = tc.tc_graph_get_info(g)
+        assert info["dense_rows"] > 0 and info["dense_wedges"] > 0
+        tri, found = tc.tc_list_triangles(g)
+        assert found == T == len(tri) and T > 10 ** 6
+        assert (tri[:, 0] < tri[:, 1]).all() and (tri[:, 1] < tri[:, 2]).all()
+        got = _sorted_rows(tri)
+        assert (np.diff(got) > 0).all()
+        assert np.array_equal(got, _sorted_rows(ref))
     finally:
         tc.tc_free(g)
 
