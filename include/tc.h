@@ -326,7 +326,9 @@ TC_API tc_status tc_graph_get_info(const tc_graph* g, tc_graph_info* info);
  */
 TC_API tc_status tc_copy_csr(const tc_graph* g, int64_t* offsets, int32_t* cols, int32_t* perm, void* stream);
 
-/* tc_free — release g and all its device memory (stream-ordered on the last stream g used).  NULL is a no-op. */
+/* tc_free — release g and all its device memory (stream-ordered on the last stream g used), then wait for that
+ * stream, so the memory is free again when tc_free returns and the next graph's buffers are served from completed
+ * frees (measured faster than returning with the frees still queued).  NULL is a no-op. */
 TC_API void tc_free(tc_graph* g);
 
 /*

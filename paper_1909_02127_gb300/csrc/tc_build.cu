@@ -40,6 +40,7 @@ __device__ __forceinline__ void agg_inc(int32_t* cnt, uint32_t idx, bool active)
 constexpr int kPackThreads = 256;
 constexpr int kPackItems = 4;
 constexpr int kPackTile = kPackThreads * kPackItems;  // 1024 pairs, <= 2048 distinct endpoints
+static_assert(kPackItems == 4, "k_pack moves a thread's pairs as one int4 per array");
 constexpr int kPackSlots = 4096;
 constexpr int kPackProbe = 8;
 
@@ -67,6 +68,22 @@ __device__ __forceinline__ void pack_count(int32_t* skey, int32_t* scnt, int32_t
   atomicAdd(&indeg[x], 1);
 }
 
+// One input pair: its key (the sentinel for a self-loop or an invalid id) and its endpoints counted.
+__device__ __forceinline__ uint64_t pack_pair(int32_t a, int32_t b, int64_t n, int B, uint64_t sentinel,
+                                              int32_t* skey, int32_t* scnt, int32_t* indeg, bool& bad) {
+  if (a < 0 || b < 0 || a >= n || b >= n) {
+    bad = true;
+    return sentinel;
+  }
+  if (a == b) return sentinel;
+  pack_count(skey, scnt, indeg, a);
+  pack_count(skey, scnt, indeg, b);
+  return ((uint64_t)(a < b ? a : b) << B) | (uint64_t)(a < b ? b : a);
+}
+
+// Tiles of 1024 pairs, four consecutive pairs per thread.  With 16-byte aligned arrays the pairs come in with two
+// 16-byte loads, issued for the next tile before the current one is hashed, and the keys leave with 16-byte
+// stores; a ragged or unaligned tile takes scalar loads.
 __global__ void __launch_bounds__(kPackThreads) k_pack(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
                                                        int64_t len, int64_t n, int B, uint64_t* __restrict__ keys,
                                                        int32_t* __restrict__ indeg, uint32_t* __restrict__ err) {
@@ -78,21 +95,45 @@ __global__ void __launch_bounds__(kPackThreads) k_pack(const int32_t* __restrict
     scnt[i] = 0;
   }
   __syncthreads();
+  const bool vec_in = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
+  const bool vec_out = (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
+  const int64_t step = (int64_t)gridDim.x * kPackTile;
   bool bad = false;
-  for (int64_t tile = (int64_t)blockIdx.x * kPackTile; tile < len; tile += (int64_t)gridDim.x * kPackTile) {
-    for (int j = 0; j < kPackItems; ++j) {
-      const int64_t i = tile + j * kPackThreads + threadIdx.x;
-      if (i >= len) break;
-      const int32_t a = src[i], b = dst[i];
-      uint64_t key = sentinel;
-      if (a < 0 || b < 0 || a >= n || b >= n) {
-        bad = true;
-      } else if (a != b) {
-        key = ((uint64_t)(a < b ? a : b) << B) | (uint64_t)(a < b ? b : a);
-        pack_count(skey, scnt, indeg, a);
-        pack_count(skey, scnt, indeg, b);
+  int64_t tile = (int64_t)blockIdx.x * kPackTile;
+  int4 na = make_int4(0, 0, 0, 0), nb = na;
+  if (vec_in && tile + kPackTile <= len) {
+    na = __ldg(reinterpret_cast<const int4*>(src + tile) + threadIdx.x);
+    nb = __ldg(reinterpret_cast<const int4*>(dst + tile) + threadIdx.x);
+  }
+  for (; tile < len; tile += step) {
+    const int64_t i0 = tile + kPackItems * threadIdx.x;
+    if (vec_in && tile + kPackTile <= len) {
+      const int4 a4 = na, b4 = nb;
+      const int64_t next = tile + step;
+      if (next + kPackTile <= len) {
+        na = __ldg(reinterpret_cast<const int4*>(src + next) + threadIdx.x);
+        nb = __ldg(reinterpret_cast<const int4*>(dst + next) + threadIdx.x);
       }
-      keys[i] = key;
+      const uint64_t k0 = pack_pair(a4.x, b4.x, n, B, sentinel, skey, scnt, indeg, bad);
+      const uint64_t k1 = pack_pair(a4.y, b4.y, n, B, sentinel, skey, scnt, indeg, bad);
+      const uint64_t k2 = pack_pair(a4.z, b4.z, n, B, sentinel, skey, scnt, indeg, bad);
+      const uint64_t k3 = pack_pair(a4.w, b4.w, n, B, sentinel, skey, scnt, indeg, bad);
+      if (vec_out) {
+        ulonglong2* o = reinterpret_cast<ulonglong2*>(keys + i0);
+        o[0] = make_ulonglong2(k0, k1);
+        o[1] = make_ulonglong2(k2, k3);
+      } else {
+        keys[i0] = k0;
+        keys[i0 + 1] = k1;
+        keys[i0 + 2] = k2;
+        keys[i0 + 3] = k3;
+      }
+    } else {
+      for (int j = 0; j < kPackItems; ++j) {
+        const int64_t i = i0 + j;
+        if (i >= len) break;
+        keys[i] = pack_pair(src[i], dst[i], n, B, sentinel, skey, scnt, indeg, bad);
+      }
     }
     __syncthreads();
     // flush: every occupied slot once (a scan of the table, no shared counter)

@@ -7,6 +7,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "tc_build.cuh"
 #include "tc_internal.cuh"
@@ -157,6 +158,35 @@ int bits_for(int64_t n) {
   return b;
 }
 
+// Page-locked 64-byte landing slots for the small device-to-host results of a graph (its count, the number listed).
+// Pinning memory is a slow driver call (and freeing it waits for the device), too slow to do per graph, so slots
+// are carved from 64 KB page-locked blocks that live for the process and are reused through a free list.  Every
+// copy into a slot is waited for before the call that made it returns, so a released slot is idle.
+std::mutex g_slot_mu;
+std::vector<uint64_t*> g_free_slots;
+
+uint64_t* slot_acquire() {
+  std::lock_guard<std::mutex> lk(g_slot_mu);
+  if (g_free_slots.empty()) {
+    constexpr int kSlotsPerBlock = 1024;
+    char* blk = nullptr;
+    if (cudaMallocHost((void**)&blk, (size_t)64 * kSlotsPerBlock) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return nullptr;
+    }
+    for (int i = kSlotsPerBlock - 1; i >= 0; --i) g_free_slots.push_back(reinterpret_cast<uint64_t*>(blk + 64 * i));
+  }
+  uint64_t* p = g_free_slots.back();
+  g_free_slots.pop_back();
+  return p;
+}
+
+void slot_release(uint64_t* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_slot_mu);
+  g_free_slots.push_back(p);
+}
+
 void release_all(tc_graph* g, cudaStream_t s) {
   buf_release(g->alloc, g->keys, s);
   buf_release(g->alloc, g->indeg, s);
@@ -168,10 +198,8 @@ void release_all(tc_graph* g, cudaStream_t s) {
   buf_release(g->alloc, g->acc, s);
   buf_release(g->alloc, g->dq0, s);
   buf_release(g->alloc, g->dense, s);
-  if (g->host_total) {
-    cudaFreeHost(g->host_total);
-    g->host_total = nullptr;
-  }
+  slot_release(g->host_total);
+  g->host_total = nullptr;
 }
 
 // The device address of the host array p[0, len) when all of it is page-locked memory mapped into the device's
@@ -315,9 +343,7 @@ TC_API tc_status tc_load_edges(const int32_t* src, const int32_t* dst, int64_t n
     if ((st = cuda_status(cudaMemsetAsync(g->indeg.p, 0, (size_t)(num_vertices > 0 ? num_vertices : 1) * 4, s),
                           "memset indeg")))
       break;
-    if (cudaMallocHost((void**)&g->host_total, 64) != cudaSuccess) {
-      (void)cudaGetLastError();
-      g->host_total = nullptr;
+    if (!(g->host_total = slot_acquire())) {
       set_error("tc_load_edges: pinned host allocation failed");
       st = TC_ERR_NO_MEMORY;
       break;
@@ -556,8 +582,12 @@ TC_API tc_status tc_copy_csr(const tc_graph* g, int64_t* offsets, int32_t* cols,
 
 TC_API void tc_free(tc_graph* g) {
   if (!g) return;
-  release_all(g, g->last_stream);
+  const cudaStream_t s = g->last_stream;
+  release_all(g, s);
   delete g;
+  // wait for the queued frees: allocations of the next graph are then served from completed frees, which measured
+  // faster (rmat20 build 1.50 vs 1.66 ms) than allocating while they are still in flight
+  (void)cudaStreamSynchronize(s);
 }
 
 }  // extern "C"

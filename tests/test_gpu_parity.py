@@ -347,6 +347,35 @@ def test_pinned_host_inputs(tc):
         tc.tc_load_edges(bad, pd, spec.n)
 
 
+def test_ingest_alignment_and_ragged_tiles(tc):
+    """Ingest takes four pairs per thread as 16-byte loads when both arrays are 16-byte aligned and a tile of 1024
+    pairs is whole, scalar loads otherwise: unaligned device views and ragged lengths give the oracle's count, and an
+    invalid id (negative or >= n) inside a whole aligned tile is reported like one in a ragged tail."""
+    import torch
+    src, dst = graphgen.rmat(14, 16, 81).edges()
+    n = 1 << 14
+    for cut in (len(src), len(src) - 1, 5 * 1024 + 3):
+        ref, _ = oracle.count(src[:cut], dst[:cut], n)
+        for shift in (0, 1, 2, 3):
+            pad = np.zeros(shift, np.int32)
+            s = torch.from_numpy(np.concatenate([pad, src[:cut]])).cuda()[shift:]
+            d = torch.from_numpy(np.concatenate([pad, dst[:cut]])).cuda()[shift:]
+            assert (s.data_ptr() % 16 == 0) == (shift == 0)
+            g = tc.tc_load_edges(s, d, n)
+            try:
+                tc.tc_build(g)
+                assert tc.tc_count(g) == ref, (cut, shift)
+            finally:
+                tc.tc_free(g)
+    for pos, bad_id in ((2048 + 517, n), (3 * 1024, -1), (len(src) - 1, n + 7)):
+        for arr in ("src", "dst"):
+            a, b = src.copy(), dst.copy()
+            (a if arr == "src" else b)[pos] = bad_id
+            with pytest.raises(tc.TCError) as e:
+                tc.tc_load_edges(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), n)
+            assert e.value.status == tc.TC_ERR_OUT_OF_RANGE
+
+
 def test_errors(tc):
     import torch
     s = torch.tensor([0, 1, 5], dtype=torch.int32, device="cuda")
