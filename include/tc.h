@@ -328,7 +328,8 @@ TC_API tc_status tc_copy_csr(const tc_graph* g, int64_t* offsets, int32_t* cols,
 
 /* tc_free — release g and all its device memory (stream-ordered on the last stream g used), then wait for that
  * stream, so the memory is free again when tc_free returns and the next graph's buffers are served from completed
- * frees (measured faster than returning with the frees still queued).  NULL is a no-op. */
+ * frees (measured faster than returning with the frees still queued).  That stream must still exist (not yet
+ * destroyed by the caller).  NULL is a no-op. */
 TC_API void tc_free(tc_graph* g);
 
 /*
