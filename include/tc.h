@@ -73,7 +73,8 @@ typedef struct tc_graph_info {
   int64_t bin_warp;        /* sources handled one warp each */
   int64_t bin_block;       /* sources handled one thread block each */
   int32_t built;           /* 1 after tc_build */
-  int32_t reserved;
+  int32_t count_ctas;      /* CTAs of the fused counting kernel's launch for this graph on the current device (a
+                              persistent grid: at most 2 per SM); 0 before tc_build */
   int64_t dense_rows;      /* rows N+(v) also stored as bitmaps over (v, n) (no more words than entries) */
   int64_t dense_wedges;    /* the part of num_wedges through dense rows (tested 128 ids per 16-byte word load) */
   int64_t dense_quads;     /* 16-byte bitmap words that tc_count reads for them: sum of d-(v) * quads(v) */
@@ -175,8 +176,11 @@ TC_API tc_status tc_count_per_vertex(tc_graph* g, uint64_t* per_vertex, uint64_t
  * (8 MiB) that every GPU which loads the library holds until the process exits.
  *   d_per_vertex  n uint64 entries of DEVICE memory, overwritten with t(x).
  *   d_total       one uint64 of DEVICE memory, overwritten with T.
- * Graphs with more than 2^20 vertices are rejected with TC_ERR_INVALID_ARG (use tc_count_per_vertex).  The first
- * call on a device looks up the array's device address (cudaGetSymbolAddress) with that device current.  All calls
+ * Graphs with more than 2^20 vertices are rejected with TC_ERR_INVALID_ARG (use tc_count_per_vertex).  The device
+ * current at the call must be the one that was current at tc_load_edges (the graph's buffers live there, and the
+ * scratch array used is the current device's); otherwise the call returns TC_ERR_INVALID_ARG and launches nothing.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls
  * on a device share the one array, and each call clears the part it uses before counting: calls whose GPU work
  * overlaps (different streams, no ordering between them) race on it and give wrong results.  Asynchronous: the
  * outputs are valid in stream order.

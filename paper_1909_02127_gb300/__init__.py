@@ -40,7 +40,7 @@ class tc_graph_info(ctypes.Structure):
     _fields_ = [("num_vertices", ctypes.c_int64), ("num_input_pairs", ctypes.c_int64), ("num_edges", ctypes.c_int64),
                 ("csr_entries", ctypes.c_int64), ("max_out_degree", ctypes.c_int64), ("num_wedges", ctypes.c_int64),
                 ("active_sources", ctypes.c_int64), ("bin_warp", ctypes.c_int64), ("bin_block", ctypes.c_int64),
-                ("built", ctypes.c_int32), ("reserved", ctypes.c_int32), ("dense_rows", ctypes.c_int64),
+                ("built", ctypes.c_int32), ("count_ctas", ctypes.c_int32), ("dense_rows", ctypes.c_int64),
                 ("dense_wedges", ctypes.c_int64), ("dense_quads", ctypes.c_int64), ("bin_thread", ctypes.c_int64)]
 
 
@@ -397,12 +397,29 @@ def tc_count_per_vertex(g: int, out=None, stream=None):
     return int(total.value), out
 
 
+def _device_words(t, need: int, what: str) -> int:
+    """Address of a CUDA tensor that holds at least `need` contiguous 64-bit entries (ValueError otherwise)."""
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{what} must be a CUDA tensor (or a raw device address as an int)")
+    if t.element_size() != 8 or not t.is_contiguous():
+        raise ValueError(f"{what} must be a contiguous tensor of 64-bit entries")
+    if t.numel() < need:
+        raise ValueError(f"{what} holds {t.numel()} entries; {need} are needed")
+    return t.data_ptr()
+
+
 def tc_count_per_vertex_noalloc(g: int, d_per_vertex, d_total, stream=None) -> None:
     """Per-vertex counts into caller-provided DEVICE memory, allocating nothing (scratch is a static device array
-    of 2^20 entries; larger graphs are rejected).  d_per_vertex: n 64-bit entries; d_total: one 64-bit entry.
+    of 2^20 entries; larger graphs are rejected).  d_per_vertex: a CUDA tensor of at least n 64-bit entries;
+    d_total: a CUDA tensor of at least one 64-bit entry.  Both are checked here (ValueError before any launch);
+    raw device addresses given as ints are passed through unchecked, and then the caller vouches for their size.
     Asynchronous on `stream`."""
-    pv = d_per_vertex if isinstance(d_per_vertex, int) else d_per_vertex.data_ptr()
-    tot = d_total if isinstance(d_total, int) else d_total.data_ptr()
+    if isinstance(d_per_vertex, int) and isinstance(d_total, int):
+        pv, tot = d_per_vertex, d_total
+    else:
+        n = tc_graph_get_info(g)["num_vertices"]
+        pv = d_per_vertex if isinstance(d_per_vertex, int) else _device_words(d_per_vertex, n, "d_per_vertex")
+        tot = d_total if isinstance(d_total, int) else _device_words(d_total, 1, "d_total")
     _check(load_library().tc_count_per_vertex_noalloc(g, pv, tot, _stream_ptr(stream)))
 
 

@@ -204,7 +204,7 @@ tc_status batch_launch(unsigned char* base, const BatchLayout& L, int32_t num_gr
     t.pt = reinterpret_cast<const int64_t*>(base + L.views_bytes + 2 * L.pre_bytes);
     t.num_graphs = num_graphs;
     const int64_t want = L.nb_total + (L.nw_total + L.nt_total + kWarpsPerCTA - 1) / kWarpsPerCTA;
-    const int grid = (int)(want < 2 * kNumSMs ? want : 2 * kNumSMs);
+    const int grid = (int)(want < 2 * num_sms() ? want : 2 * num_sms());
     k_count_batch<<<grid, kCountThreads, dev::kCountSmem, s>>>(t, counts, cursors);
     TC_CUDA(cudaGetLastError());
   }

@@ -819,7 +819,7 @@ tc_status pack_edges(tc_graph* g, const int32_t* src, const int32_t* dst, int64_
                      uint32_t* d_err, cudaStream_t s) {
   if (len <= 0) return TC_OK;
   const int64_t tiles = (len + kPackTile - 1) / kPackTile;
-  const int grid = (int)(tiles < 4 * kNumSMs ? tiles : 4 * kNumSMs);
+  const int grid = (int)(tiles < 4 * num_sms() ? tiles : 4 * num_sms());
   k_pack<<<grid, kPackThreads, 0, s>>>(src, dst, len, g->n, g->key_bits, g->keys.as<uint64_t>() + offset,
                                        g->indeg.as<int32_t>(), d_err);
   note_launch();
@@ -962,14 +962,14 @@ tc_status bucket_csr(tc_graph* g, const int32_t* rank, const int32_t* rcount, Bu
       k_rows_small<<<grid_for(n, 256), 256, 0, s>>>(pstart.as<int64_t>(), cur.as<int64_t>(), n, tgt.as<int32_t>(),
                                                     dplus.as<int32_t>(), rlist, rc);
       if ((st = launched("k_rows_small"))) break;
-      k_rows_warp<<<4 * kNumSMs, kRowThreads, 0, s>>>(pstart.as<int64_t>(), cur.as<int64_t>(), n,
+      k_rows_warp<<<4 * num_sms(), kRowThreads, 0, s>>>(pstart.as<int64_t>(), cur.as<int64_t>(), n,
                                                       tgt.as<int32_t>(), dplus.as<int32_t>(), rlist, rc);
       if ((st = launched("k_rows_warp"))) break;
       const size_t blk_smem = (size_t)kBigBits / 8;
       if ((st = cuda_status(cudaFuncSetAttribute(k_rows_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)blk_smem), "k_rows_block attribute")))
         break;
-      k_rows_block<<<kNumSMs, kBigThreads, blk_smem, s>>>(pstart.as<int64_t>(), cur.as<int64_t>(), n, mid_max,
+      k_rows_block<<<num_sms(), kBigThreads, blk_smem, s>>>(pstart.as<int64_t>(), cur.as<int64_t>(), n, mid_max,
                                                           tgt.as<int32_t>(), dplus.as<int32_t>(), rlist, rc);
       if ((st = launched("k_rows_block"))) break;
     }

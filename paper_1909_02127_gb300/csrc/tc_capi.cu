@@ -23,6 +23,29 @@ std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 namespace {
+std::atomic<int> g_sms[64] = {};
+}  // namespace
+
+int num_sms() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    (void)cudaGetLastError();
+    dev = -1;
+  }
+  if (dev >= 0) {
+    const int cached = g_sms[dev].load(std::memory_order_relaxed);
+    if (cached > 0) return cached;
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) {
+      g_sms[dev].store(v, std::memory_order_relaxed);
+      return v;
+    }
+    (void)cudaGetLastError();
+  }
+  return 1;  // no device: callers only size grids with it, and a launch would fail on its own
+}
+
+namespace {
 std::mutex g_tuning_mutex;
 // Built-in default, measured on GB300: graphs up to ~2^25 edges run fastest with every source in the warp bin;
 // larger ones with heavy sources (w(u) > 2^15) spread over a whole block; the build groups pairs in per-source
@@ -330,6 +353,10 @@ TC_API tc_status tc_load_edges(const int32_t* src, const int32_t* dst, int64_t n
     g->alloc.user = *alloc;
     g->alloc.has_user = true;
   }
+  if (cudaGetDevice(&g->device) != cudaSuccess) {
+    (void)cudaGetLastError();
+    g->device = -1;
+  }
   g->n = num_vertices;
   g->num_pairs = num_edges;
   g->key_bits = bits_for(num_vertices);
@@ -550,6 +577,7 @@ TC_API tc_status tc_graph_get_info(const tc_graph* g, tc_graph_info* info) {
   info->num_input_pairs = g->num_pairs;
   info->built = g->built ? 1 : 0;
   if (g->built) {
+    info->count_ctas = count_grid(g);
     info->num_edges = g->m;
     info->csr_entries = g->csr_entries;
     info->max_out_degree = g->max_out_degree;

@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(kCountThreads, 2)
 
 int count_grid(const tc_graph* g) {
   const int64_t want = g->nb + (g->nw + kWarpsPerCTA - 1) / kWarpsPerCTA + (g->nt + kCountThreads - 1) / kCountThreads;
-  return (int)(want < 2 * kNumSMs ? (want < 1 ? 1 : want) : 2 * kNumSMs);
+  return (int)(want < 2 * num_sms() ? (want < 1 ? 1 : want) : 2 * num_sms());
 }
 
 tc_status launch_count(const tc_graph* g, uint64_t* d_total, uint64_t* d_per_vertex, uint32_t* d_cursors,
@@ -231,7 +231,7 @@ tc_status launch_list(const tc_graph* g, int64_t first, int64_t count, int32_t* 
       break;
     // the CTAs' sources for pass 2 (their number in d_cursors[3])
     if ((st = cuda_status(cudaMemsetAsync(d_cursors + 3, 0, sizeof(uint32_t), s), "memset heavy"))) break;
-    k_list_heavy<<<2 * kNumSMs, 256, 0, s>>>(g->view(), first, count, cnt.as<uint32_t>(), heavy.as<int32_t>(),
+    k_list_heavy<<<2 * num_sms(), 256, 0, s>>>(g->view(), first, count, cnt.as<uint32_t>(), heavy.as<int32_t>(),
                                             d_cursors + 3);
     note_launch();
     if ((st = cuda_status(cudaGetLastError(), "k_list_heavy"))) break;

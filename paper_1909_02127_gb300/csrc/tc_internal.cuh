@@ -10,7 +10,9 @@
 
 namespace tc {
 
-constexpr int kNumSMs = 152;
+// Streaming multiprocessors of the current device (queried once per device, cached).  Persistent grids are sized
+// in multiples of it.
+int num_sms();
 
 // ------------------------------------------------------------------------------------------------------------
 // Errors
@@ -111,7 +113,8 @@ tc_status exclusive_scan_i32_to_i64(const Allocator& a, const int32_t* in, int64
 // Exclusive scan of n uint32 values in place; *total (device, may be null) receives the sum.
 tc_status exclusive_scan_u32(const Allocator& a, uint32_t* data, int64_t n, cudaStream_t s);
 
-int grid_for(int64_t items, int threads, int max_blocks = kNumSMs * 16);
+// max_blocks < 0: 16 CTAs per SM of the current device.
+int grid_for(int64_t items, int threads, int max_blocks = -1);
 
 }  // namespace tc
 
@@ -120,6 +123,7 @@ int grid_for(int64_t items, int threads, int max_blocks = kNumSMs * 16);
 // ------------------------------------------------------------------------------------------------------------
 struct tc_graph {
   tc::Allocator alloc;
+  int device = -1;           // the device current at tc_load_edges: every buffer of the graph lives there
   cudaStream_t last_stream = nullptr;
   int64_t n = 0;
   int64_t num_pairs = 0;

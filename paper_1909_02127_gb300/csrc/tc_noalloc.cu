@@ -63,6 +63,13 @@ extern "C" TC_API tc_status tc_count_per_vertex_noalloc(tc_graph* g, uint64_t* d
               "scratch; use tc_count_per_vertex");
     return TC_ERR_INVALID_ARG;
   }
+  int dev = -1;
+  TC_CUDA(cudaGetDevice(&dev));
+  if (dev != g->device) {
+    set_error("tc_count_per_vertex_noalloc: the graph was loaded on device " + std::to_string(g->device) +
+              " but device " + std::to_string(dev) + " is current; make the graph's device current first");
+    return TC_ERR_INVALID_ARG;
+  }
   void* scratch = nullptr;
   TC_TRY(scratch_for_current_device(&scratch));
   cudaStream_t s = (cudaStream_t)stream;

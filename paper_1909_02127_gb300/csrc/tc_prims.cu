@@ -11,6 +11,7 @@
 namespace tc {
 
 int grid_for(int64_t items, int threads, int max_blocks) {
+  if (max_blocks < 0) max_blocks = num_sms() * 16;
   int64_t b = (items + threads - 1) / threads;
   if (b > max_blocks) b = max_blocks;
   return b < 1 ? 1 : (int)b;

@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(kUfThreads) k_uf_compact2(const int64_t* __res
 
 int tiles_grid(int64_t slots) {
   const int64_t t = (slots + kUfTile - 1) / kUfTile;
-  const int64_t cap = (int64_t)kNumSMs * 8;
+  const int64_t cap = (int64_t)num_sms() * 8;
   return (int)(t < 1 ? 1 : (t > cap ? cap : t));
 }
 

@@ -122,3 +122,56 @@ def test_tuning_table_round_trip_without_gpu(lib):
         tc.tc_set_tuning([(1 << 40, 1 << 15)], isect_max_wedges_milli=ratio)
     finally:
         tc.tc_set_tuning(saved)
+
+
+class _FakeDeviceTensor:
+    """Stands in for a CUDA tensor in the binding's argument checks (no GPU here)."""
+
+    def __init__(self, numel, element_size=8, contiguous=True, is_cuda=True):
+        self._numel, self._es, self._contig, self.is_cuda = numel, element_size, contiguous, is_cuda
+
+    def numel(self):
+        return self._numel
+
+    def element_size(self):
+        return self._es
+
+    def is_contiguous(self):
+        return self._contig
+
+    def data_ptr(self):
+        return 0x1000
+
+
+def test_noalloc_binding_rejects_bad_outputs_before_any_launch(monkeypatch):
+    """tc_count_per_vertex_noalloc checks its output tensors in Python (CUDA, 8-byte, contiguous, at least n and
+    1 entries) and raises ValueError without calling into the library; raw ints pass through."""
+    import torch
+
+    import paper_1909_02127_gb300 as tc
+    calls = []
+
+    class FakeLib:
+        def tc_count_per_vertex_noalloc(self, *args):
+            calls.append(args)
+            return tc.TC_OK
+
+    monkeypatch.setattr(tc, "load_library", lambda *a, **k: FakeLib())
+    monkeypatch.setattr(tc, "tc_graph_get_info", lambda g: {"num_vertices": 10})
+    monkeypatch.setattr(tc, "_stream_ptr", lambda s: 0)
+    ok_pv, ok_tot = _FakeDeviceTensor(10), _FakeDeviceTensor(1)
+    bad = [
+        (torch.zeros(10, dtype=torch.int64), ok_tot),          # host tensor
+        (_FakeDeviceTensor(9), ok_tot),                        # shorter than n
+        (_FakeDeviceTensor(10, element_size=4), ok_tot),       # 32-bit entries
+        (_FakeDeviceTensor(10, contiguous=False), ok_tot),     # strided
+        (ok_pv, _FakeDeviceTensor(0)),                         # no room for T
+        (ok_pv, torch.zeros(1, dtype=torch.int64)),            # host total
+    ]
+    for pv, tot in bad:
+        with pytest.raises(ValueError):
+            tc.tc_count_per_vertex_noalloc(1, pv, tot)
+    assert calls == []
+    tc.tc_count_per_vertex_noalloc(1, ok_pv, ok_tot)
+    tc.tc_count_per_vertex_noalloc(1, 0x2000, 0x3000)  # raw device addresses: the caller vouches for them
+    assert len(calls) == 2
