@@ -16,6 +16,7 @@ scaling, no collective on the data path; the barrier and the max over ranks are 
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -218,8 +219,7 @@ def run_single(args, dist: Dist):
     dev = torch.device("cuda", dist.local)
     torch.cuda.set_device(dev)
     base = graphgen.config(args.workload)
-    spec = graphgen.GraphSpec(base.kind, base.n, base.num_edges, base.seed + dist.rank, base.scale, base.permute,
-                              base.name)
+    spec = dataclasses.replace(base, seed=base.seed + dist.rank)
     stream = torch.cuda.current_stream()
     ds, dd = spec.edges(device=dev)
     torch.cuda.synchronize()
@@ -398,8 +398,7 @@ def run_unfused(args, dist: Dist):
     dev = torch.device("cuda", dist.local)
     torch.cuda.set_device(dev)
     base = graphgen.config(args.graph)
-    spec = graphgen.GraphSpec(base.kind, base.n, base.num_edges, base.seed + dist.rank, base.scale, base.permute,
-                              base.name)
+    spec = dataclasses.replace(base, seed=base.seed + dist.rank)
     stream = torch.cuda.current_stream()
     ds, dd = spec.edges(device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
@@ -480,8 +479,7 @@ def run_list(args, dist: Dist):
     dev = torch.device("cuda", dist.local)
     torch.cuda.set_device(dev)
     base = graphgen.config(args.graph)
-    spec = graphgen.GraphSpec(base.kind, base.n, base.num_edges, base.seed + dist.rank, base.scale, base.permute,
-                              base.name)
+    spec = dataclasses.replace(base, seed=base.seed + dist.rank)
     stream = torch.cuda.current_stream()
     ds, dd = spec.edges(device=dev)
     g = tc.tc_load_edges(ds, dd, spec.n, stream=stream)
@@ -730,15 +728,16 @@ def run_serve(args, dist: Dist):
     dev = torch.device("cuda", dist.local)
     torch.cuda.set_device(dev)
     pool = graphgen.serve_pool(args.serve_pool, graphgen.BASE_SEED + graphgen.SERVE_SEED_OFFSET + dist.rank * 7919)
-    sizes = np.array([sp.num_edges for sp in pool], dtype=np.int64)
+    gen = [sp.edges(device=dev) for sp in pool]
+    sizes = np.array([int(s.numel()) for s, _ in gen], dtype=np.int64)
     offs = np.concatenate([[0], np.cumsum(sizes)])
     total = int(offs[-1])
     host = torch.empty(2 * total, dtype=torch.int32).pin_memory()
-    for i, sp in enumerate(pool):
-        s, d = sp.edges(device=dev)
+    for i, (s, d) in enumerate(gen):
         host[offs[i]:offs[i + 1]].copy_(s)
         host[total + offs[i]:total + offs[i + 1]].copy_(d)
     torch.cuda.synchronize()
+    del gen
     base = host.data_ptr()
     src_ptr = [base + 4 * int(offs[i]) for i in range(len(pool))]
     dst_ptr = [base + 4 * (total + int(offs[i])) for i in range(len(pool))]

@@ -22,6 +22,14 @@
  *    counter, up to GG_RMAT_MAX_ATTEMPTS attempts, after which both endpoints are reduced modulo n.
  *  - Vertex relabelling: a 4-round balanced Feistel network on 2h bits (Luby & Rackoff 1988) with cycle-walking
  *    (Black & Rogaway, "Ciphers with Arbitrary Finite Domains", CT-RSA 2002) gives a seeded bijection on [0,n).
+ *  - Erdos-Renyi G(n, p) (every pair {i, j} present independently with probability p; no self-loops, no repeats)
+ *    by geometric skipping (Batagelj & Brandes, "Efficient generation of large random networks", Phys. Rev. E 71,
+ *    2005): row i walks the candidates j = i+1 .. n-1 and jumps over a Geometric(p) number of absent pairs before
+ *    each present one.  Rows are independent (row i's draws use counters (i << 32) | t), so rows run in parallel.
+ *    The gap is drawn by inversion, floor(log2(U) / log2(1-p)) with U uniform on (0, 1], both logarithms in
+ *    Q.40 fixed point from the bit-by-bit squaring method for the binary logarithm, so the host and the device
+ *    take the same integer steps.  -log2(1-p) is an input (lq), computed once by the caller with the same method.
+ *    The gap law is exact up to the 2^-40 truncation of the logarithms.
  */
 #ifndef GRAPHGEN_GG_H
 #define GRAPHGEN_GG_H
@@ -55,8 +63,82 @@ GG_HD uint64_t gg_draw(uint64_t key, uint64_t ctr) { return gg_mix64(key + (ctr 
 /* Uniform integer in [0, n) from 32 random bits (multiply-shift). */
 GG_HD uint32_t gg_below(uint32_t r32, uint32_t n) { return (uint32_t)(((uint64_t)r32 * (uint64_t)n) >> 32); }
 
-/* Stream ids used by the generators. */
-enum { GG_STREAM_ER = 1, GG_STREAM_RMAT = 2, GG_STREAM_PERM = 3 };
+/* Stream ids used by the generators (4 and 5 are drawn by the Python workload definitions). */
+enum { GG_STREAM_ER = 1, GG_STREAM_RMAT = 2, GG_STREAM_PERM = 3, GG_STREAM_GNP = 6 };
+
+/* 64 x 64 -> 128-bit unsigned product. */
+GG_HD void gg_mul64(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo) {
+#if defined(__CUDA_ARCH__)
+  *hi = __umul64hi(a, b);
+  *lo = a * b;
+#else
+  const unsigned __int128 p = (unsigned __int128)a * b;
+  *hi = (uint64_t)(p >> 64);
+  *lo = (uint64_t)p;
+#endif
+}
+
+/* Number of leading zero bits of x != 0. */
+GG_HD int gg_clz64(uint64_t x) {
+#if defined(__CUDA_ARCH__)
+  return __clzll((long long)x);
+#else
+  return __builtin_clzll(x);
+#endif
+}
+
+#define GG_LOG_FRAC_BITS 40
+
+/* log2(x) for x >= 1 in Q.40 fixed point (truncated).  The integer part is the position of the top bit; the
+ * fraction comes one bit at a time from the mantissa m in [1, 2): square it, and a square of 2 or more is a 1 bit
+ * and is halved, else a 0 bit. */
+GG_HD uint64_t gg_log2_q40(uint64_t x) {
+  const int e = 63 - gg_clz64(x);
+  uint64_t m = x << (63 - e); /* mantissa, Q1.63 */
+  uint64_t r = (uint64_t)e << GG_LOG_FRAC_BITS;
+  for (int b = GG_LOG_FRAC_BITS - 1; b >= 0; --b) {
+    uint64_t hi, lo;
+    gg_mul64(m, m, &hi, &lo); /* m^2 in Q2.126 */
+    if (hi >> 63) {           /* m^2 >= 2: bit set, keep m^2 / 2 */
+      r |= (uint64_t)1 << b;
+      m = hi;
+    } else {
+      m = (hi << 1) | (lo >> 63);
+    }
+  }
+  return r;
+}
+
+/* A Geometric(p) variate (absent pairs before the next present one) from the 64-bit draw r, with
+ * lq = -log2(1 - p) in Q.40 (lq > 0).  U = ((r >> 1) + 1) / 2^63 lies in (0, 1]; the variate is
+ * floor(-log2(U) / lq), and P(variate >= k) = P(U <= (1-p)^k) = (1-p)^k. */
+GG_HD uint64_t gg_geometric(uint64_t r, uint64_t lq) {
+  const uint64_t x = (r >> 1) + 1;
+  const uint64_t neg_log2_u = ((uint64_t)63 << GG_LOG_FRAC_BITS) - gg_log2_q40(x);
+  return neg_log2_u / lq;
+}
+
+/* Row i of G(n, p): the present pairs {i, j}, j = i+1 .. n-1, in ascending j.  Writes them to src/dst when src is
+ * not null and returns how many there are.  lq = 0 stands for p = 0 (no pairs). */
+GG_HD int64_t gg_gnp_row(uint64_t seed, uint32_t n, uint64_t lq, uint32_t i, int32_t* src, int32_t* dst) {
+  if (lq == 0 || (uint64_t)i + 1 >= (uint64_t)n) return 0;
+  const uint64_t key = gg_key(seed, GG_STREAM_GNP);
+  const uint64_t len = (uint64_t)n - 1 - i; /* candidates */
+  uint64_t k = 0;                           /* first candidate not yet decided */
+  int64_t c = 0;
+  for (uint64_t t = 0; k < len; ++t) {
+    const uint64_t gap = gg_geometric(gg_draw(key, ((uint64_t)i << 32) | t), lq);
+    if (gap >= len - k) break;
+    k += gap;
+    if (src) {
+      src[c] = (int32_t)i;
+      dst[c] = (int32_t)(i + 1 + k);
+    }
+    ++c;
+    ++k;
+  }
+  return c;
+}
 
 /* Edge e of the uniform edge sampler on n vertices. */
 GG_HD void gg_er_edge(uint64_t seed, uint32_t n, uint64_t e, int32_t* s, int32_t* d) {

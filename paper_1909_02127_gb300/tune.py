@@ -56,7 +56,7 @@ def main():
     tc.load_library()
     scales = [14, 17, 20, 22] if args.quick else [12, 14, 16, 18, 20, 21, 22, 23, 24]
     specs = [graphgen.rmat(sc, 16, graphgen.BASE_SEED + 500 + sc, name=f"rmat{sc}") for sc in scales]
-    specs += [graphgen.er(1 << 20, 16 << 20, graphgen.BASE_SEED + 600, name="er n=2^20")]
+    specs += [graphgen.gnp(1 << 20, 16.0 / ((1 << 20) - 1), graphgen.BASE_SEED + 600, name="G(n=2^20, p=16/(n-1))")]
     reps = 3 if args.quick else 5
     d_total = torch.zeros(1, dtype=torch.int64, device="cuda")
     results = []
@@ -127,8 +127,8 @@ def main():
     batch_warp = int(min(batch_times, key=batch_times.get))
     print("batch", {k: round(v, 3) for k, v in batch_times.items()}, flush=True)
     # the per-graph choice of kernel: time both on every graph, then pick the threshold on W/m
-    method_specs = [graphgen.er(1 << lg, (deg << lg) // 2, graphgen.BASE_SEED + 700 + 10 * lg + deg,
-                                name=f"er n=2^{lg} deg {deg}")
+    method_specs = [graphgen.gnp(1 << lg, deg / ((1 << lg) - 1), graphgen.BASE_SEED + 700 + 10 * lg + deg,
+                                 name=f"G(n=2^{lg}, p={deg}/(n-1))")
                     for lg in ((16, 20, 22) if args.quick else (16, 18, 20, 22)) for deg in (4, 8, 16)]
     method_specs += [graphgen.rmat(sc, 16, graphgen.BASE_SEED + 500 + sc, name=f"rmat{sc}")
                      for sc in ((14, 18) if args.quick else (12, 16, 20))]

@@ -70,7 +70,7 @@ def test_batch_4096_all_graphs(tc):
     finally:
         for h in handles:
             tc.tc_free(h)
-    big = np.argsort([-sp.num_edges for sp in specs])[:64]
+    big = np.argsort([-sp.expected_edges for sp in specs])[:64]
     sample = sorted(set(range(0, 4096, 16)) | set(big.tolist()))
     for i in sample:
         sp = specs[i]
