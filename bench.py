@@ -51,6 +51,14 @@ def parse():
     p.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     p.add_argument("--serve-pool", type=int, default=1024, help="serve: distinct request graphs")
     p.add_argument("--build-workers", type=int, default=6, help="serve: concurrent CSR builders")
+    p.add_argument("--serve-rates", default="2000,5000,10000,20000,40000",
+                   help="serve: offered rates (req/s) of the capacity sweep, comma-separated ('' for none)")
+    p.add_argument("--sweep-duration", type=float, default=2.0, help="serve: seconds of arrivals per swept rate")
+    p.add_argument("--no-extras", action="store_true",
+                   help="rmat20: leave out the R-MAT 26, batch and serving sub-records")
+    p.add_argument("--rmat26-launches", type=int, default=5, help="R-MAT 26 sub-record: timed count launches")
+    p.add_argument("--extra-serve-duration", type=float, default=10.0,
+                   help="serving sub-record: seconds of arrivals at --rate")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--allocator", default="library", choices=["library", "torch"],
@@ -108,17 +116,99 @@ def aggregate(local_units: float, local_seconds: float, dist: Dist):
 # ------------------------------------------------------------------------------------------------------------
 # Clocks during the timed region
 # ------------------------------------------------------------------------------------------------------------
+class _Nvml:
+    """Read-only NVML queries through ctypes (SM clock, its maximum, clock-event reasons); None if unavailable."""
+    SM = 1  # NVML_CLOCK_SM
+    # clock-event reason bits (nvml.h): software power cap, hardware slowdown, software / hardware thermal
+    # slowdown, hardware power brake (reported as a hardware slowdown)
+    REASONS = ((0x4, "sw_power_cap"), (0x8, "hw_slowdown"), (0x20, "sw_thermal_slowdown"),
+               (0x40, "hw_thermal_slowdown"), (0x80, "hw_slowdown"))
+
+    def __init__(self, lib, handle):
+        import ctypes
+        self.lib, self.handle, self._u = lib, handle, ctypes.c_uint
+        self._reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons", None)
+
+    @classmethod
+    def open(cls, uuid: str = None, index: int = 0):
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return None
+            h = ctypes.c_void_p()
+            if uuid and lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h)) == 0:
+                return cls(lib, h)
+            if lib.nvmlDeviceGetHandleByIndex_v2(index, ctypes.byref(h)) == 0:
+                return cls(lib, h)
+        except (OSError, AttributeError):
+            pass
+        return None
+
+    def sample(self):
+        """(sm_mhz, sm_max_mhz, [reason names]) or None."""
+        import ctypes
+        cur, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.handle, self.SM, ctypes.byref(cur)) != 0:
+            return None
+        if self.lib.nvmlDeviceGetMaxClockInfo(self.handle, self.SM, ctypes.byref(mx)) != 0:
+            return None
+        names = []
+        if self._reasons is not None and self._reasons(self.handle, ctypes.byref(rs)) == 0:
+            names = sorted({name for bit, name in self.REASONS if rs.value & bit})
+        return float(cur.value), float(mx.value), names
+
+
+def summarize_clocks(samples, source):
+    """samples: [(sm_mhz, sm_max_mhz, reasons)] -> the bench line's clocks record."""
+    if not samples:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [f"{source}: no samples"], "samples": 0,
+                "source": source}
+    reasons = sorted({r for _, _, rs in samples for r in rs})
+    return {"sm_mhz": statistics.median(x[0] for x in samples), "sm_max_mhz": max(x[1] for x in samples),
+            "reasons": reasons, "samples": len(samples), "source": source}
+
+
 class ClockSampler:
+    """SM clocks and throttle reasons during a timed region: NVML read every 5 ms in a thread, else nvidia-smi
+    every 50 ms."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, period_s: float = 0.005):
         self.gpu = gpu_index
+        self.period = period_s
         self.proc = None
         self.path = None
+        self.nvml = None
+        self.thread = None
+        self.samples = []
+        try:
+            import torch
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(gpu_index).uuid)
+        except Exception:
+            uuid = None
+        self.nvml = _Nvml.open(uuid, gpu_index)
 
     def start(self):
+        import threading
+        self.samples = []
+        if self.nvml is not None:
+            self._stop = threading.Event()
+
+            def loop():
+                while True:
+                    x = self.nvml.sample()
+                    if x is not None:
+                        self.samples.append(x)
+                    if self._stop.wait(self.period):
+                        return
+
+            self.thread = threading.Thread(target=loop, daemon=True)
+            self.thread.start()
+            return
         import tempfile
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
@@ -130,6 +220,14 @@ class ClockSampler:
             self.proc = None
 
     def stop(self):
+        if self.thread is not None:
+            self._stop.set()
+            self.thread.join(timeout=5)
+            self.thread = None
+            x = self.nvml.sample()  # at least one sample, taken as the region ends
+            if x is not None:
+                self.samples.append(x)
+            return summarize_clocks(self.samples, "nvml 5 ms")
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -137,7 +235,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
+        samples = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
             for line in f:
@@ -145,16 +243,12 @@ class ClockSampler:
                 if len(parts) < 9:
                     continue
                 try:
-                    sm.append(float(parts[1]))
-                    smax.append(float(parts[2]))
+                    sm, smax = float(parts[1]), float(parts[2])
                 except ValueError:
                     continue
-                for name, val in zip(names, parts[5:9]):
-                    if val.lower().startswith("active"):
-                        reasons.add(name)
+                samples.append((sm, smax, [n for n, v in zip(names, parts[5:9]) if v.lower().startswith("active")]))
         os.unlink(self.path)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return summarize_clocks(samples, "nvidia-smi 50 ms")
 
 
 # ------------------------------------------------------------------------------------------------------------
@@ -201,9 +295,16 @@ def algorithmic_bytes(info: dict, grid_ctas: int) -> float:
     return 8.0 * (n + 1) + 4.0 * m + 16.0 * m + 4.0 * (W - Wd) + 16.0 * Qd + 8.0 * grid_ctas
 
 
+def algorithmic_bytes_ids(info: dict, grid_ctas: int) -> float:
+    """The same reads with every hop-2 row counted as an id list (4 bytes per candidate 2-path, 4W), as if no row
+    were read as a bitmap."""
+    n, m, W = info["num_vertices"], info["num_edges"], info["num_wedges"]
+    return 8.0 * (n + 1) + 4.0 * m + 16.0 * m + 4.0 * W + 8.0 * grid_ctas
+
+
 def count_grid(info: dict) -> int:
-    want = info["bin_block"] + (info["bin_warp"] + 15) // 16 + (info.get("bin_thread", 0) + 511) // 512
-    return int(max(1, min(want, 2 * 152)))
+    """CTAs of the counting kernel's launch, as the library reports it (tc_graph_info.count_ctas)."""
+    return int(max(1, info["count_ctas"]))
 
 
 # ------------------------------------------------------------------------------------------------------------
@@ -318,14 +419,26 @@ def run_single(args, dist: Dist):
     ratio = tc.tc_get_isect_max_wedges_milli()
     isect = ratio > 0 and m > 0 and 1000 * info["num_wedges"] <= ratio * m  # the kernel tc_count picks
     traffic = None if isect else profiled_traffic(args.workload)
-    roofline = {"bound": "hbm", "kernel": "k_count_isect" if isect else "k_count", "achieved": round(achieved, 1),
-                "peak": peak,
-                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": traffic, "algorithmic_bytes": b_alg}
+    csr_bytes = 8 * (info["num_vertices"] + 1) + 4 * info["csr_entries"]
+    l2_resident = csr_bytes <= L2_BYTES
+    roofline = {"bound": "l2" if l2_resident else "hbm", "kernel": "k_count_isect" if isect else "k_count",
+                "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "algorithmic_bytes": b_alg,
+                "dram_frac": round(traffic / mean_count_s / 1e9 / peak, 4) if traffic else None,
+                "csr_bytes": csr_bytes}
+    if l2_resident:
+        roofline["note"] = ("the CSR fits in the 129 MB L2, so the kernel reads it from L2 (DRAM traffic is "
+                            "dram_frac of the HBM peak): issue- and L2-latency-bound; frac = algorithmic bytes / "
+                            "time against the HBM copy peak")
 
     cpu = None
     if dist.rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(spec, ds, dd, T_ref)
+        if args.workload == "rmat20":
+            cpu["single_thread"] = cpu_single_thread()
+    extras = {}
+    if args.workload == "rmat20" and dist.world == 1 and not args.no_extras:
+        extras = run_extras(args, dist, dev, stream, flush)
 
     out = {
         "metric": "triangle-count GTEPS (R-MAT 20/26; ingest+build+count per step)",
@@ -344,7 +457,130 @@ def run_single(args, dist: Dist):
         "gpu_launches": int(launches),
         "clocks": clock_info,
         "wall_s_timed": round(wall, 4),
+        **extras,
     }
+    return out
+
+
+GOLDEN_RMAT26 = os.path.join(ROOT, "tests", "golden", "rmat26_oracle.json")
+
+
+def stored_oracle(path: str):
+    """A stored oracle result (written by a committed script that calls only the oracle), or None."""
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
+def sub_rmat26(args, dev, stream, flush) -> dict:
+    """R-MAT scale 26 (2^30 pairs, permuted ids): ingest + build timed once after a warm-up build, then the counting
+    pass timed over several launches with CUDA events on its stream (the 5 GB CSR is 40x the L2, so the L2 flush
+    between launches changes little).  The count is compared with the oracle's stored T."""
+    import torch
+
+    import graphgen
+    import paper_1909_02127_gb300 as tc
+
+    spec = graphgen.config("rmat26")
+    ds, dd = spec.edges(device=dev)
+    torch.cuda.synchronize()
+    build_ms = []
+    g = None
+    for _ in range(2):
+        if g is not None:
+            tc.tc_free(g)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g = tc.tc_load_edges(ds, dd, spec.n, stream=stream)
+        tc.tc_build(g, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        build_ms.append(e0.elapsed_time(e1))
+    del ds, dd
+    try:
+        info = tc.tc_graph_get_info(g)
+        d_total = torch.zeros(1, dtype=torch.int64, device=dev)
+        T = tc.tc_count(g, stream)
+        tc.tc_count_device(g, d_total, stream)  # second warm-up launch
+        count_ms = []
+        launches0 = tc.tc_kernel_launches()
+        for k in range(args.rmat26_launches):
+            flush.fill_(k)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tc.tc_count_device(g, d_total, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            count_ms.append(e0.elapsed_time(e1))
+            if int(d_total.item()) != T:
+                raise RuntimeError("R-MAT 26 count changed between launches")
+        launches = tc.tc_kernel_launches() - launches0
+    finally:
+        tc.tc_free(g)
+    torch.cuda.empty_cache()
+    peak, peak_kind = measured_peaks()
+    grid = count_grid(info)
+    t = statistics.mean(count_ms) / 1e3
+    b_kernel = algorithmic_bytes(info, grid)
+    b_ids = algorithmic_bytes_ids(info, grid)
+    m = info["num_edges"]
+    gold = stored_oracle(GOLDEN_RMAT26)
+    return {
+        "workload": spec.name, "n": spec.n, "generated_pairs": spec.num_edges, "m": m, "triangles": T,
+        "oracle_T": gold["T"] if gold else None, "matches_oracle": (gold["T"] == T and gold["m"] == m) if gold else None,
+        "wedges": info["num_wedges"], "dense_wedges": info["dense_wedges"],
+        "build_ms": round(build_ms[-1], 2), "count_ms": round(statistics.mean(count_ms), 3),
+        "count_ms_all": [round(x, 3) for x in count_ms], "count_gteps": round(m / t / 1e9, 4),
+        "step_gteps": round(m / (t + build_ms[-1] / 1e3) / 1e9, 4), "triangles_per_s": round(T / t, 1),
+        "roofline": {"bound": "hbm", "kernel": "k_count", "achieved": round(b_kernel / t / 1e9, 1), "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": round(b_kernel / t / 1e9 / peak, 4),
+                     "frac_of_nominal_8tbs": round(b_kernel / t / 8e12, 4), "algorithmic_bytes": b_kernel,
+                     "traffic": None,
+                     "traffic_note": "DRAM counters are taken only on small captures; the CSR (5 GB) is 40x the L2, "
+                                     "so DRAM bytes track the algorithmic bytes less L2 reuse of hub rows"},
+        "roofline_id_lists": {"achieved": round(b_ids / t / 1e9, 1), "frac": round(b_ids / t / 1e9 / peak, 4),
+                              "algorithmic_bytes": b_ids,
+                              "note": "every hop-2 row counted as 4 B per candidate 2-path (4W)"},
+        "gpu_launches": int(launches),
+    }
+
+
+def sub_serve(args, dist: Dist) -> dict:
+    """The serving workload on a shorter trace (--extra-serve-duration s at --rate) in both modes, then the
+    offered-rate sweep."""
+    pool = ServePool(args, dist)
+    arrivals, pick = pool.trace(args.rate, args.extra_serve_duration)
+    batched = serve_replay(args, pool, arrivals, pick, True, args.extra_serve_duration * 20 + 300)
+    single = serve_replay(args, pool, arrivals, pick, False, args.extra_serve_duration * 20 + 300)
+    out = {"workload": f"Poisson {args.rate:g} req/s for {args.extra_serve_duration:g} s (a shorter trace than the "
+                       f"60 s config) over {len(pool.specs)} G(n,p)/R-MAT graphs, sizes log-uniform [1e3, 4e6]",
+           "pool_pairs": pool.total_pairs, "batched": batched, "one_by_one": single}
+    if args.serve_rates:
+        out["capacity"] = serve_capacity(args, pool, [float(x) for x in args.serve_rates.split(",")],
+                                         args.sweep_duration)
+    del pool
+    return out
+
+
+def run_extras(args, dist: Dist, dev, stream, flush) -> dict:
+    """The sub-records of the default line: R-MAT 26, the 4096-graph batch, serving.  A failure is reported in its
+    record (and raised again when it is a count mismatch)."""
+    import torch
+    out = {}
+    for name, fn in (("rmat26", lambda: sub_rmat26(args, dev, stream, flush)),
+                     ("batch", lambda: batch_measure(args, dist, 10, 3)),
+                     ("serve", lambda: sub_serve(args, dist))):
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn()
+        except RuntimeError as e:
+            if "differ" in str(e) or "changed" in str(e):
+                raise
+            out[name] = {"error": str(e)[:300]}
+        out[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+        torch.cuda.empty_cache()
     return out
 
 
@@ -385,6 +621,27 @@ def cpu_baseline(spec, ds, dd, T_expect):
         raise RuntimeError(f"oracle {T} != GPU {T_expect}")
     return {"value": round(m / t / 1e9, 5), "unit": "GTEPS", "cores": cores, "kind": "oracle",
             "sample": f"{what} (sort+CSR+merge count), m = {m}, {t:.2f} s"}
+
+
+def cpu_single_thread() -> list:
+    """The oracle on one host thread: the ER-4096 graph whole, and R-MAT scale 17 of the R-MAT 20 recipe (edge
+    factor 16, noise; one sixteenth of R-MAT 20's merge work), so that the row stays within seconds."""
+    import graphgen
+    import oracle
+    rows = []
+    for spec, what in ((graphgen.config("er4096"), "whole ER-4096 graph"),
+                       (graphgen.rmat(17, 16, graphgen.BASE_SEED + 1, name="R-MAT scale 17 ef 16"),
+                        "R-MAT scale 17 ef 16, the R-MAT 20 recipe at 1/8 of the vertices")):
+        hs, hd = spec.edges()
+        times = []
+        for _ in range(3 if spec.num_edges < (1 << 20) else 1):
+            t0 = time.perf_counter()
+            T, m = oracle.count(hs, hd, spec.n, threads=1)
+            times.append(time.perf_counter() - t0)
+        t = min(times)
+        rows.append({"value": round(m / t / 1e9, 6), "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                     "sample": f"{what} (sort+CSR+merge count), m = {m}, {t:.3f} s"})
+    return rows
 
 
 def run_unfused(args, dist: Dist):
@@ -567,7 +824,10 @@ def run_list(args, dist: Dist):
     }
 
 
-def run_batch(args, dist: Dist):
+def batch_measure(args, dist: Dist, steps: int, warmup: int, clocks=None) -> dict:
+    """The 4096-graph mix: every graph built once (CSRs resident), then one step = one replay of the batch plan (one
+    persistent launch captured as a CUDA graph) against one graph per launch (tc_count per graph) on the same
+    graphs, at identical counts."""
     import numpy as np
     import torch
 
@@ -575,62 +835,79 @@ def run_batch(args, dist: Dist):
     import paper_1909_02127_gb300 as tc
 
     dev = torch.device("cuda", dist.local)
-    torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
     specs = graphgen.batch_mix(args.batch_graphs, graphgen.BASE_SEED + graphgen.BATCH_SEED_OFFSET
                                + dist.rank * 1000003)
     handles = []
-    for sp in specs:
-        s, d = sp.edges(device=dev)
-        h = tc.tc_load_edges(s, d, sp.n, stream=stream)
-        tc.tc_build(h, stream)
-        handles.append(h)
-    torch.cuda.synchronize()
-    solo = np.array([tc.tc_count(h, stream) for h in handles], dtype=np.uint64)
-    if not np.array_equal(tc.tc_count_batch(handles, stream), solo):
-        raise RuntimeError("batched counts differ from one-by-one counts")
-    plan = tc.tc_batch_plan_create(handles, stream)  # the launch sequence, captured once as a CUDA graph
-    got = np.zeros(len(handles), dtype=np.uint64)
-    for _ in range(args.warmup):
-        tc.tc_batch_plan_run(plan, len(handles), stream, got)
-        if not np.array_equal(got, solo):
+    try:
+        for sp in specs:
+            s, d = sp.edges(device=dev)
+            h = tc.tc_load_edges(s, d, sp.n, stream=stream)
+            handles.append(h)
+            tc.tc_build(h, stream)
+        torch.cuda.synchronize()
+        m_total = sum(tc.tc_graph_get_info(h)["num_edges"] for h in handles)
+        solo = np.array([tc.tc_count(h, stream) for h in handles], dtype=np.uint64)
+        if not np.array_equal(tc.tc_count_batch(handles, stream), solo):
             raise RuntimeError("batched counts differ from one-by-one counts")
-    dist.barrier()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(dist.local)
-    clocks.start()
-    l0 = tc.tc_kernel_launches()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        tc.tc_batch_plan_run(plan, len(handles), stream, got)
-    torch.cuda.synchronize()
-    t_batch = time.perf_counter() - t0
-    launches = tc.tc_kernel_launches() - l0
-    clock_info = clocks.stop()
-    if not np.array_equal(got, solo):
-        raise RuntimeError("batched counts differ")
-    # one graph per launch, same graphs and counts
-    t0 = time.perf_counter()
-    for _ in range(max(1, args.steps // 2)):
+        plan = tc.tc_batch_plan_create(handles, stream)  # the launch sequence, captured once as a CUDA graph
+        try:
+            got = np.zeros(len(handles), dtype=np.uint64)
+            for _ in range(warmup):
+                tc.tc_batch_plan_run(plan, len(handles), stream, got)
+                if not np.array_equal(got, solo):
+                    raise RuntimeError("batched counts differ from one-by-one counts")
+            dist.barrier()
+            torch.cuda.synchronize()
+            if clocks:
+                clocks.start()
+            l0 = tc.tc_kernel_launches()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                tc.tc_batch_plan_run(plan, len(handles), stream, got)
+            torch.cuda.synchronize()
+            t_batch = time.perf_counter() - t0
+            launches = tc.tc_kernel_launches() - l0
+            clock_info = clocks.stop() if clocks else None
+            if not np.array_equal(got, solo):
+                raise RuntimeError("batched counts differ")
+        finally:
+            tc.tc_batch_plan_free(plan)
+        # one graph per launch, same graphs and counts
+        reps = max(1, steps // 2)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            for h, c in zip(handles, solo):
+                if tc.tc_count(h, stream) != int(c):
+                    raise RuntimeError("one-by-one count changed")
+        t_solo = (time.perf_counter() - t0) / reps
+    finally:
         for h in handles:
-            tc.tc_count(h, stream)
-    t_solo = (time.perf_counter() - t0) / max(1, args.steps // 2)
-    units, secs = aggregate(len(handles) * args.steps, t_batch, dist)
+            tc.tc_free(h)
+    units, secs = aggregate(len(handles) * steps, t_batch, dist)
     u1, s1 = aggregate(len(handles), t_solo, dist)
-    tc.tc_batch_plan_free(plan)
-    for h in handles:
-        tc.tc_free(h)
+    return {"graphs": len(handles), "graphs_per_s": round(units / secs, 2),
+            "ms_per_replay": round(t_batch / steps * 1e3, 4), "one_by_one_graphs_per_s": round(u1 / s1, 2),
+            "one_by_one_ms": round(t_solo * 1e3, 3), "speedup_vs_one_by_one": round((units / secs) / (u1 / s1), 3),
+            "edges": int(m_total), "total_triangles": int(solo.sum()), "steps": steps, "gpu_launches": int(launches),
+            "clocks": clock_info}
+
+
+def run_batch(args, dist: Dist):
+    import torch
+    torch.cuda.set_device(torch.device("cuda", dist.local))
+    b = batch_measure(args, dist, args.steps, args.warmup, ClockSampler(dist.local))
     return {
         "metric": "batched graphs/s (4096-graph mix, one persistent launch replayed from a CUDA graph) vs one graph "
                   "per launch",
-        "value": round(units / secs, 2), "unit": "graphs/s", "n_gpus": dist.world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(t_batch / args.steps * 1e3, 4), "higher_is_better": True,
+        "value": b["graphs_per_s"], "unit": "graphs/s", "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": b["ms_per_replay"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32/uint64 (exact integer)", "data": "synthetic",
-        "config": {"workload": f"batch of {len(handles)} graphs (ER/R-MAT mix, n log-uniform [64, 65536])",
-                   "total_triangles": int(solo.sum()), "parallelism": f"replicas x{dist.world}"},
-        "one_by_one_graphs_per_s": round(u1 / s1, 2),
-        "speedup_vs_one_by_one": round((units / secs) / (u1 / s1), 3),
-        "e2e": None, "gpu_launches": int(launches), "clocks": clock_info,
+        "config": {"workload": f"batch of {b['graphs']} graphs (G(n,p)/R-MAT mix, n log-uniform [64, 65536])",
+                   "total_triangles": b["total_triangles"], "parallelism": f"replicas x{dist.world}"},
+        "one_by_one_graphs_per_s": b["one_by_one_graphs_per_s"],
+        "speedup_vs_one_by_one": b["speedup_vs_one_by_one"],
+        "e2e": None, "gpu_launches": b["gpu_launches"], "clocks": b["clocks"],
     }
 
 
@@ -714,105 +991,166 @@ def run_prune(args, dist: Dist):
     }
 
 
-def run_serve(args, dist: Dist):
-    """Replay one Poisson arrival trace against the serving loop twice: continuous batching, then one graph per
-    launch.  Every result is checked against the graph's solo count."""
+class ServePool:
+    """The serving workload's request graphs in one page-locked host buffer, with each graph's solo count."""
+
+    def __init__(self, args, dist: Dist):
+        import numpy as np
+        import torch
+
+        import graphgen
+        import paper_1909_02127_gb300 as tc
+
+        dev = torch.device("cuda", dist.local)
+        self.specs = graphgen.serve_pool(args.serve_pool,
+                                         graphgen.BASE_SEED + graphgen.SERVE_SEED_OFFSET + dist.rank * 7919)
+        sizes = []
+        chunks = []
+        for sp in self.specs:
+            s, d = sp.edges(device=dev)
+            sizes.append(int(s.numel()))
+            chunks.append((s.cpu(), d.cpu()))
+        self.sizes = np.array(sizes, dtype=np.int64)
+        offs = np.concatenate([[0], np.cumsum(self.sizes)])
+        total = int(offs[-1])
+        self.host = torch.empty(2 * total, dtype=torch.int32).pin_memory()
+        for i, (s, d) in enumerate(chunks):
+            self.host[offs[i]:offs[i + 1]].copy_(s)
+            self.host[total + offs[i]:total + offs[i + 1]].copy_(d)
+        del chunks
+        base = self.host.data_ptr()
+        self.src_ptr = [base + 4 * int(offs[i]) for i in range(len(self.specs))]
+        self.dst_ptr = [base + 4 * (total + int(offs[i])) for i in range(len(self.specs))]
+        self.total_pairs = total
+        self.solo = []
+        for i, sp in enumerate(self.specs):
+            g = tc.tc_load_edges(self.host[offs[i]:offs[i + 1]], self.host[total + offs[i]:total + offs[i + 1]], sp.n)
+            tc.tc_build(g)
+            self.solo.append(tc.tc_count(g))
+            tc.tc_free(g)
+
+    def trace(self, rate: float, duration: float, seed_offset: int = 0):
+        """Poisson arrivals and the pool graph each one requests (even / odd requests alternate kinds)."""
+        import graphgen
+        arrivals = graphgen.poisson_arrivals(rate, duration, graphgen.BASE_SEED + graphgen.SERVE_SEED_OFFSET - 1
+                                             + seed_offset)
+        key = graphgen.stream_key(graphgen.BASE_SEED + graphgen.SERVE_SEED_OFFSET - 2 + seed_offset,
+                                  graphgen.STREAM_PARAMS)
+        half = len(self.specs) // 2
+        pick = [2 * (graphgen.draw(key, j) % half) + (j % 2) for j in range(len(arrivals))]
+        return arrivals, pick
+
+
+def serve_replay(args, pool: ServePool, arrivals, pick, batching: bool, deadline_s: float) -> dict:
+    """Replay one arrival trace against a server; every result is checked against its graph's solo count.  Latency
+    = finish - submission, the host-to-device copy inside it."""
     import threading
 
     import numpy as np
-    import torch
 
-    import graphgen
     import paper_1909_02127_gb300 as tc
 
-    dev = torch.device("cuda", dist.local)
-    torch.cuda.set_device(dev)
-    pool = graphgen.serve_pool(args.serve_pool, graphgen.BASE_SEED + graphgen.SERVE_SEED_OFFSET + dist.rank * 7919)
-    gen = [sp.edges(device=dev) for sp in pool]
-    sizes = np.array([int(s.numel()) for s, _ in gen], dtype=np.int64)
-    offs = np.concatenate([[0], np.cumsum(sizes)])
-    total = int(offs[-1])
-    host = torch.empty(2 * total, dtype=torch.int32).pin_memory()
-    for i, (s, d) in enumerate(gen):
-        host[offs[i]:offs[i + 1]].copy_(s)
-        host[total + offs[i]:total + offs[i + 1]].copy_(d)
-    torch.cuda.synchronize()
-    del gen
-    base = host.data_ptr()
-    src_ptr = [base + 4 * int(offs[i]) for i in range(len(pool))]
-    dst_ptr = [base + 4 * (total + int(offs[i])) for i in range(len(pool))]
-    solo = []
-    for i, sp in enumerate(pool):
-        g = tc.tc_load_edges(host[offs[i]:offs[i + 1]], host[total + offs[i]:total + offs[i + 1]], sp.n)
-        tc.tc_build(g)
-        solo.append(tc.tc_count(g))
-        tc.tc_free(g)
-    arrivals = graphgen.poisson_arrivals(args.rate, args.duration)
-    key = graphgen.stream_key(graphgen.BASE_SEED + graphgen.SERVE_SEED_OFFSET - 2, graphgen.STREAM_PARAMS)
-    half = len(pool) // 2
-    pick = [2 * (graphgen.draw(key, j) % half) + (j % 2) for j in range(len(arrivals))]
+    srv = tc.tc_server_create(batching=batching, build_workers=args.build_workers)
+    results = []
+    done = threading.Event()
+    expected = len(arrivals)
 
-    def replay(batching: bool):
-        srv = tc.tc_server_create(batching=batching, build_workers=args.build_workers)
-        results = []
-        done = threading.Event()
-        expected = len(arrivals)
+    def poller():
+        while len(results) < expected and not done.is_set():
+            results.extend(tc.tc_server_poll(srv, 8192, 20))
 
-        def poller():
-            while len(results) < expected and not done.is_set():
-                results.extend(tc.tc_server_poll(srv, 8192, 20))
+    th = threading.Thread(target=poller)
+    th.start()
+    owner = {}
+    t0 = time.perf_counter()
+    for j, ta in enumerate(arrivals):
+        wait = t0 + ta - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        k = pick[j]
+        owner[tc.tc_server_submit(srv, pool.src_ptr[k], pool.dst_ptr[k], int(pool.sizes[k]), pool.specs[k].n)] = k
+    th.join(timeout=deadline_s)
+    done.set()
+    th.join()
+    stats = tc.tc_server_get_stats(srv)
+    tc.tc_server_destroy(srv)
+    if len(results) != expected:
+        raise RuntimeError(f"serve: {len(results)} of {expected} requests finished")
+    bad = [r for r in results if r["status"] != 0 or r["triangles"] != pool.solo[owner[r["id"]]]]
+    if bad:
+        raise RuntimeError(f"serve: {len(bad)} results differ from their solo counts")
+    lat = np.array([(r["t_done_ns"] - r["t_submit_ns"]) / 1e6 for r in results])
+    span = (max(r["t_done_ns"] for r in results) - min(r["t_submit_ns"] for r in results)) / 1e9
+    return {"graphs_per_s": round(expected / span, 2), "p50_ms": round(float(np.percentile(lat, 50)), 3),
+            "p99_ms": round(float(np.percentile(lat, 99)), 3), "mean_ms": round(float(lat.mean()), 3),
+            "launches": stats["launches"], "max_batch": stats["max_batch_seen"],
+            "mean_batch": round(stats["completed"] / max(1, stats["launches"]), 2),
+            "peak_held_gb": round(stats["peak_held_bytes"] / 1e9, 3), "requests": expected,
+            "span_s": round(span, 3)}
 
-        th = threading.Thread(target=poller)
-        th.start()
-        owner = {}
-        t0 = time.perf_counter()
-        for j, ta in enumerate(arrivals):
-            wait = t0 + ta - time.perf_counter()
-            if wait > 0:
-                time.sleep(wait)
-            k = pick[j]
-            owner[tc.tc_server_submit(srv, src_ptr[k], dst_ptr[k], int(sizes[k]), pool[k].n)] = k
-        th.join(timeout=args.duration * 20 + 600)
-        done.set()
-        stats = tc.tc_server_get_stats(srv)
-        tc.tc_server_destroy(srv)
-        if len(results) != expected:
-            raise RuntimeError(f"serve: {len(results)} of {expected} requests finished")
-        bad = [r for r in results if r["status"] != 0 or r["triangles"] != solo[owner[r["id"]]]]
-        if bad:
-            raise RuntimeError(f"serve: {len(bad)} results differ from their solo counts")
-        lat = np.array([(r["t_done_ns"] - r["t_submit_ns"]) / 1e6 for r in results])
-        span = (max(r["t_done_ns"] for r in results) - min(r["t_submit_ns"] for r in results)) / 1e9
-        return {"graphs_per_s": round(expected / span, 2), "p50_ms": round(float(np.percentile(lat, 50)), 3),
-                "p99_ms": round(float(np.percentile(lat, 99)), 3), "mean_ms": round(float(lat.mean()), 3),
-                "launches": stats["launches"], "max_batch": stats["max_batch_seen"],
-                "mean_batch": round(stats["completed"] / max(1, stats["launches"]), 2),
-                "peak_held_gb": round(stats["peak_held_bytes"] / 1e9, 3), "requests": expected,
-                "span_s": round(span, 3)}
 
-    clocks = ClockSampler(dist.local)
+# A mode keeps up with an offered rate when it serves at least this share of it and its p99 stays below the cap.
+KEEP_UP_SHARE = 0.95
+KEEP_UP_P99_MS = 50.0
+
+
+def serve_capacity(args, pool: ServePool, rates, duration: float) -> dict:
+    """The offered-rate sweep: for each rate, the same trace against both modes; the highest rate each mode keeps
+    up with."""
+    out = {"rates": list(rates), "duration_s": duration, "keep_up": {"share": KEEP_UP_SHARE, "p99_ms": KEEP_UP_P99_MS},
+           "batched": [], "one_by_one": []}
+    for i, rate in enumerate(rates):
+        arrivals, pick = pool.trace(rate, duration, seed_offset=100 + i)
+        for mode, batching in (("batched", True), ("one_by_one", False)):
+            r = serve_replay(args, pool, arrivals, pick, batching, duration * 20 + 300)
+            out[mode].append({"rate": rate, "graphs_per_s": r["graphs_per_s"], "p50_ms": r["p50_ms"],
+                              "p99_ms": r["p99_ms"], "mean_batch": r["mean_batch"]})
+    for mode in ("batched", "one_by_one"):
+        ok = [x["rate"] for x in out[mode]
+              if x["graphs_per_s"] >= KEEP_UP_SHARE * x["rate"] and x["p99_ms"] <= KEEP_UP_P99_MS]
+        out[f"{mode}_max_rate"] = max(ok) if ok else None
+    return out
+
+
+def run_serve(args, dist: Dist):
+    """Replay one Poisson arrival trace against the serving loop twice: continuous batching, then one graph per
+    launch.  Every result is checked against the graph's solo count."""
+    import torch
+
+    import paper_1909_02127_gb300 as tc
+
+    torch.cuda.set_device(torch.device("cuda", dist.local))
+    pool = ServePool(args, dist)
+    arrivals, pick = pool.trace(args.rate, args.duration)
+    clocks = ClockSampler(dist.local, period_s=0.05)
     dist.barrier()
     clocks.start()
     l0 = tc.tc_kernel_launches()
-    batched = replay(True)
+    batched = serve_replay(args, pool, arrivals, pick, True, args.duration * 20 + 600)
     launches = tc.tc_kernel_launches() - l0
     clock_info = clocks.stop()
-    single = replay(False)
+    single = serve_replay(args, pool, arrivals, pick, False, args.duration * 20 + 600)
     units, secs = aggregate(batched["requests"], batched["span_s"], dist)
-    return {
+    out = {
         "metric": "served graphs/s with p50/p99 latency (Poisson arrivals, continuous batching) vs one graph per launch",
         "value": round(units / secs, 2), "unit": "graphs/s", "n_gpus": dist.world, "steps": 1, "warmup": 0,
         "ms_per_step": round(batched["span_s"] * 1e3, 2), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32/uint64 (exact integer)", "data": "synthetic",
-        "config": {"workload": f"Poisson {args.rate:g} req/s for {args.duration:g} s over {len(pool)} R-MAT/ER "
-                               f"graphs, pairs log-uniform [1e3, 4e6]",
-                   "pool_pairs": total, "build_workers": args.build_workers, "parallelism": f"replicas x{dist.world}"},
+        "config": {"workload": f"Poisson {args.rate:g} req/s for {args.duration:g} s over {len(pool.specs)} "
+                               f"G(n,p)/R-MAT graphs, sizes log-uniform [1e3, 4e6]",
+                   "pool_pairs": pool.total_pairs, "build_workers": args.build_workers,
+                   "parallelism": f"replicas x{dist.world}"},
         "p50_ms": batched["p50_ms"], "p99_ms": batched["p99_ms"], "batched": batched, "one_by_one": single,
         "speedup_vs_one_by_one": round(batched["graphs_per_s"] / single["graphs_per_s"], 3),
         "e2e": {"value": round(units / secs, 2), "unit": "graphs/s",
-                "h2d_bytes_per_step": int(8 * sum(sizes[k] for k in pick)), "d2h_bytes_per_step": 8 * len(pick)},
+                "h2d_bytes_per_step": int(8 * sum(int(pool.sizes[k]) for k in pick)),
+                "d2h_bytes_per_step": 8 * len(pick)},
         "gpu_launches": int(launches), "clocks": clock_info,
     }
+    if args.serve_rates:
+        out["capacity"] = serve_capacity(args, pool, [float(x) for x in args.serve_rates.split(",")],
+                                         args.sweep_duration)
+    return out
 
 
 # ------------------------------------------------------------------------------------------------------------

@@ -1,5 +1,6 @@
-"""bench.py's host-side arithmetic on CPU: the algorithmic bytes of one counting pass, the counting grid, and the
-rule that ncu traffic is reported only when the summary was taken on the current count-kernel source."""
+"""bench.py's host-side arithmetic on CPU: the algorithmic bytes of one counting pass, the counting grid, the clock
+record, and the rule that ncu traffic is reported only when the summary was taken on the current count-kernel
+source."""
 import pytest
 
 import bench
@@ -19,13 +20,32 @@ def test_dense_rows_trade_their_ids_for_quads():
     assert plain - bench.algorithmic_bytes(info, 4) == 4 * 600 - 16 * 7
 
 
-@pytest.mark.parametrize("bins,grid", [({"bin_block": 0, "bin_warp": 0}, 1),
-                                       ({"bin_block": 3, "bin_warp": 17, "bin_thread": 513}, 3 + 2 + 2),
-                                       ({"bin_block": 10 ** 6, "bin_warp": 0}, 2 * 152)])
-def test_count_grid(bins, grid):
-    """One CTA per block-bin source, one per 16 warp-bin sources and one per 512 thread-bin sources, at most two
-    per SM."""
-    assert bench.count_grid(bins) == grid
+def test_count_grid_is_the_library_s():
+    """The counting grid comes from tc_graph_info.count_ctas (the launch the library makes), not from a copy of its
+    arithmetic."""
+    assert bench.count_grid({"count_ctas": 7, "bin_block": 10 ** 6}) == 7
+    assert bench.count_grid({"count_ctas": 0}) == 1
+
+
+def test_id_list_bytes_count_every_2path_as_an_id():
+    info = {"num_vertices": 10, "num_edges": 20, "num_wedges": 1000, "dense_wedges": 600, "dense_quads": 7}
+    assert bench.algorithmic_bytes_ids(info, 4) == bench.algorithmic_bytes(
+        {**info, "dense_wedges": 0, "dense_quads": 0}, 4)
+
+
+def test_clock_summary():
+    s = bench.summarize_clocks([(2070.0, 2070.0, []), (1995.0, 2070.0, ["sw_power_cap"]), (2070.0, 2070.0, [])],
+                               "test")
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    assert bench.summarize_clocks([], "test")["samples"] == 0
+
+
+def test_nvml_reason_bits():
+    """The clock-event reason bits of nvml.h map to the names the bench line reports."""
+    names = dict(bench._Nvml.REASONS)
+    assert names[0x4] == "sw_power_cap" and names[0x8] == "hw_slowdown"
+    assert names[0x20] == "sw_thermal_slowdown" and names[0x40] == "hw_thermal_slowdown"
 
 
 def test_profiled_traffic_only_for_the_current_source(tmp_path, monkeypatch):

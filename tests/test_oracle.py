@@ -143,12 +143,13 @@ def test_out_of_range_ids_rejected():
 
 
 def test_er4096_statistical_sanity():
-    """Not a parity pin: uniform sampling of 32768 pairs on 4096 vertices keeps ~32.7K distinct edges, and the
-    expected triangle count is about C(n,3) p^3 = 683 for p = m / C(n,2); a 30% band is > 7 standard deviations."""
+    """Not a parity pin: G(4096, 16/4095) draws no repeats, so the oracle keeps every generated pair (m within 4
+    standard deviations of C(n,2) p = 32768), and the expected triangle count is C(n,3) p^3 = 682.7; a 30% band is
+    > 7 standard deviations."""
     spec = graphgen.config("er4096")
     s, d = spec.edges()
     T, m = oracle.count(s, d, spec.n)
-    assert 32500 < m <= 32768
-    p = m / math.comb(4096, 2)
+    p = 16 / 4095
+    assert m == s.size and abs(m - 32768) < 4 * math.sqrt(32768 * (1 - p))
     expect = math.comb(4096, 3) * p ** 3
     assert abs(T - expect) < 0.3 * expect
