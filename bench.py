@@ -552,11 +552,11 @@ def sub_serve(args, dist: Dist) -> dict:
     offered-rate sweep."""
     pool = ServePool(args, dist)
     arrivals, pick = pool.trace(args.rate, args.extra_serve_duration)
-    batched = serve_replay(args, pool, arrivals, pick, True, args.extra_serve_duration * 20 + 300)
-    single = serve_replay(args, pool, arrivals, pick, False, args.extra_serve_duration * 20 + 300)
     out = {"workload": f"Poisson {args.rate:g} req/s for {args.extra_serve_duration:g} s (a shorter trace than the "
                        f"60 s config) over {len(pool.specs)} G(n,p)/R-MAT graphs, sizes log-uniform [1e3, 4e6]",
-           "pool_pairs": pool.total_pairs, "batched": batched, "one_by_one": single}
+           "pool_pairs": pool.total_pairs}
+    for mode, batching in SERVE_MODES:
+        out[mode] = serve_replay(args, pool, arrivals, pick, batching, args.extra_serve_duration * 20 + 300)
     if args.serve_rates:
         out["capacity"] = serve_capacity(args, pool, [float(x) for x in args.serve_rates.split(",")],
                                          args.sweep_duration)
@@ -839,9 +839,11 @@ def batch_measure(args, dist: Dist, steps: int, warmup: int, clocks=None) -> dic
     specs = graphgen.batch_mix(args.batch_graphs, graphgen.BASE_SEED + graphgen.BATCH_SEED_OFFSET
                                + dist.rank * 1000003)
     handles = []
+    edges = []
     try:
         for sp in specs:
             s, d = sp.edges(device=dev)
+            edges.append((s, d, sp.n))
             h = tc.tc_load_edges(s, d, sp.n, stream=stream)
             handles.append(h)
             tc.tc_build(h, stream)
@@ -884,13 +886,63 @@ def batch_measure(args, dist: Dist, steps: int, warmup: int, clocks=None) -> dic
     finally:
         for h in handles:
             tc.tc_free(h)
+    pipe = pipeline_measure(edges, solo, stream, max(1, steps // 5))
+    del edges
     units, secs = aggregate(len(handles) * steps, t_batch, dist)
     u1, s1 = aggregate(len(handles), t_solo, dist)
     return {"graphs": len(handles), "graphs_per_s": round(units / secs, 2),
             "ms_per_replay": round(t_batch / steps * 1e3, 4), "one_by_one_graphs_per_s": round(u1 / s1, 2),
             "one_by_one_ms": round(t_solo * 1e3, 3), "speedup_vs_one_by_one": round((units / secs) / (u1 / s1), 3),
             "edges": int(m_total), "total_triangles": int(solo.sum()), "steps": steps, "gpu_launches": int(launches),
-            "clocks": clock_info}
+            "clocks": clock_info, "whole_path": pipe}
+
+
+def pipeline_measure(edges, solo, stream, reps: int) -> dict:
+    """The whole path (ingest + build + count) of every graph from device-resident edges: batched by tc_count_many
+    in chunks of at most the compact build's pair limit (each chunk one disjoint union), against one graph at a time
+    (tc_load_edges, tc_build, tc_count, tc_free), at identical counts."""
+    import numpy as np
+    import torch
+
+    import paper_1909_02127_gb300 as tc
+    cap = max(1, tc.tc_get_compact_max_pairs())
+    chunks, cur, pairs = [], [], 0
+    for i, (s, d, n) in enumerate(edges):
+        if cur and pairs + s.numel() > cap:
+            chunks.append(cur)
+            cur, pairs = [], 0
+        cur.append(i)
+        pairs += s.numel()
+    if cur:
+        chunks.append(cur)
+
+    def batched():
+        return np.concatenate([tc.tc_count_many([edges[i] for i in c], stream) for c in chunks])
+
+    if not np.array_equal(batched(), solo):
+        raise RuntimeError("tc_count_many counts differ from one-by-one counts")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        got = batched()
+    torch.cuda.synchronize()
+    t_many = (time.perf_counter() - t0) / reps
+    if not np.array_equal(got, solo):
+        raise RuntimeError("tc_count_many counts differ from one-by-one counts")
+    t0 = time.perf_counter()
+    for (s, d, n), c in zip(edges, solo):
+        g = tc.tc_load_edges(s, d, n, stream=stream)
+        tc.tc_build(g, stream)
+        if tc.tc_count(g, stream) != int(c):
+            raise RuntimeError("one-by-one count changed")
+        tc.tc_free(g)
+    torch.cuda.synchronize()
+    t_one = time.perf_counter() - t0
+    k = len(edges)
+    return {"what": "ingest + build + count of every graph from device-resident edges",
+            "batched_graphs_per_s": round(k / t_many, 1), "batched_calls": len(chunks),
+            "one_by_one_graphs_per_s": round(k / t_one, 1), "speedup_vs_one_by_one": round(t_one / t_many, 3),
+            "reps": reps}
 
 
 def run_batch(args, dist: Dist):
@@ -1041,7 +1093,7 @@ class ServePool:
         return arrivals, pick
 
 
-def serve_replay(args, pool: ServePool, arrivals, pick, batching: bool, deadline_s: float) -> dict:
+def serve_replay(args, pool: ServePool, arrivals, pick, batching, deadline_s: float) -> dict:
     """Replay one arrival trace against a server; every result is checked against its graph's solo count.  Latency
     = finish - submission, the host-to-device copy inside it."""
     import threading
@@ -1051,6 +1103,18 @@ def serve_replay(args, pool: ServePool, arrivals, pick, batching: bool, deadline
     import paper_1909_02127_gb300 as tc
 
     srv = tc.tc_server_create(batching=batching, build_workers=args.build_workers)
+    # warm-up before the timed trace (pool growth, first launches of each kernel): every pool graph once, spread
+    # over the workers, all results awaited
+    warm = list(range(min(len(pool.specs), 256)))
+    for k in warm:
+        tc.tc_server_submit(srv, pool.src_ptr[k], pool.dst_ptr[k], int(pool.sizes[k]), pool.specs[k].n)
+    got = 0
+    t_end = time.perf_counter() + 300
+    while got < len(warm) and time.perf_counter() < t_end:
+        got += len(tc.tc_server_poll(srv, 8192, 50))
+    if got < len(warm):
+        raise RuntimeError("serve: warm-up requests did not finish")
+    stats0 = tc.tc_server_get_stats(srv)
     results = []
     done = threading.Event()
     expected = len(arrivals)
@@ -1081,13 +1145,18 @@ def serve_replay(args, pool: ServePool, arrivals, pick, batching: bool, deadline
         raise RuntimeError(f"serve: {len(bad)} results differ from their solo counts")
     lat = np.array([(r["t_done_ns"] - r["t_submit_ns"]) / 1e6 for r in results])
     span = (max(r["t_done_ns"] for r in results) - min(r["t_submit_ns"] for r in results)) / 1e9
+    launches = stats["launches"] - stats0["launches"]
     return {"graphs_per_s": round(expected / span, 2), "p50_ms": round(float(np.percentile(lat, 50)), 3),
-            "p99_ms": round(float(np.percentile(lat, 99)), 3), "mean_ms": round(float(lat.mean()), 3),
-            "launches": stats["launches"], "max_batch": stats["max_batch_seen"],
-            "mean_batch": round(stats["completed"] / max(1, stats["launches"]), 2),
+            "p99_ms": round(float(np.percentile(lat, 99)), 3), "p999_ms": round(float(np.percentile(lat, 99.9)), 3),
+            "mean_ms": round(float(lat.mean()), 3), "launches": launches, "max_batch": stats["max_batch_seen"],
+            "mean_batch": round((stats["completed"] - stats0["completed"]) / max(1, launches), 2),
             "peak_held_gb": round(stats["peak_held_bytes"] / 1e9, 3), "requests": expected,
             "span_s": round(span, 3)}
 
+
+# The serving modes compared: the whole path batched (each batch of pending requests ingested, built and counted
+# as one disjoint union), the count alone batched, and one graph per launch.
+SERVE_MODES = (("batched", "pipeline"), ("count_batched", True), ("one_by_one", False))
 
 # A mode keeps up with an offered rate when it serves at least this share of it and its p99 stays below the cap.
 KEEP_UP_SHARE = 0.95
@@ -1098,14 +1167,14 @@ def serve_capacity(args, pool: ServePool, rates, duration: float) -> dict:
     """The offered-rate sweep: for each rate, the same trace against both modes; the highest rate each mode keeps
     up with."""
     out = {"rates": list(rates), "duration_s": duration, "keep_up": {"share": KEEP_UP_SHARE, "p99_ms": KEEP_UP_P99_MS},
-           "batched": [], "one_by_one": []}
+           **{mode: [] for mode, _ in SERVE_MODES}}
     for i, rate in enumerate(rates):
         arrivals, pick = pool.trace(rate, duration, seed_offset=100 + i)
-        for mode, batching in (("batched", True), ("one_by_one", False)):
+        for mode, batching in SERVE_MODES:
             r = serve_replay(args, pool, arrivals, pick, batching, duration * 20 + 300)
             out[mode].append({"rate": rate, "graphs_per_s": r["graphs_per_s"], "p50_ms": r["p50_ms"],
                               "p99_ms": r["p99_ms"], "mean_batch": r["mean_batch"]})
-    for mode in ("batched", "one_by_one"):
+    for mode, _ in SERVE_MODES:
         ok = [x["rate"] for x in out[mode]
               if x["graphs_per_s"] >= KEEP_UP_SHARE * x["rate"] and x["p99_ms"] <= KEEP_UP_P99_MS]
         out[f"{mode}_max_rate"] = max(ok) if ok else None
@@ -1126,9 +1195,10 @@ def run_serve(args, dist: Dist):
     dist.barrier()
     clocks.start()
     l0 = tc.tc_kernel_launches()
-    batched = serve_replay(args, pool, arrivals, pick, True, args.duration * 20 + 600)
+    batched = serve_replay(args, pool, arrivals, pick, "pipeline", args.duration * 20 + 600)
     launches = tc.tc_kernel_launches() - l0
     clock_info = clocks.stop()
+    count_batched = serve_replay(args, pool, arrivals, pick, True, args.duration * 20 + 600)
     single = serve_replay(args, pool, arrivals, pick, False, args.duration * 20 + 600)
     units, secs = aggregate(batched["requests"], batched["span_s"], dist)
     out = {
@@ -1140,7 +1210,8 @@ def run_serve(args, dist: Dist):
                                f"G(n,p)/R-MAT graphs, sizes log-uniform [1e3, 4e6]",
                    "pool_pairs": pool.total_pairs, "build_workers": args.build_workers,
                    "parallelism": f"replicas x{dist.world}"},
-        "p50_ms": batched["p50_ms"], "p99_ms": batched["p99_ms"], "batched": batched, "one_by_one": single,
+        "p50_ms": batched["p50_ms"], "p99_ms": batched["p99_ms"], "batched": batched,
+        "count_batched": count_batched, "one_by_one": single,
         "speedup_vs_one_by_one": round(batched["graphs_per_s"] / single["graphs_per_s"], 3),
         "e2e": {"value": round(units / secs, 2), "unit": "graphs/s",
                 "h2d_bytes_per_step": int(8 * sum(int(pool.sizes[k]) for k in pick)),

@@ -242,6 +242,26 @@ TC_API tc_status tc_count_unfused(tc_graph* g, uint64_t* out_total, int64_t max_
 TC_API tc_status tc_count_batch(tc_graph* const* gs, int32_t num_graphs, uint64_t* out_counts, void* stream);
 
 /*
+ * tc_count_many — count k graphs given as edge lists, ingested, built and counted together as one pipeline: their
+ * disjoint union (graph j's ids offset past the vertices of graphs 0..j-1) is built once, and every triangle, found
+ * once from its first vertex in the visiting order (Sec. III-A, III-C), is credited to the graph holding that vertex.
+ * No triangle spans two graphs, so counts[j] is graph j's own T (Def. 2, Sec. II-A).  The batching itself has no
+ * counterpart in the paper: for many small graphs it replaces one launch sequence per graph with one per batch.
+ *   srcs, dsts    k pointers to int32 arrays of num_edges[j] pairs each (host or device per flags, all alike; host
+ *                 arrays that are page-locked and mapped are read in place, other host arrays are copied first).
+ *                 The caller keeps them; they are not needed after the call returns.
+ *   num_edges     k pair counts; num_vertices: k vertex counts (graph j's ids in [0, num_vertices[j])).
+ *   counts        k uint64 (host), overwritten with each graph's triangle count.
+ * The vertices of all k graphs together must fit the int32 id range and their pairs number below 2^32 - 1
+ * (TC_ERR_INVALID_ARG otherwise).  An id outside its graph's range gives TC_ERR_OUT_OF_RANGE.  Self-loops and
+ * repeated pairs are dropped per graph, as in tc_load_edges.  Device memory comes from the library's pool.
+ * Blocks until the counts are valid.
+ */
+TC_API tc_status tc_count_many(const int32_t* const* srcs, const int32_t* const* dsts, const int64_t* num_edges,
+                               const int64_t* num_vertices, int32_t k, uint32_t flags, uint64_t* counts,
+                               void* stream);
+
+/*
  * Batch plans — tc_count_batch for a fixed set of graphs counted repeatedly.  tc_batch_plan_create uploads the
  * batch's work table once and captures the launch sequence (zero the counters, the persistent kernel, the copy of
  * the counts to pinned host memory) as a CUDA graph on `stream`; tc_batch_plan_run replays it with one graph launch
@@ -264,7 +284,10 @@ typedef struct tc_server tc_server; /* opaque */
 typedef struct tc_server_config {
   int32_t build_workers;      /* threads that copy and build admitted requests, one stream each (0: 4)           */
   int32_t max_batch;          /* most graphs per counting launch (0: 4096)                                        */
-  int32_t batching;           /* 1: continuous batching; 0: one graph per launch                                  */
+  int32_t batching;           /* 1: continuous batching of the count (each request built alone, ready graphs
+                                 counted together); 2: continuous batching of the whole path (the pending requests
+                                 that the budget admits ingested, built and counted together, as tc_count_many);
+                                 0: one graph per launch                                                          */
   int32_t max_inflight;       /* most admitted, unfinished requests (0: 8192)                                     */
   int64_t hbm_reserve_bytes;  /* device memory never used by admissions (< 0: 8 GiB)                              */
   int64_t hbm_budget_bytes;   /* if > 0, an upper bound on the admission budget                                   */
@@ -363,6 +386,17 @@ typedef struct tc_tuning {
                                                           and by a radix sort of all pairs above it (the buckets'
                                                           random accesses stop fitting in L2); 0: always buckets.
                                                           >= 0 */
+  int64_t compact_max_pairs;                           /* tc_build of a graph with at most this many input pairs (on
+                                                          the bucketed path) synchronises with the host once: buffers
+                                                          whose size depends on the data are allocated at bounds
+                                                          known from n and the pair count, and every size is read
+                                                          back at the end.  Above it, sizes are read as they become
+                                                          known (smaller allocations).  0: never.  >= 0 */
+  int64_t stage_min_csr_bytes;                         /* tc_count and tc_count_device walk long hop-2 rows through a
+                                                          ring of shared memory filled by asynchronous copies
+                                                          (cp.async) for graphs whose CSR (8(n+1) + 4 csr_entries
+                                                          bytes) is at least this large, i.e. read from DRAM rather
+                                                          than L2.  0: never.  >= 0 */
 } tc_tuning;
 
 /* tc_set_tuning — replace the table (TC_ERR_INVALID_ARG if malformed).  Applies to graphs built afterwards. */

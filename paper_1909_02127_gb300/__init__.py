@@ -52,7 +52,8 @@ class tc_tuning(ctypes.Structure):
                 ("batch_warp_max_edges", ctypes.c_int64),
                 ("class_max_edges", ctypes.c_int64 * TC_TUNING_MAX_CLASSES),
                 ("block_min_work", ctypes.c_int64 * TC_TUNING_MAX_CLASSES),
-                ("isect_max_wedges_milli", ctypes.c_int64), ("bucket_max_pairs", ctypes.c_int64)]
+                ("isect_max_wedges_milli", ctypes.c_int64), ("bucket_max_pairs", ctypes.c_int64),
+                ("compact_max_pairs", ctypes.c_int64), ("stage_min_csr_bytes", ctypes.c_int64)]
 
 
 class tc_server_config(ctypes.Structure):
@@ -87,7 +88,7 @@ EXPORTED = ["tc_load_edges", "tc_build", "tc_build_pruned", "tc_count", "tc_coun
             "tc_server_poll", "tc_server_get_stats", "tc_server_destroy", "tc_batch_plan_create",
             "tc_batch_plan_run", "tc_batch_plan_free",
             "tc_graph_get_info", "tc_copy_csr", "tc_free", "tc_last_error", "tc_kernel_launches", "tc_set_tuning",
-            "tc_get_tuning"]
+            "tc_get_tuning", "tc_count_many"]
 
 _lib = None
 
@@ -126,6 +127,9 @@ def load_library(path: str = LIB_PATH):
     lib.tc_count_per_vertex_noalloc.restype = st
     lib.tc_count_batch.argtypes = [ctypes.POINTER(vp), i32, u64p, vp]
     lib.tc_count_batch.restype = st
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    lib.tc_count_many.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), i64p, i64p, i32, u32, u64p, vp]
+    lib.tc_count_many.restype = st
     lib.tc_graph_get_info.argtypes = [vp, ctypes.POINTER(tc_graph_info)]
     lib.tc_graph_get_info.restype = st
     lib.tc_copy_csr.argtypes = [vp, vp, vp, vp, vp]
@@ -182,19 +186,24 @@ def _apply_tuning_file(lib, path: str = TUNING_FILE) -> bool:
         lib.tc_get_tuning(ctypes.byref(cur))
         t = _tuning_struct(data["classes"], data.get("batch_warp_max_edges", 1 << 25),
                            data.get("isect_max_wedges_milli", 0),
-                           data.get("bucket_max_pairs", cur.bucket_max_pairs))
+                           data.get("bucket_max_pairs", cur.bucket_max_pairs),
+                           data.get("compact_max_pairs", cur.compact_max_pairs),
+                           data.get("stage_min_csr_bytes", cur.stage_min_csr_bytes))
         return lib.tc_set_tuning(ctypes.byref(t)) == TC_OK
     except Exception:
         return False
 
 
 def _tuning_struct(classes, batch_warp_max_edges: int = 1 << 25, isect_max_wedges_milli: int = 0,
-                   bucket_max_pairs: int = 1 << 29) -> "tc_tuning":
+                   bucket_max_pairs: int = 1 << 29, compact_max_pairs: int = 1 << 25,
+                   stage_min_csr_bytes: int = 4 << 30) -> "tc_tuning":
     t = tc_tuning()
     t.num_classes = len(classes)
     t.batch_warp_max_edges = int(batch_warp_max_edges)
     t.isect_max_wedges_milli = int(isect_max_wedges_milli)
     t.bucket_max_pairs = int(bucket_max_pairs)
+    t.compact_max_pairs = int(compact_max_pairs)
+    t.stage_min_csr_bytes = int(stage_min_csr_bytes)
     for i, (max_edges, work) in enumerate(classes):
         t.class_max_edges[i] = int(max_edges)
         t.block_min_work[i] = int(work)
@@ -202,9 +211,11 @@ def _tuning_struct(classes, batch_warp_max_edges: int = 1 << 25, isect_max_wedge
 
 
 def tc_set_tuning(classes, batch_warp_max_edges: Optional[int] = None,
-                  isect_max_wedges_milli: Optional[int] = None, bucket_max_pairs: Optional[int] = None) -> None:
+                  isect_max_wedges_milli: Optional[int] = None, bucket_max_pairs: Optional[int] = None,
+                  compact_max_pairs: Optional[int] = None, stage_min_csr_bytes: Optional[int] = None) -> None:
     """classes: [(max_edges, block_min_work), ...] with ascending max_edges; batch_warp_max_edges,
-    isect_max_wedges_milli and bucket_max_pairs: keep the current values if None."""
+    isect_max_wedges_milli, bucket_max_pairs, compact_max_pairs and stage_min_csr_bytes: keep the current values if
+    None."""
     if not 1 <= len(classes) <= TC_TUNING_MAX_CLASSES:
         raise ValueError("1..16 classes")
     cur = tc_tuning()
@@ -215,7 +226,12 @@ def tc_set_tuning(classes, batch_warp_max_edges: Optional[int] = None,
         isect_max_wedges_milli = cur.isect_max_wedges_milli
     if bucket_max_pairs is None:
         bucket_max_pairs = cur.bucket_max_pairs
-    t = _tuning_struct(classes, batch_warp_max_edges, isect_max_wedges_milli, bucket_max_pairs)
+    if compact_max_pairs is None:
+        compact_max_pairs = cur.compact_max_pairs
+    if stage_min_csr_bytes is None:
+        stage_min_csr_bytes = cur.stage_min_csr_bytes
+    t = _tuning_struct(classes, batch_warp_max_edges, isect_max_wedges_milli, bucket_max_pairs, compact_max_pairs,
+                       stage_min_csr_bytes)
     _check(load_library().tc_set_tuning(ctypes.byref(t)))
 
 
@@ -223,6 +239,18 @@ def tc_get_tuning():
     t = tc_tuning()
     _check(load_library().tc_get_tuning(ctypes.byref(t)))
     return [(int(t.class_max_edges[i]), int(t.block_min_work[i])) for i in range(t.num_classes)]
+
+
+def tc_get_stage_min_csr_bytes() -> int:
+    t = tc_tuning()
+    _check(load_library().tc_get_tuning(ctypes.byref(t)))
+    return int(t.stage_min_csr_bytes)
+
+
+def tc_get_compact_max_pairs() -> int:
+    t = tc_tuning()
+    _check(load_library().tc_get_tuning(ctypes.byref(t)))
+    return int(t.compact_max_pairs)
 
 
 def tc_get_bucket_max_pairs() -> int:
@@ -467,6 +495,36 @@ def tc_count_batch(gs: Sequence[int], stream=None) -> np.ndarray:
     return out
 
 
+def tc_count_many(graphs, stream=None) -> np.ndarray:
+    """Triangle counts of several graphs counted as one pipeline (their disjoint union built once).  graphs: a
+    sequence of (src, dst, num_vertices) with src/dst int32 numpy arrays (host) or CUDA tensors (device), all of one
+    kind.  Returns a uint64 array of the counts."""
+    lib = load_library()
+    k = len(graphs)
+    keep, sp, dp = [], [], []
+    flags = None
+    for src, dst, _ in graphs:
+        s_, d_, m, f, kp = _edge_ptrs(src, dst)
+        if flags is not None and f != flags:
+            raise ValueError("all graphs' arrays must be on the host, or all on the device")
+        flags = f
+        keep.append(kp)
+        sp.append(s_)
+        dp.append(d_)
+    ne = np.array([len(g[0]) for g in graphs], dtype=np.int64)
+    nv = np.array([int(g[2]) for g in graphs], dtype=np.int64)
+    out = np.zeros(k, dtype=np.uint64)
+    if k == 0:
+        return out
+    arr_s = (ctypes.c_void_p * k)(*sp)
+    arr_d = (ctypes.c_void_p * k)(*dp)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    _check(lib.tc_count_many(arr_s, arr_d, ne.ctypes.data_as(i64p), nv.ctypes.data_as(i64p), k, flags,
+                             out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), _stream_ptr(stream)))
+    del keep
+    return out
+
+
 def tc_batch_plan_create(gs: Sequence[int], stream=None) -> int:
     arr = (ctypes.c_void_p * len(gs))(*gs)
     out = ctypes.c_void_p()
@@ -510,10 +568,11 @@ def tc_free(g: int) -> None:
         load_library().tc_free(g)
 
 
-def tc_server_create(build_workers: int = 4, max_batch: int = 4096, batching: bool = True, max_inflight: int = 8192,
+def tc_server_create(build_workers: int = 4, max_batch: int = 4096, batching=True, max_inflight: int = 8192,
                      hbm_reserve_bytes: int = -1, hbm_budget_bytes: int = 0) -> int:
-    cfg = tc_server_config(build_workers, max_batch, 1 if batching else 0, max_inflight, hbm_reserve_bytes,
-                           hbm_budget_bytes)
+    """batching: True / 1 batches the count, 2 (or "pipeline") the whole path, False / 0 neither."""
+    mode = 2 if batching == "pipeline" else int(batching)
+    cfg = tc_server_config(build_workers, max_batch, mode, max_inflight, hbm_reserve_bytes, hbm_budget_bytes)
     out = ctypes.c_void_p()
     _check(load_library().tc_server_create(ctypes.byref(cfg), ctypes.byref(out)))
     return out.value

@@ -229,7 +229,7 @@ extern "C" TC_API tc_status tc_count_batch(tc_graph* const* gs, int32_t num_grap
   const Allocator& a = gs[0]->alloc;
   std::vector<unsigned char> host;
   const BatchLayout L = batch_table(gs, num_graphs, host);
-  TC_CUDA(cudaFuncSetAttribute(k_count_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, dev::kCountSmem));
+  TC_TRY(smem_attribute_once<k_count_batch>(dev::kCountSmem));
   Buf dev;
   TC_TRY(buf_alloc(a, dev, L.total_bytes, s));
   tc_status st = cuda_status(cudaMemcpyAsync(dev.p, host.data(), L.table_bytes, cudaMemcpyHostToDevice, s), "H2D");

@@ -17,6 +17,7 @@
 // relabelled before the one sort that also removes the repeats.  Relabelling by rank gives the kernel two things:
 // hubs get the highest ids, so a bitmap over the top ids answers most closing-edge tests; and hub rows, which are
 // re-read by many sources, sit together in memory.
+#include <atomic>
 #include <climits>
 
 #include "tc_build.cuh"
@@ -141,6 +142,73 @@ __global__ void __launch_bounds__(kPackThreads) k_pack(const int32_t* __restrict
       const int32_t k = skey[slot];
       if (k >= 0) {
         atomicAdd(&indeg[k], scnt[slot]);
+        skey[slot] = -1;
+        scnt[slot] = 0;
+      }
+    }
+    __syncthreads();
+  }
+  if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(err, 1u);
+}
+
+// Ingest of several graphs as their disjoint union: pair i belongs to graph k with eoff[k] <= i < eoff[k + 1], its
+// ids are checked against that graph's vertex range [0, voff[k + 1] - voff[k]) and then offset by voff[k].  The
+// arrays of graph k are srcs[k], dsts[k] (device-readable).  Tiles of kPackTile pairs, four consecutive pairs per
+// thread; the counts are combined per tile as in k_pack.
+struct ManyInput {
+  const int32_t* const* srcs;
+  const int32_t* const* dsts;
+  const int64_t* eoff;  // k + 1 pair offsets
+  const int64_t* voff;  // k + 1 vertex offsets
+  int32_t k;
+};
+
+__global__ void __launch_bounds__(kPackThreads) k_pack_many(ManyInput in, int64_t len, int64_t n, int B,
+                                                            uint64_t* __restrict__ keys, int32_t* __restrict__ indeg,
+                                                            uint32_t* __restrict__ err) {
+  __shared__ int32_t skey[kPackSlots];
+  __shared__ int32_t scnt[kPackSlots];
+  const uint64_t sentinel = (1ull << (2 * B)) - 1ull;
+  for (int i = threadIdx.x; i < kPackSlots; i += kPackThreads) {
+    skey[i] = -1;
+    scnt[i] = 0;
+  }
+  __syncthreads();
+  bool bad = false;
+  for (int64_t tile = (int64_t)blockIdx.x * kPackTile; tile < len; tile += (int64_t)gridDim.x * kPackTile) {
+    const int64_t i0 = tile + kPackItems * threadIdx.x;
+    if (i0 < len) {
+      int a = 0, b = in.k;  // graph of pair i0: the last k with eoff[k] <= i0
+      while (b - a > 1) {
+        const int mid = (a + b) >> 1;
+        if (__ldg(&in.eoff[mid]) <= i0)
+          a = mid;
+        else
+          b = mid;
+      }
+      int g = a;
+      for (int j = 0; j < kPackItems; ++j) {
+        const int64_t i = i0 + j;
+        if (i >= len) break;
+        while (__ldg(&in.eoff[g + 1]) <= i) ++g;  // graphs without pairs are skipped
+        const int64_t e = i - __ldg(&in.eoff[g]);
+        const int64_t v0 = __ldg(&in.voff[g]), nv = __ldg(&in.voff[g + 1]) - v0;
+        const int32_t x = __ldg(&in.srcs[g][e]), y = __ldg(&in.dsts[g][e]);
+        uint64_t key;
+        if (x < 0 || y < 0 || x >= nv || y >= nv) {
+          bad = true;
+          key = sentinel;
+        } else {
+          key = pack_pair((int32_t)(x + v0), (int32_t)(y + v0), n, B, sentinel, skey, scnt, indeg, bad);
+        }
+        keys[i] = key;
+      }
+    }
+    __syncthreads();
+    for (int slot = threadIdx.x; slot < kPackSlots; slot += kPackThreads) {
+      const int32_t key = skey[slot];
+      if (key >= 0) {
+        atomicAdd(&indeg[key], scnt[slot]);
         skey[slot] = -1;
         scnt[slot] = 0;
       }
@@ -616,8 +684,13 @@ __global__ void __launch_bounds__(kBigThreads) k_rows_block(const int64_t* __res
 // one quad is written by its own lane with one 16-byte store; longer rows by the whole warp.
 __global__ void k_rows_copy(const int64_t* __restrict__ pstart, const int32_t* __restrict__ tgt,
                             const int32_t* __restrict__ d, const int64_t* __restrict__ off, int64_t n,
-                            int32_t* __restrict__ col, int32_t pad) {
+                            int32_t* __restrict__ col, int32_t pad, int64_t* __restrict__ entries_out) {
   const int lane = threadIdx.x & 31;
+  if (entries_out && blockIdx.x == 0 && threadIdx.x < 4) {  // the spare quad after the last row, and off[n]
+    const int64_t e = off[n];
+    col[e + threadIdx.x] = pad;
+    if (threadIdx.x == 0) *entries_out = e;
+  }
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t base = warp0 * 32; base < n; base += nwarps * 32) {
@@ -775,7 +848,9 @@ __global__ void k_dense_select(const int32_t* __restrict__ dplus, int64_t n, int
 
 // dq0[i] = first quad of the dense row of base_w + i, or -1; qoff is the exclusive scan of the quad counts.
 __global__ void k_dense_index(const int32_t* __restrict__ nq, const int64_t* __restrict__ qoff, int64_t wn,
-                              int32_t* __restrict__ dq0, unsigned long long* __restrict__ rows) {
+                              int32_t* __restrict__ dq0, unsigned long long* __restrict__ rows,
+                              int64_t* __restrict__ quads_out) {
+  if (quads_out && blockIdx.x == 0 && threadIdx.x == 0) *quads_out = qoff[wn];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < wn; i += (int64_t)gridDim.x * blockDim.x) {
     const bool on = nq[i] > 0;
     dq0[i] = on ? (int32_t)qoff[i] : -1;
@@ -784,10 +859,12 @@ __global__ void k_dense_index(const int32_t* __restrict__ nq, const int64_t* __r
   }
 }
 
-// One warp per window vertex: the bits of N+(v) into its (zeroed) dense row.
+// One warp per window vertex: the bits of N+(v) into its dense row, which is zero beforehand, or is zeroed here
+// first when nq (its quad count per window vertex) is given.
 __global__ void k_dense_fill(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
                              const int32_t* __restrict__ dplus, int64_t n, int32_t base_w,
-                             const int32_t* __restrict__ dq0, uint32_t* __restrict__ words) {
+                             const int32_t* __restrict__ dq0, uint32_t* __restrict__ words,
+                             const int32_t* __restrict__ nq) {
   const int lane = threadIdx.x & 31;
   const int64_t wn = n - base_w;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -799,6 +876,11 @@ __global__ void k_dense_fill(const int64_t* __restrict__ off, const int32_t* __r
     const int64_t beg = off[v];
     const int32_t d = dplus[v];
     const int64_t w0 = 4 * (int64_t)q0 - 4 * ((v + 1 - base_w) >> 7);  // word of window word 0, relative
+    if (nq) {
+      uint4* q = reinterpret_cast<uint4*>(words) + q0;
+      for (int32_t j = lane; j < nq[i]; j += 32) q[j] = make_uint4(0u, 0u, 0u, 0u);
+      __syncwarp();
+    }
     for (int32_t j = lane; j < d; j += 32) {
       const int32_t b = col[beg + j] - base_w;
       atomicOr(&words[w0 + (b >> 5)], 1u << (b & 31));
@@ -822,6 +904,19 @@ tc_status pack_edges(tc_graph* g, const int32_t* src, const int32_t* dst, int64_
   const int grid = (int)(tiles < 4 * num_sms() ? tiles : 4 * num_sms());
   k_pack<<<grid, kPackThreads, 0, s>>>(src, dst, len, g->n, g->key_bits, g->keys.as<uint64_t>() + offset,
                                        g->indeg.as<int32_t>(), d_err);
+  note_launch();
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+tc_status pack_edges_many(tc_graph* g, const int32_t* const* d_srcs, const int32_t* const* d_dsts,
+                          const int64_t* d_eoff, const int64_t* d_voff, int32_t k, uint32_t* d_err, cudaStream_t s) {
+  const int64_t len = g->num_pairs;
+  if (len <= 0) return TC_OK;
+  const int64_t tiles = (len + kPackTile - 1) / kPackTile;
+  const int grid = (int)(tiles < 4 * num_sms() ? tiles : 4 * num_sms());
+  k_pack_many<<<grid, kPackThreads, 0, s>>>(ManyInput{d_srcs, d_dsts, d_eoff, d_voff, k}, len, g->n, g->key_bits,
+                                            g->keys.as<uint64_t>(), g->indeg.as<int32_t>(), d_err);
   note_launch();
   TC_CUDA(cudaGetLastError());
   return TC_OK;
@@ -1004,7 +1099,8 @@ tc_status bucket_csr(tc_graph* g, const int32_t* rank, const int32_t* rcount, Bu
     if ((st = launched("k_fill"))) break;
     if (n > 0 && *entries > 0) {
       k_rows_copy<<<grid_for(n, 256), 256, 0, s>>>(pstart.as<int64_t>(), tgt.as<int32_t>(), dplus.as<int32_t>(),
-                                                   g->off.as<int64_t>(), n, g->col.as<int32_t>(), (int32_t)n);
+                                                   g->off.as<int64_t>(), n, g->col.as<int32_t>(), (int32_t)n,
+                                                   nullptr);
       if ((st = launched("k_rows_copy"))) break;
     }
   } while (0);
@@ -1012,7 +1108,11 @@ tc_status bucket_csr(tc_graph* g, const int32_t* rank, const int32_t* rcount, Bu
   return st;
 }
 
-tc_status build_graph(tc_graph* g, cudaStream_t s) { return build_graph_pruned(g, -1, nullptr, s); }
+tc_status build_graph(tc_graph* g, cudaStream_t s) {
+  if (g->n > 0 && g->num_pairs > 0 && g->num_pairs <= compact_max_pairs() && use_buckets(g->num_pairs))
+    return build_graph_compact(g, s);
+  return build_graph_pruned(g, -1, nullptr, s);
+}
 
 tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* ps, cudaStream_t s) {
   const Allocator& a = g->alloc;
@@ -1159,7 +1259,7 @@ tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* p
       if ((st = launched("k_dense_select"))) break;
       if ((st = exclusive_scan_i32_to_i64(a, dnq.as<int32_t>(), dqoff.as<int64_t>(), wn, s))) break;
       k_dense_index<<<grid_for(wn, 256), 256, 0, s>>>(dnq.as<int32_t>(), dqoff.as<int64_t>(), wn,
-                                                      g->dq0.as<int32_t>(), drows);
+                                                      g->dq0.as<int32_t>(), drows, nullptr);
       if ((st = launched("k_dense_index"))) break;
       if ((st = cuda_status(cudaMemcpyAsync(&dquads, dqoff.as<int64_t>() + wn, 8, cudaMemcpyDeviceToHost, s),
                             "copy dense quads")))
@@ -1187,7 +1287,7 @@ tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* p
       if ((st = cuda_status(cudaMemsetAsync(g->dense.p, 0, (size_t)dquads * 16, s), "memset dense"))) break;
       k_dense_fill<<<grid_for(wn * 32, 256), 256, 0, s>>>(g->off.as<int64_t>(), g->col.as<int32_t>(),
                                                            odeg.as<int32_t>(), n, vw.base_w, g->dq0.as<int32_t>(),
-                                                           g->dense.as<uint32_t>());
+                                                           g->dense.as<uint32_t>(), nullptr);
       if ((st = launched("k_dense_fill"))) break;
       // the graph is complete when tc_build returns: another stream may count it next
       if ((st = cuda_status(cudaStreamSynchronize(s), "sync dense rows"))) break;
@@ -1203,6 +1303,7 @@ tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* p
     buf_release(a, *b, s);
   buf_release(a, g->keys, s);
   buf_release(a, g->indeg, s);
+  buf_release(a, g->ingest, s);
   if (st != TC_OK) return st;
   g->wedges = (int64_t)hb.wedges;
   g->dense_wedges = g->dense_rows > 0 ? (int64_t)hb.dense_wedges : 0;
@@ -1213,6 +1314,199 @@ tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* p
   g->nt = hb.nt;
   g->max_out_degree = hb.max_out;
   return TC_OK;
+}
+
+}  // namespace tc
+
+namespace tc {
+namespace {
+
+// What a compact build reads back once, at its end (it lands in the graph's pinned slot after the count word).
+struct CompactSizes {
+  RowCounters rc;
+  BinCounters bc;
+  int64_t entries;              // padded column entries: off[n]
+  int64_t dquads;               // quads of the dense rows
+  unsigned long long dense_rows;
+  int32_t maxdeg;               // (written by k_rank_keys; unused)
+  int32_t pad;
+};
+static_assert(sizeof(CompactSizes) + 8 <= kHostSlotBytes, "the compact build's sizes must fit the landing slot");
+
+int bits_of(int64_t x) {
+  int b = 0;
+  while (b < 63 && (int64_t(1) << b) <= x) ++b;
+  return b;
+}
+
+// Scratch of a compact build, all pieces of one allocation.
+struct CompactScratch {
+  CompactSizes* sizes;
+  uint64_t *rkeys, *rkeys_alt;
+  int32_t *rank, *rcount, *tgt, *odeg, *lists, *plen, *dnq;
+  int64_t *pstart, *cur, *dqoff;
+  int2* rowinfo;
+  void *scan_tmp, *sort_tmp;
+};
+
+CompactScratch compact_scratch(Arena& ar, int64_t n, int64_t M, int64_t wn) {
+  CompactScratch c;
+  c.sizes = ar.take<CompactSizes>(1);
+  c.rkeys = ar.take<uint64_t>(n);
+  c.rkeys_alt = ar.take<uint64_t>(n);
+  c.rank = ar.take<int32_t>(n);
+  c.rcount = ar.take<int32_t>(n);
+  c.pstart = ar.take<int64_t>(n + 1);
+  c.cur = ar.take<int64_t>(n);
+  c.tgt = ar.take<int32_t>(2 * M);
+  c.odeg = ar.take<int32_t>(n);
+  c.lists = ar.take<int32_t>(n);
+  c.plen = ar.take<int32_t>(n);
+  c.rowinfo = ar.take<int2>(n);
+  c.dnq = ar.take<int32_t>(wn > 0 ? wn : 1);
+  c.dqoff = ar.take<int64_t>(wn + 1);
+  c.scan_tmp = ar.take<char>(scan_temp_bytes(n > wn ? n : wn));
+  c.sort_tmp = ar.take<char>(radix_temp_bytes(n));
+  return c;
+}
+
+// The graph's arrays of a compact build as views into one block: off, col (at the column bound), perm, the source
+// lists, the dense-row index and store (at the dense bound).
+void csr_views(Arena& ar, tc_graph* g, int64_t n, int64_t bound_entries, int64_t wn, int64_t dense_quads) {
+  g->off = ar.view((size_t)(n + 1) * 8);
+  g->col = ar.view((size_t)(bound_entries + 4) * 4);
+  g->perm = ar.view((size_t)n * 4);
+  g->list = ar.view((size_t)n * 4);
+  g->tlist = ar.view((size_t)n * 4);
+  g->dq0 = ar.view((size_t)(wn > 0 ? wn : 1) * 4);
+  g->dense = ar.view((size_t)dense_quads * 16);
+}
+
+}  // namespace
+
+// tc_build for inputs of up to compact_max_pairs() pairs, on the bucketed path, with one host synchronisation and
+// few host calls: the same kernels as build_graph_pruned, launched back to back; every buffer whose size depends on
+// the data is allocated at a bound known from n and the pair count M, and every size is read back once at the end.
+//   rank sort   on bits(M) count bits (an input-pair count is at most M) instead of the measured maximum
+//   columns     at most M + 3 min(n, M) padded entries (m <= M; padding adds at most 3 per non-empty row)
+//   dense rows  at most M / 4 quads (a row is dense only when it has at least 4 entries per quad); each row is
+//               zeroed by the warp that fills it
+// All scratch is one allocation, and the graph's arrays are views into one block, so a build makes two allocation
+// calls: for small graphs the host calls, not the kernels, took most of the build.
+tc_status build_graph_compact(tc_graph* g, cudaStream_t s) {
+  const Allocator& a = g->alloc;
+  const int B = g->key_bits;
+  const int64_t M = g->num_pairs;
+  const int64_t n = g->n;
+  tc_status st = TC_OK;
+  auto launched = [&](const char* what) {
+    note_launch();
+    return cuda_status(cudaGetLastError(), what);
+  };
+  int32_t mid_max = 2048;
+  while ((2 * M) / mid_max > (int64_t)kBigBits) mid_max <<= 1;
+  const int64_t bound_entries = M + 3 * (n < M ? n : M);
+  const int64_t bound_quads = M / 4 + 1;
+  const int64_t base_w = tc_graph::window_base(n, kWarpBitmapBits);
+  const int64_t wn = n - base_w;
+  Buf scratch;
+  do {
+    // ---- the two allocations ----
+    Arena sizing;
+    compact_scratch(sizing, n, M, wn);
+    if ((st = buf_alloc(a, scratch, sizing.used, s))) break;
+    Arena sa{scratch.as<char>()};
+    const CompactScratch c = compact_scratch(sa, n, M, wn);
+    Arena bsizing;
+    csr_views(bsizing, g, n, bound_entries, wn, bound_quads);
+    if ((st = buf_alloc(a, g->block, bsizing.used, s))) break;
+    Arena ba{g->block.as<char>()};
+    csr_views(ba, g, n, bound_entries, wn, bound_quads);
+    if ((st = cuda_status(cudaMemsetAsync(c.sizes, 0, sizeof(CompactSizes), s), "memset sizes"))) break;
+    CompactSizes* ds = c.sizes;
+    // ---- rank: stable sort of (count << B) | id on the count bits ----
+    k_rank_keys<<<grid_for(n, 256), 256, 0, s>>>(g->indeg.as<int32_t>(), n, B, c.rkeys, &ds->maxdeg);
+    if ((st = launched("k_rank_keys"))) break;
+    uint64_t* rs = nullptr;
+    if ((st = radix_sort_u64(a, c.rkeys, c.rkeys_alt, n, B, B + bits_of(M), &rs, s, c.sort_tmp))) break;
+    k_rank<<<grid_for(n, 256), 256, 0, s>>>(rs, n, B, c.rank, g->perm.as<int32_t>(), c.rcount);
+    if ((st = launched("k_rank"))) break;
+    // ---- buckets: group by the lower-ranked endpoint, sort and de-duplicate each ----
+    if ((st = exclusive_scan_i32_to_i64(a, c.rcount, c.pstart, n, s, c.scan_tmp))) break;
+    if ((st = cuda_status(cudaMemcpyAsync(c.cur, c.pstart, (size_t)n * 8, cudaMemcpyDeviceToDevice, s),
+                          "copy cursors")))
+      break;
+    k_bucket<<<grid_for(M, 256), 256, 0, s>>>(g->keys.as<uint64_t>(), M, B, c.rank,
+                                              reinterpret_cast<unsigned long long*>(c.cur), c.tgt);
+    if ((st = launched("k_bucket"))) break;
+    RowCounters* rc = &ds->rc;
+    k_rows_small<<<grid_for(n, 256), 256, 0, s>>>(c.pstart, c.cur, n, c.tgt, c.odeg, c.lists, rc);
+    if ((st = launched("k_rows_small"))) break;
+    k_rows_warp<<<4 * num_sms(), kRowThreads, 0, s>>>(c.pstart, c.cur, n, c.tgt, c.odeg, c.lists, rc);
+    if ((st = launched("k_rows_warp"))) break;
+    const size_t blk_smem = (size_t)kBigBits / 8;
+    if ((st = smem_attribute_once<k_rows_block>((int)blk_smem))) break;
+    k_rows_block<<<num_sms(), kBigThreads, blk_smem, s>>>(c.pstart, c.cur, n, mid_max, c.tgt, c.odeg, c.lists, rc);
+    if ((st = launched("k_rows_block"))) break;
+    // ---- CSR: padded offsets, then the rows ----
+    k_padded_len<<<grid_for(n, 256), 256, 0, s>>>(c.odeg, n, c.plen);
+    if ((st = launched("k_padded_len"))) break;
+    if ((st = exclusive_scan_i32_to_i64(a, c.plen, g->off.as<int64_t>(), n, s, c.scan_tmp))) break;
+    k_rows_copy<<<grid_for(n, 256), 256, 0, s>>>(c.pstart, c.tgt, c.odeg, g->off.as<int64_t>(), n,
+                                                 g->col.as<int32_t>(), (int32_t)n, &ds->entries);
+    if ((st = launched("k_rows_copy"))) break;
+    // ---- dense rows: selection and quad offsets ----
+    const int32_t wtopq = n > base_w ? (int32_t)(((n - 1 - base_w) >> 7) + 1) : 0;
+    k_dense_select<<<grid_for(n, 256), 256, 0, s>>>(c.odeg, n, (int32_t)base_w, wtopq, c.dnq, c.rowinfo);
+    if ((st = launched("k_dense_select"))) break;
+    if ((st = exclusive_scan_i32_to_i64(a, c.dnq, c.dqoff, wn, s, c.scan_tmp))) break;
+    k_dense_index<<<grid_for(wn, 256), 256, 0, s>>>(c.dnq, c.dqoff, wn, g->dq0.as<int32_t>(), &ds->dense_rows,
+                                                    &ds->dquads);
+    if ((st = launched("k_dense_index"))) break;
+    // ---- bins ----
+    k_bins<<<grid_for(n, 256), 256, 0, s>>>(g->off.as<int64_t>(), g->col.as<int32_t>(), c.rowinfo, n,
+                                            block_min_work_for(M), g->list.as<int32_t>(), g->tlist.as<int32_t>(),
+                                            &ds->bc);
+    if ((st = launched("k_bins"))) break;
+    // ---- dense rows: the bitmaps (each row zeroed by its own warp) ----
+    k_dense_fill<<<grid_for(wn * 32, 256), 256, 0, s>>>(g->off.as<int64_t>(), g->col.as<int32_t>(), c.odeg, n,
+                                                         (int32_t)base_w, g->dq0.as<int32_t>(),
+                                                         g->dense.as<uint32_t>(), c.dnq);
+    if ((st = launched("k_dense_fill"))) break;
+    // ---- every size at once, then the one synchronisation ----
+    CompactSizes* hs = reinterpret_cast<CompactSizes*>(g->host_total + 1);
+    if ((st = cuda_status(cudaMemcpyAsync(hs, ds, sizeof(CompactSizes), cudaMemcpyDeviceToHost, s), "copy sizes")))
+      break;
+    // the graph is complete when tc_build returns: another stream may count it next
+    if ((st = cuda_status(cudaStreamSynchronize(s), "tc_build sync"))) break;
+    if (hs->rc.err) {
+      set_error("tc_build: a bucket's targets exceeded the range bound (inconsistent pair counts)");
+      st = TC_ERR_INTERNAL;
+      break;
+    }
+    if (hs->entries > bound_entries || hs->dquads > bound_quads) {
+      set_error("tc_build: the compact build's size bounds were exceeded");
+      st = TC_ERR_INTERNAL;
+      break;
+    }
+    g->m = (int64_t)hs->rc.m;
+    g->csr_entries = hs->entries;
+    g->dense_rows = (int64_t)hs->dense_rows;
+    g->dense_quads = hs->dquads;
+    g->wedges = (int64_t)hs->bc.wedges;
+    g->dense_wedges = g->dense_rows > 0 ? (int64_t)hs->bc.dense_wedges : 0;
+    g->dense_visits = g->dense_rows > 0 ? (int64_t)hs->bc.dense_visits : 0;
+    g->active = (int64_t)hs->bc.active;
+    g->nb = hs->bc.nb;
+    g->nw = hs->bc.nw;
+    g->nt = hs->bc.nt;
+    g->max_out_degree = hs->bc.max_out;
+  } while (0);
+  buf_release(a, scratch, s);
+  buf_release(a, g->keys, s);
+  buf_release(a, g->indeg, s);
+  buf_release(a, g->ingest, s);
+  return st;
 }
 
 }  // namespace tc

@@ -17,4 +17,9 @@ tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* p
 // Whether tc_build groups `pairs` input pairs by per-source buckets (true) or by a radix sort (the tuning table).
 bool use_buckets(int64_t pairs);
 
+// tc_build with one host synchronisation (sizes bounded from n and the pair count, read back once at the end), for
+// graphs of at most compact_max_pairs() input pairs (the tuning table) on the bucketed path.
+tc_status build_graph_compact(tc_graph* g, cudaStream_t s);
+int64_t compact_max_pairs();
+
 }  // namespace tc

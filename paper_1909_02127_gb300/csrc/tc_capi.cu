@@ -59,6 +59,9 @@ tc_tuning g_tuning = [] {
   t.block_min_work[1] = int64_t(1) << 15;
   t.batch_warp_max_edges = int64_t(1) << 25;
   t.bucket_max_pairs = int64_t(1) << 29;  // measured: buckets faster up to R-MAT 25 (2^29 pairs), sort at 2^30
+  t.compact_max_pairs = int64_t(1) << 25;  // measured faster than reading sizes as known, R-MAT 12-20
+  // measured: staged long rows 1.5% faster at R-MAT 26 (5 GB CSR), 2-7% slower at R-MAT 20-24 (up to 1.2 GB)
+  t.stage_min_csr_bytes = int64_t(4) << 30;
   return t;
 }();
 }  // namespace
@@ -77,6 +80,16 @@ bool use_intersection(const tc_graph* g) {
   }
   if (r <= 0 || g->m <= 0) return false;
   return (long double)g->wedges * 1000.0L <= (long double)r * (long double)g->m;
+}
+
+int64_t stage_min_csr_bytes() {
+  std::lock_guard<std::mutex> lk(g_tuning_mutex);
+  return g_tuning.stage_min_csr_bytes;
+}
+
+int64_t compact_max_pairs() {
+  std::lock_guard<std::mutex> lk(g_tuning_mutex);
+  return g_tuning.compact_max_pairs;
 }
 
 bool use_buckets(int64_t pairs) {
@@ -165,7 +178,7 @@ tc_status buf_alloc(const Allocator& a, Buf& b, size_t bytes, cudaStream_t s) {
 }
 
 void buf_release(const Allocator& a, Buf& b, cudaStream_t s) {
-  if (b.p) a.free(b.p, s);
+  if (b.p && b.owned) a.free(b.p, s);
   b = Buf{};
 }
 
@@ -173,31 +186,38 @@ void buf_release(const Allocator& a, Buf& b, cudaStream_t s) {
 
 using namespace tc;
 
-namespace {
-
+namespace tc {
 int bits_for(int64_t n) {
   int b = 1;
   while (b < 31 && (1ll << b) < n) ++b;
   return b;
 }
+}  // namespace tc
 
-// Page-locked 64-byte landing slots for the small device-to-host results of a graph (its count, the number listed).
-// Pinning memory is a slow driver call (and freeing it waits for the device), too slow to do per graph, so slots
-// are carved from 64 KB page-locked blocks that live for the process and are reused through a free list.  Every
+namespace {
+
+// Page-locked landing slots (kHostSlotBytes each) for the small device-to-host results of a graph: its count, the
+// number listed, and the sizes a compact build reads back at its end.  Pinning memory is a slow driver call (and
+// freeing it waits for the device), too slow to do per graph, so slots are carved from 64 KB page-locked blocks that
+// live for the process and are reused through a free list.  Every
 // copy into a slot is waited for before the call that made it returns, so a released slot is idle.
 std::mutex g_slot_mu;
 std::vector<uint64_t*> g_free_slots;
 
+}  // namespace
+
+namespace tc {
 uint64_t* slot_acquire() {
   std::lock_guard<std::mutex> lk(g_slot_mu);
   if (g_free_slots.empty()) {
-    constexpr int kSlotsPerBlock = 1024;
+    constexpr int kSlotsPerBlock = 256;
     char* blk = nullptr;
-    if (cudaMallocHost((void**)&blk, (size_t)64 * kSlotsPerBlock) != cudaSuccess) {
+    if (cudaMallocHost((void**)&blk, kHostSlotBytes * kSlotsPerBlock) != cudaSuccess) {
       (void)cudaGetLastError();
       return nullptr;
     }
-    for (int i = kSlotsPerBlock - 1; i >= 0; --i) g_free_slots.push_back(reinterpret_cast<uint64_t*>(blk + 64 * i));
+    for (int i = kSlotsPerBlock - 1; i >= 0; --i)
+      g_free_slots.push_back(reinterpret_cast<uint64_t*>(blk + kHostSlotBytes * i));
   }
   uint64_t* p = g_free_slots.back();
   g_free_slots.pop_back();
@@ -209,6 +229,9 @@ void slot_release(uint64_t* p) {
   std::lock_guard<std::mutex> lk(g_slot_mu);
   g_free_slots.push_back(p);
 }
+}  // namespace tc
+
+namespace {
 
 void release_all(tc_graph* g, cudaStream_t s) {
   buf_release(g->alloc, g->keys, s);
@@ -221,10 +244,19 @@ void release_all(tc_graph* g, cudaStream_t s) {
   buf_release(g->alloc, g->acc, s);
   buf_release(g->alloc, g->dq0, s);
   buf_release(g->alloc, g->dense, s);
+  buf_release(g->alloc, g->ingest, s);
+  buf_release(g->alloc, g->block, s);
   slot_release(g->host_total);
   g->host_total = nullptr;
 }
 
+}  // namespace
+
+namespace tc {
+void release_graph(tc_graph* g, cudaStream_t s) { release_all(g, s); }
+}  // namespace tc
+
+namespace tc {
 // The device address of the host array p[0, len) when all of it is page-locked memory mapped into the device's
 // address space (as cudaHostAlloc gives under unified addressing), else null.  Both ends are checked, so an array
 // that runs past a registered range is never read by the device.
@@ -240,6 +272,9 @@ const int32_t* mapped_for_device(const int32_t* p, int64_t len) {
   if (static_cast<const int32_t*>(b.devicePointer) != da + (len - 1)) return nullptr;
   return da;
 }
+}  // namespace tc
+
+namespace {
 
 // Host arrays streamed through a device staging buffer (`stage`, allocated here) in chunks.
 tc_status pack_staged(tc_graph* g, const int32_t* src, const int32_t* dst, int64_t num_edges, uint32_t* d_err,
@@ -280,8 +315,10 @@ TC_API tc_status tc_set_tuning(const tc_tuning* t) {
     set_error("tc_set_tuning: num_classes must be in 1..TC_TUNING_MAX_CLASSES");
     return TC_ERR_INVALID_ARG;
   }
-  if (t->isect_max_wedges_milli < 0 || t->bucket_max_pairs < 0) {
-    set_error("tc_set_tuning: isect_max_wedges_milli and bucket_max_pairs must be >= 0");
+  if (t->isect_max_wedges_milli < 0 || t->bucket_max_pairs < 0 || t->compact_max_pairs < 0 ||
+      t->stage_min_csr_bytes < 0) {
+    set_error("tc_set_tuning: isect_max_wedges_milli, bucket_max_pairs, compact_max_pairs and stage_min_csr_bytes "
+              "must be >= 0");
     return TC_ERR_INVALID_ARG;
   }
   for (int i = 0; i < t->num_classes; ++i) {
@@ -366,19 +403,35 @@ TC_API tc_status tc_load_edges(const int32_t* src, const int32_t* dst, int64_t n
   uint32_t h_err = 0;
   do {
     if ((st = buf_alloc(g->alloc, g->acc, 64, s))) break;
-    if ((st = buf_alloc(g->alloc, g->indeg, (size_t)(num_vertices > 0 ? num_vertices : 1) * 4, s))) break;
-    if ((st = cuda_status(cudaMemsetAsync(g->indeg.p, 0, (size_t)(num_vertices > 0 ? num_vertices : 1) * 4, s),
-                          "memset indeg")))
-      break;
     if (!(g->host_total = slot_acquire())) {
       set_error("tc_load_edges: pinned host allocation failed");
       st = TC_ERR_NO_MEMORY;
       break;
     }
-    if (num_edges == 0) break;
-    if ((st = buf_alloc(g->alloc, g->keys, (size_t)num_edges * 8, s))) break;
-    if ((st = buf_alloc(g->alloc, err, 16, s))) break;
-    if ((st = cuda_status(cudaMemsetAsync(err.p, 0, 4, s), "memset err"))) break;
+    const size_t n4 = (size_t)(num_vertices > 0 ? num_vertices : 1) * 4;
+    if (num_edges > 0 && num_vertices > 0 && num_edges <= compact_max_pairs() && use_buckets(num_edges)) {
+      // a graph that tc_build will build compactly: the error word, the counts and the keys in one block,
+      // cleared up to the keys with one call
+      Arena sizing;
+      sizing.take<uint32_t>(4);
+      sizing.view(n4);
+      const size_t clear = sizing.used;
+      sizing.view((size_t)num_edges * 8);
+      if ((st = buf_alloc(g->alloc, g->ingest, sizing.used, s))) break;
+      Arena ar{g->ingest.as<char>()};
+      err.p = ar.take<uint32_t>(4);
+      err.owned = false;
+      g->indeg = ar.view(n4);
+      g->keys = ar.view((size_t)num_edges * 8);
+      if ((st = cuda_status(cudaMemsetAsync(g->ingest.p, 0, clear, s), "memset counts"))) break;
+    } else {
+      if ((st = buf_alloc(g->alloc, g->indeg, n4, s))) break;
+      if ((st = cuda_status(cudaMemsetAsync(g->indeg.p, 0, n4, s), "memset indeg"))) break;
+      if (num_edges == 0) break;
+      if ((st = buf_alloc(g->alloc, g->keys, (size_t)num_edges * 8, s))) break;
+      if ((st = buf_alloc(g->alloc, err, 16, s))) break;
+      if ((st = cuda_status(cudaMemsetAsync(err.p, 0, 4, s), "memset err"))) break;
+    }
     if (flags == TC_PTR_DEVICE) {
       if ((st = pack_edges(g, src, dst, num_edges, 0, err.as<uint32_t>(), s))) break;
     } else {

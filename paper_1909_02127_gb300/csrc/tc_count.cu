@@ -9,7 +9,7 @@
 namespace tc {
 namespace {
 
-template <int MODE>
+template <int MODE, bool STAGED>
 __global__ void __launch_bounds__(kCountThreads, 2)
     k_count(CsrView g, unsigned long long* __restrict__ total, dev::Sink sk, uint32_t* __restrict__ cursors) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(kCountThreads, 2)
     for (int i = threadIdx.x; i < nhub; i += kCountThreads) sk.hub[i] = 0u;
     __syncthreads();
   }
-  unsigned long long acc = dev::count_graph<MODE>(g, sk, cursors, smem, ws, &s_idx);
+  unsigned long long acc = dev::count_graph<MODE, STAGED>(g, sk, cursors, smem, ws, &s_idx);
   acc = warp_sum(acc);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
@@ -43,6 +43,11 @@ __global__ void __launch_bounds__(kCountThreads, 2)
 
 }  // namespace
 
+bool use_staged_rows(const tc_graph* g) {
+  const int64_t t = stage_min_csr_bytes();
+  return t > 0 && 8 * (g->n + 1) + 4 * g->csr_entries >= t;
+}
+
 int count_grid(const tc_graph* g) {
   const int64_t want = g->nb + (g->nw + kWarpsPerCTA - 1) / kWarpsPerCTA + (g->nt + kCountThreads - 1) / kCountThreads;
   return (int)(want < 2 * num_sms() ? (want < 1 ? 1 : want) : 2 * num_sms());
@@ -50,23 +55,26 @@ int count_grid(const tc_graph* g) {
 
 tc_status launch_count(const tc_graph* g, uint64_t* d_total, uint64_t* d_per_vertex, uint32_t* d_cursors,
                        cudaStream_t s) {
-  TC_CUDA(cudaMemsetAsync(d_total, 0, sizeof(uint64_t), s));
+  const bool adjacent = reinterpret_cast<uint64_t*>(d_cursors) == d_total + 1;  // the graph's own count words
+  TC_CUDA(cudaMemsetAsync(d_total, 0, sizeof(uint64_t) + (adjacent ? 3 * sizeof(uint32_t) : 0), s));
   if (d_per_vertex && g->n > 0) TC_CUDA(cudaMemsetAsync(d_per_vertex, 0, (size_t)g->n * sizeof(uint64_t), s));
   if (g->nb + g->nw + g->nt == 0) return TC_OK;
-  TC_CUDA(cudaMemsetAsync(d_cursors, 0, 3 * sizeof(uint32_t), s));
+  if (!adjacent) TC_CUDA(cudaMemsetAsync(d_cursors, 0, 3 * sizeof(uint32_t), s));
   const int grid = count_grid(g);
   dev::Sink sk;
   if (d_per_vertex) {
     sk.pv = (unsigned long long*)d_per_vertex;
-    TC_CUDA(cudaFuncSetAttribute(k_count<dev::kModeVertex>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 dev::kVertexSmem));
-    k_count<dev::kModeVertex><<<grid, kCountThreads, dev::kVertexSmem, s>>>(g->view(), (unsigned long long*)d_total,
-                                                                            sk, d_cursors);
+    TC_TRY((smem_attribute_once<k_count<dev::kModeVertex, false>>(dev::kVertexSmem)));
+    k_count<dev::kModeVertex, false><<<grid, kCountThreads, dev::kVertexSmem, s>>>(
+        g->view(), (unsigned long long*)d_total, sk, d_cursors);
+  } else if (use_staged_rows(g)) {  // CSR beyond L2: long hop-2 rows staged through shared memory
+    TC_TRY((smem_attribute_once<k_count<dev::kModeCount, true>>(dev::kCountStagedSmem)));
+    k_count<dev::kModeCount, true><<<grid, kCountThreads, dev::kCountStagedSmem, s>>>(
+        g->view(), (unsigned long long*)d_total, sk, d_cursors);
   } else {
-    TC_CUDA(cudaFuncSetAttribute(k_count<dev::kModeCount>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 dev::kCountSmem));
-    k_count<dev::kModeCount><<<grid, kCountThreads, dev::kCountSmem, s>>>(g->view(), (unsigned long long*)d_total,
-                                                                          sk, d_cursors);
+    TC_TRY((smem_attribute_once<k_count<dev::kModeCount, false>>(dev::kCountSmem)));
+    k_count<dev::kModeCount, false><<<grid, kCountThreads, dev::kCountSmem, s>>>(
+        g->view(), (unsigned long long*)d_total, sk, d_cursors);
   }
   note_launch();
   TC_CUDA(cudaGetLastError());
@@ -198,7 +206,57 @@ __global__ void k_list_heavy(CsrView g, int64_t first, int64_t count, const uint
   }
 }
 
+// Per-graph sums of per-source triangle counts: the source of rank r is the original (union) vertex perm[r], which
+// belongs to the graph j with voff[j] <= perm[r] < voff[j + 1].  Lanes of a warp that land on the same graph add
+// once.
+__global__ void k_graph_sums(const uint32_t* __restrict__ cnt, const int32_t* __restrict__ perm, int64_t n,
+                             const int64_t* __restrict__ voff, int32_t k, unsigned long long* __restrict__ counts) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {  // warp-uniform trip count
+    const int64_t r = base + threadIdx.x;
+    const uint32_t c = r < n ? __ldg(&cnt[r]) : 0u;
+    int j = -1;
+    if (c) {
+      const int64_t x = __ldg(&perm[r]);
+      int a = 0, b = k;  // the last j with voff[j] <= x
+      while (b - a > 1) {
+        const int mid = (a + b) >> 1;
+        if (__ldg(&voff[mid]) <= x)
+          a = mid;
+        else
+          b = mid;
+      }
+      j = a;
+    }
+    // the lanes of one graph sum their counts (each below 2^31) in 16-bit halves, so no 32-bit sum can wrap;
+    // lanes without a count form the group j = -1 and add nothing
+    const unsigned peers = __match_any_sync(kFull, j);
+    const unsigned lo = __reduce_add_sync(peers, c & 0xffffu);
+    const unsigned hi = __reduce_add_sync(peers, c >> 16);
+    const unsigned long long sum = ((unsigned long long)hi << 16) + lo;
+    if (j >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1 && sum) atomicAdd(&counts[j], sum);
+  }
+}
+
 }  // namespace
+
+tc_status launch_graph_counts(const tc_graph* g, const int64_t* d_voff, int32_t k, uint64_t* d_counts,
+                              uint32_t* d_cnt, uint32_t* d_cursors, cudaStream_t s) {
+  if (g->n == 0 || g->nb + g->nw + g->nt == 0) return TC_OK;
+  TC_CUDA(cudaMemsetAsync(d_cnt, 0, (size_t)g->n * 4, s));
+  TC_CUDA(cudaMemsetAsync(d_cursors, 0, 3 * sizeof(uint32_t), s));
+  TC_TRY((smem_attribute_once<k_list<dev::kModeCount>>(dev::kCountSmem)));
+  dev::Sink none;
+  k_list<dev::kModeCount><<<count_grid(g), kCountThreads, dev::kCountSmem, s>>>(
+      g->view(), 0, g->n, none, d_cursors, d_cnt, nullptr, g->list.as<int32_t>(), nullptr);
+  note_launch();
+  TC_CUDA(cudaGetLastError());
+  k_graph_sums<<<grid_for(g->n, 256), 256, 0, s>>>(d_cnt, g->perm.as<int32_t>(), g->n, d_voff, k,
+                                                   (unsigned long long*)d_counts);
+  note_launch();
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
 
 tc_status launch_list(const tc_graph* g, int64_t first, int64_t count, int32_t* d_triples, int64_t capacity,
                       uint64_t* d_found, uint32_t* d_cursors, cudaStream_t s) {

@@ -265,6 +265,54 @@ __device__ __forceinline__ uint32_t long_row(const int4* __restrict__ col4, uint
   return hits;
 }
 
+// ---- long rows staged through shared memory by cp.async -------------------------------------------------------
+// Where the graph does not fit in L2, hop-2 rows come from DRAM, and a warp walking a long row with plain loads has
+// one window of loads in flight, then none while it tests them.  The staged walk keeps the next steps' quads in
+// flight instead, in a ring of shared memory filled by asynchronous copies, at no cost in registers.
+__device__ __forceinline__ void cp_async_quad(int4* smem_dst, const int4* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// One long row (quads [q0, q0 + nq)) walked by the calling warp 32 quads per step, with the quads of the next S - 1
+// steps in flight: step k's quads go to slot k mod S of `ring` (S x 32 quads of this warp's shared memory, lane l
+// using entry l of each slot).  Each lane copies and later reads only its own quads, so the only wait is for the
+// lane's own copy group; a slot is refilled one step after it was read and tested.  A lane whose quad lies past
+// the row copies nothing and tests the pad id.
+template <int MODE, int S, class C>
+__device__ __forceinline__ uint32_t long_row_staged(const int4* __restrict__ col4, uint32_t q0, uint32_t nq,
+                                                    const C& c, const Sink& sk, int32_t v, int32_t pad, int4* ring) {
+  const uint32_t lane = threadIdx.x & 31;
+  const int4* p = col4 + q0 + lane;
+  int4* slot = ring + lane;
+  const uint32_t steps = (nq + 31) >> 5;
+#pragma unroll
+  for (uint32_t k = 0; k + 1 < (uint32_t)S; ++k) {
+    if (32 * k + lane < nq) cp_async_quad(slot + 32 * k, p + 32 * k);
+    cp_async_commit();
+  }
+  uint32_t hits = 0;
+  for (uint32_t k = 0; k < steps; ++k) {
+    const uint32_t kn = k + S - 1;  // into slot (k - 1) mod S, read and tested at step k - 1
+    if (32 * kn + lane < nq) cp_async_quad(slot + 32 * (kn % S), p + 32 * kn);
+    cp_async_commit();
+    cp_async_wait<S - 1>();  // step k's copy has landed
+    const int4 q = 32 * k + lane < nq ? slot[32 * (k % S)] : make_int4(pad, pad, pad, pad);
+    hits += test_quad<MODE>(q, c, sk, v);
+  }
+  // every copy group left pending is empty (its step lies past the row)
+  if (MODE == kModeVertex) {
+    const uint32_t s = warp_sum(hits);
+    if (lane == 0 && s) vertex_add(sk, v, s);
+  }
+  return hits;
+}
+
 // Short rows in shared memory: row k covers quads [q0[k], q0[k] + P[k+1] - P[k]); P is strictly increasing.
 struct Rows {
   uint32_t* q0;
@@ -405,7 +453,8 @@ __device__ __forceinline__ uint32_t dense_list_walk(const Rows& r, int R, uint32
 }
 
 // Is v's row also stored as a dense bitmap?  Returns its first quad or -1 (always -1 in per-vertex mode, which
-// walks the id rows).
+// walks the id rows: expanding the set bits of each AND into per-vertex adds measured twice as slow, 15.8 vs 7 ms at
+// R-MAT 20).
 template <int MODE>
 __device__ __forceinline__ int32_t dense_row(const CsrView& g, int32_t v) {
   if (MODE == kModeVertex || g.dq0 == nullptr || v < g.base_w || v >= g.n) return -1;
@@ -447,10 +496,15 @@ __device__ __forceinline__ uint32_t mark_row(const int32_t* __restrict__ row, in
   return low;
 }
 
-// All second hops of source u for the calling warp, given its closing test.
+// Ring slots of the staged long-row walk: per warp in warp mode, and per warp of the CTA in block mode.
+constexpr int kWarpRingSlots = 4;
+constexpr int kBlockRingSlots = 2;
+
+// All second hops of source u for the calling warp, given its closing test.  ring: this warp's kWarpRingSlots x 32
+// quads for staged long rows, or null for plain loads.
 template <int MODE, class C>
 __device__ __forceinline__ uint32_t warp_hops(const CsrView& g, int64_t beg, int64_t len, const C& c, const Rows& r,
-                                              const Sink& sk) {
+                                              const Sink& sk, int4* ring = nullptr) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
   const int4* col4 = reinterpret_cast<const int4*>(g.col);
@@ -469,7 +523,10 @@ __device__ __forceinline__ uint32_t warp_hops(const CsrView& g, int64_t beg, int
       longs &= longs - 1;
       const uint32_t q0 = __shfl_sync(kFull, ro.q0, k), nq = __shfl_sync(kFull, ro.nq, k);
       const int32_t vk = MODE != kModeCount ? __shfl_sync(kFull, v, k) : 0;
-      hits += long_row<MODE>(col4, q0, nq, c, sk, vk, (int32_t)g.n);
+      if (ring)
+        hits += long_row_staged<MODE, kWarpRingSlots>(col4, q0, nq, c, sk, vk, (int32_t)g.n, ring);
+      else
+        hits += long_row<MODE>(col4, q0, nq, c, sk, vk, (int32_t)g.n);
     }
     const bool is_short = ro.nq > 0 && !is_long;
     const unsigned shorts = __ballot_sync(kFull, is_short);
@@ -531,7 +588,7 @@ __device__ __forceinline__ uint32_t warp_hops(const CsrView& g, int64_t beg, int
 // low-entry hash (all -1 on entry and on return).
 template <int MODE>
 __device__ __forceinline__ uint32_t warp_source(int32_t u, const CsrView& g, uint32_t* bm, int32_t* ltab,
-                                                const Rows& r, const Sink& sk_in) {
+                                                const Rows& r, const Sink& sk_in, int4* ring = nullptr) {
   const int lane = threadIdx.x & 31;
   Sink sk = sk_in;
   sk.u = u;
@@ -543,15 +600,15 @@ __device__ __forceinline__ uint32_t warp_source(int32_t u, const CsrView& g, uin
   constexpr uint32_t cap = (uint32_t)kWarpBitmapBits, lmask = (uint32_t)kWarpLowSlots - 1;
   uint32_t hits;
   if (nlow == 0) {
-    hits = warp_hops<MODE>(g, beg, len, Closing<kLowNone>{bm, g.base_w, row, 0, cap, 0}, r, sk);
+    hits = warp_hops<MODE>(g, beg, len, Closing<kLowNone>{bm, g.base_w, row, 0, cap, 0}, r, sk, ring);
   } else if (nlow <= (uint32_t)kWarpLowSlots / 2) {
     low_insert(row, (int)nlow, ltab, lmask, lane, 32);
     __syncwarp();
-    hits = warp_hops<MODE>(g, beg, len, Closing<kLowHash>{bm, g.base_w, ltab, (int32_t)lmask, cap, 0}, r, sk);
+    hits = warp_hops<MODE>(g, beg, len, Closing<kLowHash>{bm, g.base_w, ltab, (int32_t)lmask, cap, 0}, r, sk, ring);
     __syncwarp();
     for (int i = lane; i < kWarpLowSlots; i += 32) ltab[i] = -1;
   } else {
-    hits = warp_hops<MODE>(g, beg, len, Closing<kLowSearch>{bm, g.base_w, row, (int32_t)nlow, cap, 0}, r, sk);
+    hits = warp_hops<MODE>(g, beg, len, Closing<kLowSearch>{bm, g.base_w, row, (int32_t)nlow, cap, 0}, r, sk, ring);
   }
   __syncwarp();
   mark_row(row, len, g.n, g.base_w, bm, false, lane, 32);
@@ -576,7 +633,8 @@ struct BlockRows {
 
 template <int MODE, class C>
 __device__ __forceinline__ uint32_t block_hops(const CsrView& g, int64_t beg, int64_t len, const C& c,
-                                               const BlockRows& br, uint32_t* ws, const Sink& sk) {
+                                               const BlockRows& br, uint32_t* ws, const Sink& sk,
+                                               int4* ring = nullptr) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int4* col4 = reinterpret_cast<const int4*>(g.col);
   uint32_t hits = 0;
@@ -622,7 +680,12 @@ __device__ __forceinline__ uint32_t block_hops(const CsrView& g, int64_t beg, in
       if (lane == 0) k = atomicAdd(br.next, 1u);
       k = __shfl_sync(kFull, k, 0);
       if (k >= NL) break;
-      hits += long_row<MODE>(col4, br.lq0[k], br.lnq[k], c, sk, MODE != kModeCount ? br.lv[k] : 0, (int32_t)g.n);
+      if (ring)
+        hits += long_row_staged<MODE, kBlockRingSlots>(col4, br.lq0[k], br.lnq[k], c, sk,
+                                                       MODE != kModeCount ? br.lv[k] : 0, (int32_t)g.n, ring);
+      else
+        hits += long_row<MODE>(col4, br.lq0[k], br.lnq[k], c, sk, MODE != kModeCount ? br.lv[k] : 0,
+                               (int32_t)g.n);
     }
     // short rows: equal contiguous shares of the quad stream
     const uint32_t per = (Q + kWarpsPerCTA - 1) / kWarpsPerCTA;
@@ -646,7 +709,7 @@ __device__ __forceinline__ uint32_t block_hops(const CsrView& g, int64_t beg, in
 // br.ltab its low-entry hash (all -1 on entry and on return).
 template <int MODE>
 __device__ __forceinline__ uint32_t block_source(int32_t u, const CsrView& g, uint32_t* bm, const BlockRows& br,
-                                                 uint32_t* ws, const Sink& sk_in) {
+                                                 uint32_t* ws, const Sink& sk_in, int4* ring = nullptr) {
   const int tid = threadIdx.x, lane = tid & 31;
   Sink sk = sk_in;
   sk.u = u;
@@ -659,14 +722,17 @@ __device__ __forceinline__ uint32_t block_source(int32_t u, const CsrView& g, ui
   constexpr uint32_t cap = (uint32_t)kBlockBitmapBits, lmask = (uint32_t)kBlockLowSlots - 1;
   uint32_t hits;
   if (nlow == 0) {
-    hits = block_hops<MODE>(g, beg, len, Closing<kLowNone>{bm, g.base_b, row, 0, cap, g.dq_delta}, br, ws, sk);
+    hits = block_hops<MODE>(g, beg, len, Closing<kLowNone>{bm, g.base_b, row, 0, cap, g.dq_delta}, br, ws, sk,
+                            ring);
   } else if (nlow <= (uint32_t)kBlockLowSlots / 2) {
     low_insert(row, (int)nlow, br.ltab, lmask, tid, kCountThreads);
     __syncthreads();
-    hits = block_hops<MODE>(g, beg, len, Closing<kLowHash>{bm, g.base_b, br.ltab, (int32_t)lmask, cap, g.dq_delta}, br, ws, sk);
+    hits = block_hops<MODE>(g, beg, len, Closing<kLowHash>{bm, g.base_b, br.ltab, (int32_t)lmask, cap, g.dq_delta},
+                            br, ws, sk, ring);
     for (int i = tid; i < kBlockLowSlots; i += kCountThreads) br.ltab[i] = -1;  // block_hops ended with a barrier
   } else {
-    hits = block_hops<MODE>(g, beg, len, Closing<kLowSearch>{bm, g.base_b, row, (int32_t)nlow, cap, g.dq_delta}, br, ws, sk);
+    hits = block_hops<MODE>(g, beg, len, Closing<kLowSearch>{bm, g.base_b, row, (int32_t)nlow, cap, g.dq_delta},
+                            br, ws, sk, ring);
   }
   mark_row(row, len, g.n, g.base_b, bm, false, tid, kCountThreads);
   if (MODE == kModeVertex) {
@@ -756,6 +822,16 @@ constexpr int kBlockRowWords = 3 * kBlockRows + 2 * kBlockRows + (kBlockRows + 1
 // (long, short, counter, dense)
 constexpr int kBlockSmem = (kBlockBitmapWords + kBlockRowWords + kBlockLowSlots) * 4;
 constexpr int kCountSmem = kBlockSmem > kWarpSmem ? kBlockSmem : kWarpSmem;
+// Staged counting (count mode only): a kWarpRingSlots-slot ring after each warp's region in warp mode, and a
+// kBlockRingSlots-slot ring per warp after the block-mode layout.  Two CTAs per SM still fit.
+constexpr int kWarpRingBytes = kWarpRingSlots * 32 * 16;
+constexpr int kBlockRingBytes = kBlockRingSlots * 32 * 16;
+constexpr int kWarpStagedSmem = kWarpsPerCTA * (kWarpRegionWords * 4 + kWarpRingBytes);
+constexpr int kBlockRingOffset = (kBlockSmem + 15) & ~15;  // 16-byte aligned for the copies
+constexpr int kBlockStagedSmem = kBlockRingOffset + kWarpsPerCTA * kBlockRingBytes;
+constexpr int kCountStagedSmem = kBlockStagedSmem > kWarpStagedSmem ? kBlockStagedSmem : kWarpStagedSmem;
+// two CTAs per SM: dynamic + static (272 bytes in k_count) + the 1 KB the runtime reserves per CTA, within 228 KB
+static_assert(2 * (kCountStagedSmem + 512 + 1024) <= 228 * 1024, "staged counting must keep two CTAs per SM");
 constexpr int kVertexSmem = kCountSmem + kHubRanks * 4;  // kModeVertex: the hub counters follow
 // two CTAs per SM: dynamic + static (< 1 KB) + the 1 KB the runtime reserves per CTA, within 228 KB
 static_assert(2 * (kVertexSmem + 2048) <= 228 * 1024, "vertex-mode counting must keep two CTAs per SM");
@@ -795,14 +871,18 @@ __device__ __forceinline__ void zero_words(uint32_t* p, int nwords, int t, int s
 
 // Count the triangles of one graph: block-bin sources first (one CTA each), then warp-bin sources, then thread-bin
 // sources (one lane each).  cursors[0..2]: zeroed work counters of this graph.  Returns this thread's count.
-template <int MODE>
+template <int MODE, bool STAGED = false>
 __device__ __forceinline__ unsigned long long count_graph(const CsrView& g, const Sink& sk,
                                                           uint32_t* cursors, uint32_t* smem, uint32_t* ws,
                                                           int* s_idx) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   unsigned long long acc = 0;
+  // staged layout: warp regions are kWarpRegionWords + the ring apart; block-mode rings follow the block layout
+  constexpr int kRegionStride = STAGED ? kWarpRegionWords + kWarpRingBytes / 4 : kWarpRegionWords;
   if (g.nb > 0) {
     const BlockRows br = block_rows(smem);
+    int4* bring =
+        STAGED ? reinterpret_cast<int4*>(smem + kBlockRingOffset / 4) + warp * (kBlockRingSlots * 32) : nullptr;
     zero_words(smem, kBlockBitmapWords, tid, kCountThreads);
     for (int i = tid; i < kBlockLowSlots; i += kCountThreads) br.ltab[i] = -1;
     __syncthreads();
@@ -812,11 +892,12 @@ __device__ __forceinline__ unsigned long long count_graph(const CsrView& g, cons
       const int idx = *s_idx;
       __syncthreads();
       if (idx >= g.nb) break;
-      acc += block_source<MODE>(g.list[idx], g, smem, br, ws, sk);
+      acc += block_source<MODE>(g.list[idx], g, smem, br, ws, sk, bring);
     }
   }
   if (g.nw > 0) {
-    uint32_t* region = smem + warp * kWarpRegionWords;
+    uint32_t* region = smem + warp * kRegionStride;
+    int4* wring = STAGED ? reinterpret_cast<int4*>(region + kWarpRegionWords) : nullptr;
     const Rows r = warp_rows(region);
     int32_t* ltab = warp_low(region);
     zero_words(region, kWarpBitmapWords, lane, 32);
@@ -830,7 +911,7 @@ __device__ __forceinline__ unsigned long long count_graph(const CsrView& g, cons
       idx = __shfl_sync(kFull, idx, 0);
       if (idx >= g.nw) break;
       const int e = min(idx + kChunk, g.nw);
-      for (int k = idx; k < e; ++k) acc += warp_source<MODE>(wlist[k], g, region, ltab, r, sk);
+      for (int k = idx; k < e; ++k) acc += warp_source<MODE>(wlist[k], g, region, ltab, r, sk, wring);
     }
   }
   if (g.nt > 0) {  // thread bin: 32 sources per warp, one per lane

@@ -4,11 +4,15 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 
 #include "tc.h"
 
 namespace tc {
+
+// Bytes of a graph's page-locked landing slot (see tc_graph::host_total).
+constexpr size_t kHostSlotBytes = 256;
 
 // Streaming multiprocessors of the current device (queried once per device, cached).  Persistent grids are sized
 // in multiples of it.
@@ -44,13 +48,36 @@ struct Allocator {
   void free(void* p, cudaStream_t s) const;
 };
 
-// A buffer owned by the code that allocated it (freed in stream order by release()).
+// A buffer owned by the code that allocated it (freed in stream order by buf_release()), or a view into another
+// buffer (owned = false: buf_release forgets it, and its owner frees the memory).
 struct Buf {
   void* p = nullptr;
   size_t bytes = 0;
+  bool owned = true;
   template <class T>
   T* as() const {
     return static_cast<T*>(p);
+  }
+};
+
+// Pieces of one region of device memory, handed out in order at 256-byte boundaries with no allocation call.  With
+// base null it only adds up the sizes asked for, so one layout function can first size the region and then carve
+// it.
+struct Arena {
+  char* base = nullptr;
+  size_t used = 0;
+  template <class T>
+  T* take(size_t count) {
+    const size_t off = (used + 255) & ~size_t(255);
+    used = off + count * sizeof(T);
+    return base ? reinterpret_cast<T*>(base + off) : nullptr;
+  }
+  Buf view(size_t bytes) {
+    Buf b;
+    b.p = take<char>(bytes);
+    b.bytes = bytes;
+    b.owned = false;
+    return b;
   }
 };
 
@@ -72,6 +99,7 @@ constexpr int kLongQuads = 16;                     // rows of >= 16 quads (64 id
 // The warp/block split of sources (w(u) above the threshold -> a whole CTA) comes from the tuning table.
 int64_t block_min_work_for(int64_t m);
 int64_t batch_warp_max_edges();
+int64_t stage_min_csr_bytes();
 
 // Per-graph view used by the counting kernels.  Vertices are relabelled by rank in the (input-pair count, id)
 // order, so every oriented edge goes from a lower to a higher id and rows hold ascending ids.  Rows start on
@@ -107,14 +135,34 @@ constexpr int kTinyMaxDegree = 8;    // thread-bin sources have at most this man
 // LSD radix sort of uint64 keys on bits [bit_lo, bit_hi), stable.  keys/alt: n elements each; the sorted result
 // is in *result (either keys or alt).
 tc_status radix_sort_u64(const Allocator& a, uint64_t* keys, uint64_t* alt, int64_t n, int bit_lo, int bit_hi,
-                         uint64_t** result, cudaStream_t s);
-// Exclusive scan of n int32 values into n+1 int64 values (out[n] = total).
-tc_status exclusive_scan_i32_to_i64(const Allocator& a, const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
+                         uint64_t** result, cudaStream_t s, void* tmp = nullptr);
+// Exclusive scan of n int32 values into n+1 int64 values (out[n] = total).  tmp: device scratch of
+// scan_temp_bytes(n) bytes, or null to allocate it through `a`.
+tc_status exclusive_scan_i32_to_i64(const Allocator& a, const int32_t* in, int64_t* out, int64_t n, cudaStream_t s,
+                                    void* tmp = nullptr);
 // Exclusive scan of n uint32 values in place; *total (device, may be null) receives the sum.
-tc_status exclusive_scan_u32(const Allocator& a, uint32_t* data, int64_t n, cudaStream_t s);
+tc_status exclusive_scan_u32(const Allocator& a, uint32_t* data, int64_t n, cudaStream_t s, void* tmp = nullptr);
+// Scratch bytes of a scan of n elements (partial sums of every level; 8-byte elements, enough for both scans).
+size_t scan_temp_bytes(int64_t n);
+// Scratch bytes of radix_sort_u64 over n keys (tile histograms and their scan).
+size_t radix_temp_bytes(int64_t n);
 
 // max_blocks < 0: 16 CTAs per SM of the current device.
 int grid_for(int64_t items, int threads, int max_blocks = -1);
+
+// cudaFuncSetAttribute(kernel, MaxDynamicSharedMemorySize, bytes) once per device: the attribute stays set, and a
+// build of a small graph should not pay a host call for it every time.
+template <auto Kernel>
+tc_status smem_attribute_once(int bytes) {
+  static std::atomic<int> done[64] = {};
+  int dev = 0;
+  TC_CUDA(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 64 && done[dev].load(std::memory_order_acquire) >= bytes) return TC_OK;
+  TC_CUDA(cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  if (dev >= 0 && dev < 64) done[dev].store(bytes, std::memory_order_release);
+  return TC_OK;
+}
+
 
 }  // namespace tc
 
@@ -130,6 +178,8 @@ struct tc_graph {
   int key_bits = 1;          // B: bits per vertex id in packed keys
   tc::Buf keys;              // packed (lo << B) | hi keys, until tc_build
   tc::Buf indeg;             // int32[n]: input pairs at each vertex (self-loops excluded), until tc_build
+  tc::Buf ingest;            // small graphs: one block holding keys and indeg (then views), until tc_build
+  tc::Buf block;             // compact builds: one block holding off, col, perm, list, tlist, dq0, dense (views)
   bool built = false;
   // built state
   int64_t m = 0;
@@ -149,7 +199,7 @@ struct tc_graph {
   tc::Buf dense;             // int4[dense_quads]: dense row bitmaps
   int64_t dense_rows = 0, dense_quads = 0;       // rows stored dense; quads of storage
   int64_t dense_wedges = 0, dense_visits = 0;    // 2-paths through dense rows; quads read for them per count
-  uint64_t* host_total = nullptr;  // pinned 8-byte landing slot
+  uint64_t* host_total = nullptr;  // pinned landing slot of kHostSlotBytes: [0, 8) results, [8, ...) build sizes
   // The bitmap windows start at a multiple of 128 ids at or above n - (bitmap bits), so they end at id n.
   static int64_t window_base(int64_t n, int64_t bits) { return n > bits ? ((n - bits + 127) & ~int64_t(127)) : 0; }
   tc::CsrView view() const {
@@ -174,10 +224,26 @@ struct tc_graph {
 };
 
 namespace tc {
+// tc_capi.cu
+int bits_for(int64_t n);                                  // bits per vertex id in packed keys
+const int32_t* mapped_for_device(const int32_t* p, int64_t len);  // device address of mapped host memory, or null
+uint64_t* slot_acquire();                                 // a page-locked landing slot (kHostSlotBytes)
+void slot_release(uint64_t* p);
+void release_graph(tc_graph* g, cudaStream_t s);           // every buffer of g, in stream order
+// tc_many.cu: k graphs counted as their disjoint union (arrays device-readable, or host arrays to copy where
+// stage[j] != 0); counts: k host uint64.  Blocks until the counts are valid.
+tc_status count_many(const int32_t* const* srcs, const int32_t* const* dsts, const int64_t* num_edges,
+                     const int64_t* num_vertices, const uint8_t* stage, int32_t k, uint64_t* counts,
+                     const tc_allocator* user_alloc, cudaStream_t s);
 // tc_build.cu
 tc_status pack_edges(tc_graph* g, const int32_t* src, const int32_t* dst, int64_t len, int64_t offset,
                      uint32_t* d_err, cudaStream_t s);
 tc_status build_graph(tc_graph* g, cudaStream_t s);
+// The disjoint union of k graphs into g's keys and counts (g->n and g->num_pairs are the union's sizes): pairs
+// [eoff[j], eoff[j+1]) come from d_srcs[j], d_dsts[j] (device-readable) with ids in [0, voff[j+1] - voff[j]),
+// offset by voff[j].  Out-of-range ids set *d_err.  All arrays device-resident.
+tc_status pack_edges_many(tc_graph* g, const int32_t* const* d_srcs, const int32_t* const* d_dsts,
+                          const int64_t* d_eoff, const int64_t* d_voff, int32_t k, uint32_t* d_err, cudaStream_t s);
 // by_id[perm[r]] = by_rank[r] for the n vertices (device arrays)
 tc_status unpermute_counts(const tc_graph* g, const uint64_t* by_rank, uint64_t* by_id, cudaStream_t s);
 // tc_count.cu
@@ -185,6 +251,14 @@ tc_status unpermute_counts(const tc_graph* g, const uint64_t* by_rank, uint64_t*
 tc_status launch_count(const tc_graph* g, uint64_t* d_total, uint64_t* d_per_vertex, uint32_t* d_cursors,
                        cudaStream_t s);
 int count_grid(const tc_graph* g);
+// Whether tc_count stages long hop-2 rows through shared memory for this graph: its CSR (offsets and columns) is
+// at least the tuning table's stage_min_csr_bytes (0: never).
+bool use_staged_rows(const tc_graph* g);
+// Per-graph counts of a disjoint union: each source's triangles (the counting kernel's closing tests) are added to
+// d_counts[j] of the graph j holding it, j found from the union's vertex offsets d_voff (k + 1 entries).
+// d_counts: k zeroed uint64; d_cursors: three scratch words; d_cnt: n uint32 of scratch.
+tc_status launch_graph_counts(const tc_graph* g, const int64_t* d_voff, int32_t k, uint64_t* d_counts,
+                              uint32_t* d_cnt, uint32_t* d_cursors, cudaStream_t s);
 // Lists into d_triples (capacity triples) the triangles whose first vertex has rank in [first, first + count);
 // *d_found receives how many there are (also past capacity).  d_cursors: four scratch words.
 tc_status launch_list(const tc_graph* g, int64_t first, int64_t count, int32_t* d_triples, int64_t capacity,

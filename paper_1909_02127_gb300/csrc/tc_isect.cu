@@ -140,7 +140,7 @@ tc_status launch_count_isect(const tc_graph* g, uint64_t* d_total, uint32_t* d_c
   TC_CUDA(cudaMemsetAsync(d_cursor, 0, sizeof(uint32_t), s));
   const int64_t want = (g->nb + g->nw + g->nt + kIsChunk * kIsWarps - 1) / (kIsChunk * kIsWarps);
   const int grid = (int)(want < 2 * num_sms() ? (want < 1 ? 1 : want) : 2 * num_sms());
-  TC_CUDA(cudaFuncSetAttribute(k_count_isect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIsSmem));
+  TC_TRY(smem_attribute_once<k_count_isect>((int)kIsSmem));
   k_count_isect<<<grid, kIsThreads, kIsSmem, s>>>(g->view(), (unsigned long long*)d_total, d_cursor);
   note_launch();
   TC_CUDA(cudaGetLastError());

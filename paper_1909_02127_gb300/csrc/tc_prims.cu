@@ -84,8 +84,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const Tin* in, Tout*
   if (total && blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1) *total = run;
 }
 
+// tmp: scratch for the partial sums of this level and the levels below (scan_temp_bytes), or null to allocate it.
 template <class Tin, class Tout>
-tc_status scan_rec(const Allocator& a, const Tin* in, Tout* out, int64_t n, Tout* total, cudaStream_t s) {
+tc_status scan_rec(const Allocator& a, const Tin* in, Tout* out, int64_t n, Tout* total, cudaStream_t s,
+                   void* tmp) {
   if (n <= 0) {
     if (total) TC_CUDA(cudaMemsetAsync(total, 0, sizeof(Tout), s));
     return TC_OK;
@@ -97,10 +99,16 @@ tc_status scan_rec(const Allocator& a, const Tin* in, Tout* out, int64_t n, Tout
     return TC_OK;
   }
   Buf part;
-  TC_TRY(buf_alloc(a, part, (size_t)tiles * sizeof(Tout), s));
+  if (tmp) {
+    part.p = tmp;
+    part.owned = false;
+  } else {
+    TC_TRY(buf_alloc(a, part, (size_t)tiles * sizeof(Tout), s));
+  }
+  void* below = tmp ? static_cast<char*>(tmp) + (((size_t)tiles * 8 + 255) & ~size_t(255)) : nullptr;
   k_scan_reduce<Tin, Tout><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, part.as<Tout>()); note_launch();
   tc_status st = cuda_status(cudaGetLastError(), "k_scan_reduce");
-  if (st == TC_OK) st = scan_rec<Tout, Tout>(a, part.as<Tout>(), part.as<Tout>(), tiles, nullptr, s);
+  if (st == TC_OK) st = scan_rec<Tout, Tout>(a, part.as<Tout>(), part.as<Tout>(), tiles, nullptr, s, below);
   if (st == TC_OK) {
     k_scan_down<Tin, Tout><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, part.as<Tout>(), total); note_launch();
     st = cuda_status(cudaGetLastError(), "k_scan_down");
@@ -204,16 +212,28 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t* __res
 }  // namespace
 
 tc_status exclusive_scan_i32_to_i64(const Allocator& a, const int32_t* in, int64_t* out, int64_t n,
-                                    cudaStream_t s) {
-  return scan_rec<int32_t, int64_t>(a, in, out, n, out + n, s);
+                                    cudaStream_t s, void* tmp) {
+  return scan_rec<int32_t, int64_t>(a, in, out, n, out + n, s, tmp);
 }
 
-tc_status exclusive_scan_u32(const Allocator& a, uint32_t* data, int64_t n, cudaStream_t s) {
-  return scan_rec<uint32_t, uint32_t>(a, data, data, n, nullptr, s);
+tc_status exclusive_scan_u32(const Allocator& a, uint32_t* data, int64_t n, cudaStream_t s, void* tmp) {
+  return scan_rec<uint32_t, uint32_t>(a, data, data, n, nullptr, s, tmp);
+}
+
+size_t scan_temp_bytes(int64_t n) {
+  size_t bytes = 0;
+  for (int64_t tiles = (n + kScanTile - 1) / kScanTile; tiles > 1; tiles = (tiles + kScanTile - 1) / kScanTile)
+    bytes += ((size_t)tiles * 8 + 255) & ~size_t(255);
+  return bytes;
+}
+
+size_t radix_temp_bytes(int64_t n) {
+  const int64_t ntiles = (n + kRsTile - 1) / kRsTile;
+  return (((size_t)ntiles * kRsBins * sizeof(uint32_t) + 255) & ~size_t(255)) + scan_temp_bytes(ntiles * kRsBins);
 }
 
 tc_status radix_sort_u64(const Allocator& a, uint64_t* keys, uint64_t* alt, int64_t n, int bit_lo, int bit_hi,
-                         uint64_t** result, cudaStream_t s) {
+                         uint64_t** result, cudaStream_t s, void* tmp) {
   *result = keys;
   if (n <= 1 || bit_hi <= bit_lo) return TC_OK;
   if (n >= (int64_t)0xffffffffLL) {
@@ -222,7 +242,14 @@ tc_status radix_sort_u64(const Allocator& a, uint64_t* keys, uint64_t* alt, int6
   }
   const int64_t ntiles = (n + kRsTile - 1) / kRsTile;
   Buf hist;
-  TC_TRY(buf_alloc(a, hist, (size_t)ntiles * kRsBins * sizeof(uint32_t), s));
+  void* scan_tmp = nullptr;
+  if (tmp) {
+    hist.p = tmp;
+    hist.owned = false;
+    scan_tmp = static_cast<char*>(tmp) + (((size_t)ntiles * kRsBins * sizeof(uint32_t) + 255) & ~size_t(255));
+  } else {
+    TC_TRY(buf_alloc(a, hist, (size_t)ntiles * kRsBins * sizeof(uint32_t), s));
+  }
   uint64_t* src = keys;
   uint64_t* dst = alt;
   tc_status st = TC_OK;
@@ -232,7 +259,7 @@ tc_status radix_sort_u64(const Allocator& a, uint64_t* keys, uint64_t* alt, int6
     k_rs_hist<<<(unsigned)ntiles, kRsThreads, 0, s>>>(src, n, shift, mask, hist.as<uint32_t>(), ntiles); note_launch();
     st = cuda_status(cudaGetLastError(), "k_rs_hist");
     if (st != TC_OK) break;
-    st = exclusive_scan_u32(a, hist.as<uint32_t>(), ntiles * kRsBins, s);
+    st = exclusive_scan_u32(a, hist.as<uint32_t>(), ntiles * kRsBins, s, scan_tmp);
     if (st != TC_OK) break;
     k_rs_scatter<<<(unsigned)ntiles, kRsThreads, 0, s>>>(src, dst, n, shift, mask, hist.as<uint32_t>(), ntiles); note_launch();
     st = cuda_status(cudaGetLastError(), "k_rs_scatter");

@@ -7,8 +7,13 @@
 // resident until counted.  One counting thread runs continuously: each time a launch finishes it takes every
 // graph that became ready meanwhile and counts them all in one persistent launch (tc_count_batch), so requests
 // that arrive while others are on the GPU join the next launch instead of waiting for a queue to drain.  With
-// batching off, it counts one graph per launch instead (the baseline).  Every wait is on a host condition
-// variable; nothing spins on the device.
+// batching off, it counts one graph per launch instead (the baseline).
+//
+// Pipeline batching (batching = 2) batches the whole path, not only the count: each build worker takes every
+// pending request that the memory budget admits (up to the compact build's pair limit) and ingests, builds and
+// counts them together as their disjoint union (tc_count_many), so the launch sequence of a build, which costs more
+// than the count for most requests, is paid once per batch.  Every wait is on a host condition variable; nothing
+// spins on the device.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -19,6 +24,7 @@
 #include <thread>
 #include <vector>
 
+#include "tc_build.cuh"
 #include "tc_internal.cuh"
 
 namespace {
@@ -32,6 +38,9 @@ struct Request {
   tc_request_result res{};
   const int32_t* src = nullptr;
   const int32_t* dst = nullptr;
+  const int32_t* dsrc = nullptr;  // pipeline batching: device-readable arrays (mapped host memory), or the host ones
+  const int32_t* ddst = nullptr;
+  uint8_t stage = 0;              // pipeline batching: 1 if the arrays must be copied to the device
   int64_t m = 0;
   int64_t n = 0;
   int64_t bytes = 0;
@@ -136,6 +145,83 @@ void builder_loop(tc_server* s) {
   cudaStreamDestroy(st);
 }
 
+// Pipeline batching: a build worker that counts batches of pending requests as one disjoint union.
+void batch_builder_loop(tc_server* s) {
+  cudaSetDevice(s->device);
+  cudaStream_t st = nullptr;
+  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  const int64_t pair_cap = std::max<int64_t>(1, tc::compact_max_pairs());
+  std::vector<Request*> batch;
+  std::vector<const int32_t*> srcs, dsts;
+  std::vector<int64_t> ne, nv;
+  std::vector<uint8_t> stage;
+  std::vector<uint64_t> counts;
+  while (true) {
+    batch.clear();
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv.wait(lk, [&] {
+        if (s->stop) return true;
+        if (s->pending.empty()) return false;
+        Request* h = s->pending.front();
+        const bool fits = s->held + h->bytes <= s->budget || s->inflight == 0;  // a lone request always runs
+        return fits && s->inflight < s->cfg.max_inflight;
+      });
+      if (s->stop) break;
+      int64_t pairs = 0;
+      while (!s->pending.empty() && (int64_t)batch.size() < s->cfg.max_batch) {
+        Request* h = s->pending.front();
+        const bool fits = s->held + h->bytes <= s->budget || s->inflight == 0;
+        if (!fits || s->inflight >= s->cfg.max_inflight) break;
+        if (!batch.empty() && pairs + h->m > pair_cap) break;
+        s->pending.pop_front();
+        s->held += h->bytes;
+        s->inflight += 1;
+        s->stats.admitted += 1;
+        s->stats.peak_held_bytes = std::max<int64_t>(s->stats.peak_held_bytes, s->held);
+        pairs += h->m;
+        batch.push_back(h);
+      }
+      s->stats.launches += 1;
+      s->stats.max_batch_seen = std::max<int64_t>(s->stats.max_batch_seen, (int64_t)batch.size());
+    }
+    const int64_t t_admit = now_ns();
+    const int32_t k = (int32_t)batch.size();
+    srcs.resize(k);
+    dsts.resize(k);
+    ne.resize(k);
+    nv.resize(k);
+    stage.resize(k);
+    counts.assign(k, 0);
+    for (int32_t i = 0; i < k; ++i) {
+      Request* r = batch[i];
+      r->res.t_admit_ns = t_admit;
+      srcs[i] = r->dsrc;
+      dsts[i] = r->ddst;
+      ne[i] = r->m;
+      nv[i] = r->n;
+      stage[i] = r->stage;
+    }
+    tc_status rc = tc::count_many(srcs.data(), dsts.data(), ne.data(), nv.data(), stage.data(), k, counts.data(),
+                              &s->alloc, st);
+    if (rc == TC_ERR_OUT_OF_RANGE && k > 1) {  // one bad request: every request of the batch on its own
+      for (int32_t i = 0; i < k; ++i) {
+        uint64_t c = 0;
+        const tc_status ri = tc::count_many(&srcs[i], &dsts[i], &ne[i], &nv[i], &stage[i], 1, &c, &s->alloc, st);
+        batch[i]->res.t_built_ns = now_ns();
+        finish(s, batch[i], ri, ri == TC_OK ? c : 0);
+      }
+      continue;
+    }
+    const int64_t t_built = now_ns();
+    for (int32_t i = 0; i < k; ++i) {
+      batch[i]->res.t_built_ns = t_built;
+      finish(s, batch[i], rc, rc == TC_OK ? counts[i] : 0);
+    }
+  }
+  cudaStreamDestroy(st);
+}
+
 void counter_loop(tc_server* s) {
   cudaSetDevice(s->device);
   std::vector<Request*> batch;
@@ -202,8 +288,8 @@ TC_API tc_status tc_server_create(const tc_server_config* cfg, tc_server** out) 
     if (cfg->hbm_reserve_bytes >= 0) c.hbm_reserve_bytes = cfg->hbm_reserve_bytes;
     c.hbm_budget_bytes = cfg->hbm_budget_bytes;
   }
-  if (c.build_workers > 64 || c.max_batch > (1 << 20)) {
-    set_error("tc_server_create: build_workers must be <= 64 and max_batch <= 2^20");
+  if (c.build_workers > 64 || c.max_batch > (1 << 20) || c.batching < 0 || c.batching > 2) {
+    set_error("tc_server_create: build_workers must be <= 64, max_batch <= 2^20 and batching 0, 1 or 2");
     return TC_ERR_INVALID_ARG;
   }
   tc_server* s = new (std::nothrow) tc_server();
@@ -243,7 +329,7 @@ TC_API tc_status tc_server_create(const tc_server_config* cfg, tc_server** out) 
     delete s;
     return st;
   }
-  for (int i = 0; i < c.build_workers; ++i) s->builders.emplace_back(builder_loop, s);
+  for (int i = 0; i < c.build_workers; ++i) s->builders.emplace_back(c.batching == 2 ? batch_builder_loop : builder_loop, s);
   s->counter = std::thread(counter_loop, s);
   *out = s;
   return TC_OK;
@@ -266,6 +352,18 @@ TC_API tc_status tc_server_submit(tc_server* s, const int32_t* src, const int32_
   r->n = num_vertices;
   r->bytes = estimate_bytes(num_edges, num_vertices);
   r->res.t_submit_ns = now_ns();
+  r->dsrc = src;
+  r->ddst = dst;
+  if (s->cfg.batching == 2 && num_edges > 0) {  // where the union's ingest reads this request's arrays from
+    const int32_t* ms = tc::mapped_for_device(src, num_edges);
+    const int32_t* md = ms ? tc::mapped_for_device(dst, num_edges) : nullptr;
+    if (ms && md) {
+      r->dsrc = ms;
+      r->ddst = md;
+    } else {
+      r->stage = 1;
+    }
+  }
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->stop) {
     delete r;

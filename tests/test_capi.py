@@ -90,6 +90,20 @@ def test_argument_errors_without_gpu(lib):
     assert lib.tc_batch_plan_create(None, 0, None, ctypes.byref(plan)) == tc.TC_ERR_INVALID_ARG
     assert lib.tc_batch_plan_run(None, None, None) == tc.TC_ERR_INVALID_ARG
     lib.tc_batch_plan_free(None)  # no-op
+    # many graphs: argument checks before any device call
+    cnt = (ctypes.c_uint64 * 1)()
+    assert lib.tc_count_many(None, None, None, None, -1, tc.TC_PTR_HOST, None, None) == tc.TC_ERR_INVALID_ARG
+    assert lib.tc_count_many(None, None, None, None, 1, tc.TC_PTR_HOST, cnt, None) == tc.TC_ERR_INVALID_ARG
+    assert lib.tc_count_many(None, None, None, None, 0, 3, None, None) == tc.TC_ERR_INVALID_ARG
+    assert lib.tc_count_many(None, None, None, None, 0, tc.TC_PTR_HOST, None, None) == tc.TC_OK
+    ptrs = (ctypes.c_void_p * 1)(None)
+    ne = (ctypes.c_int64 * 1)(3)
+    nv = (ctypes.c_int64 * 1)(5)
+    assert lib.tc_count_many(ptrs, ptrs, ne, nv, 1, tc.TC_PTR_HOST, cnt, None) == tc.TC_ERR_INVALID_ARG  # NULL arrays
+    nv0 = (ctypes.c_int64 * 1)(0)
+    arr = (ctypes.c_int32 * 3)(0, 1, 2)
+    aptr = (ctypes.c_void_p * 1)(ctypes.addressof(arr))
+    assert lib.tc_count_many(aptr, aptr, ne, nv0, 1, tc.TC_PTR_HOST, cnt, None) == tc.TC_ERR_OUT_OF_RANGE
 
 
 def test_missing_library_fails_loudly(tmp_path):

@@ -83,6 +83,40 @@ def test_random_small_graphs(tc, seed):
     np.testing.assert_array_equal(gt, t)
 
 
+STAGED_CASES = [("rmat16", lambda: (*graphgen.rmat(16, 16, 31).edges(), 1 << 16), None),
+                ("rmat17p_block", lambda: (*graphgen.rmat(17, 16, 32, n=120000, permute=True).edges(), 120000),
+                 [(1 << 62, 1 << 12)]),
+                ("k1500_block", lambda: graphs.complete(1500)[:3], [(1 << 62, 1 << 12)]),
+                ("k1500_warp", lambda: graphs.complete(1500)[:3], [(1 << 62, 1 << 40)]),
+                ("gnp_dense", lambda: (*graphgen.gnp(3000, 0.2, 33).edges(), 3000), None)]
+
+
+@pytest.mark.parametrize("name,make,classes", STAGED_CASES, ids=[c[0] for c in STAGED_CASES])
+def test_staged_long_rows_give_the_same_counts(tc, name, make, classes):
+    """Long hop-2 rows walked through the shared-memory ring filled by asynchronous copies (forced on for every
+    graph) give the oracle's count, in warp mode and in block mode, with rows of every length mod 32 quads."""
+    hs, hd, n = make()
+    T_ref = oracle.count(hs, hd, n)[0]
+    saved = tc.tc_get_tuning()
+    saved_stage, saved_isect = tc.tc_get_stage_min_csr_bytes(), tc.tc_get_isect_max_wedges_milli()
+    try:
+        if classes:
+            tc.tc_set_tuning(classes)
+        for stage in (1, 0, 1):
+            tc.tc_set_tuning(tc.tc_get_tuning(), stage_min_csr_bytes=stage, isect_max_wedges_milli=0)
+            g = tc.tc_load_edges(hs, hd, n)
+            try:
+                tc.tc_build(g)
+                info = tc.tc_graph_get_info(g)
+                assert tc.tc_count(g) == T_ref, f"stage_min_csr_bytes={stage}"
+            finally:
+                tc.tc_free(g)
+    finally:
+        tc.tc_set_tuning(saved, stage_min_csr_bytes=saved_stage, isect_max_wedges_milli=saved_isect)
+    if classes and classes[0][1] < (1 << 20):
+        assert info["bin_block"] > 0
+
+
 def test_hub_heavy_graph(tc):
     """One hub joined to everything plus a dense core: long N+(v) rows re-read by many sources."""
     rng = np.random.default_rng(7)
@@ -251,15 +285,15 @@ CSR_CASES = [("rmat13", lambda: (*graphgen.rmat(13, 12, 21).edges(), 1 << 13)),
              ("er_sparse", lambda: (*graphgen.er(30000, 20000, 22).edges(), 30000))]
 
 
-@pytest.mark.parametrize("path", ["buckets", "sort"])
-@pytest.mark.parametrize("name,make", CSR_CASES, ids=[c[0] for c in CSR_CASES])
-def test_csr_structure(tc, name, make, path):
-    """The oriented CSR: vertices relabelled by rank in the (count, id) order, each undirected edge stored once
-    from its lower to its higher rank, rows ascending, 16-byte aligned and padded with the id n.  Both ways of
-    grouping the pairs (per-source buckets, radix sort) give the same CSR."""
-    hs, hd, n = make()
-    saved = tc.tc_get_bucket_max_pairs()
-    tc.tc_set_tuning(tc.tc_get_tuning(), bucket_max_pairs=0 if path == "buckets" else 1)
+BUILD_PATHS = {"compact": dict(bucket_max_pairs=0, compact_max_pairs=1 << 40),   # buckets, one host sync
+               "buckets": dict(bucket_max_pairs=0, compact_max_pairs=0),         # buckets, sizes read as known
+               "sort": dict(bucket_max_pairs=1, compact_max_pairs=0)}            # radix sort of all pairs
+
+
+def _build_with(tc, path, hs, hd, n):
+    """(off, col, perm, info, T) of the graph built on the given path."""
+    saved = (tc.tc_get_bucket_max_pairs(), tc.tc_get_compact_max_pairs())
+    tc.tc_set_tuning(tc.tc_get_tuning(), **BUILD_PATHS[path])
     try:
         g = tc.tc_load_edges(hs, hd, n)
         try:
@@ -270,7 +304,19 @@ def test_csr_structure(tc, name, make, path):
         finally:
             tc.tc_free(g)
     finally:
-        tc.tc_set_tuning(tc.tc_get_tuning(), bucket_max_pairs=saved)
+        tc.tc_set_tuning(tc.tc_get_tuning(), bucket_max_pairs=saved[0], compact_max_pairs=saved[1])
+    return off, col, perm, info, T
+
+
+@pytest.mark.parametrize("path", list(BUILD_PATHS))
+@pytest.mark.parametrize("name,make", CSR_CASES, ids=[c[0] for c in CSR_CASES])
+def test_csr_structure(tc, name, make, path):
+    """The oriented CSR: vertices relabelled by rank in the (count, id) order, each undirected edge stored once
+    from its lower to its higher rank, rows ascending, 16-byte aligned and padded with the id n.  The three ways of
+    building it (per-source buckets with one host synchronisation or with sizes read as they become known, and a
+    radix sort of all pairs) give this same CSR."""
+    hs, hd, n = make()
+    off, col, perm, info, T = _build_with(tc, path, hs, hd, n)
     assert T == oracle.count(hs, hd, n)[0]
     lo = np.minimum(hs, hd)
     hi = np.maximum(hs, hd)
@@ -310,6 +356,28 @@ def test_csr_structure(tc, name, make, path):
     assert info["dense_quads"] == int(quads[targets][dense[targets]].sum())
     if name.startswith("rmat"):
         assert info["dense_rows"] > 0
+
+
+COMPACT_CASES = CSR_CASES + [("er4096", lambda: (*graphgen.config("er4096").edges(), 4096)),
+                             ("k40", lambda: graphs.complete(40)[:3]),
+                             ("wheel9", lambda: graphs.wheel(9)[:3]),
+                             ("one_edge", lambda: (np.array([3], np.int32), np.array([5], np.int32), 9)),
+                             ("self_loops_only", lambda: (np.arange(7, dtype=np.int32), np.arange(7, dtype=np.int32),
+                                                          7))]
+
+
+@pytest.mark.parametrize("name,make", COMPACT_CASES, ids=[c[0] for c in COMPACT_CASES])
+def test_compact_build_equals_synchronising_build(tc, name, make):
+    """The build with one host synchronisation (buffers at size bounds, sizes read back at the end) gives exactly
+    the graph of the build that reads each size as it becomes known: offsets, columns, visiting order, every
+    reported size and bin, and the count (also against the oracle)."""
+    hs, hd, n = make()
+    a = _build_with(tc, "compact", hs, hd, n)
+    b = _build_with(tc, "buckets", hs, hd, n)
+    for x, y in zip(a[:3], b[:3]):
+        np.testing.assert_array_equal(x, y)
+    assert a[3] == b[3]
+    assert a[4] == b[4] == oracle.count(hs, hd, n)[0]
 
 
 def test_host_and_device_inputs_and_allocators_agree(tc):

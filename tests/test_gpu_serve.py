@@ -61,7 +61,7 @@ def test_alone_equals_in_the_mix(tc, requests_and_solo):
     pool, edges, solo = requests_and_solo
     rng = np.random.default_rng(5)
     order = list(rng.permutation(len(pool))) + list(rng.integers(0, len(pool), size=64))  # with repeats
-    for batching in (True, False):
+    for batching in ("pipeline", True, False):
         got, stats = _run(tc, pool, edges, order, batching=batching, build_workers=4)
         for k, counts in got.items():
             assert all(c == solo[k] for c in counts), (k, counts, solo[k])
@@ -71,12 +71,38 @@ def test_alone_equals_in_the_mix(tc, requests_and_solo):
             assert stats["max_batch_seen"] == 1
 
 
-def test_tight_memory_budget(tc, requests_and_solo):
+def test_pipeline_batch_with_a_bad_request(tc, requests_and_solo):
+    """With the whole path batched, a request with an out-of-range id fails alone; its batch-mates still get their
+    counts."""
+    pool, edges, solo = requests_and_solo
+    order = list(range(min(40, len(pool))))
+    bad_k = order[len(order) // 2]
+    s, d = edges[bad_k]
+    d_bad = d.copy()
+    d_bad[0] = pool[bad_k].n  # one id past the range
+    statuses = {}
+    with tc.Server(batching="pipeline", build_workers=1) as srv:
+        ids = {}
+        for k in order:
+            ss, dd = (s, d_bad) if k == bad_k else edges[k]
+            ids[srv.submit(ss, dd, pool[k].n)] = k
+        deadline = time.time() + 120
+        while len(statuses) < len(ids) and time.time() < deadline:
+            for r in srv.poll(timeout_ms=100):
+                statuses[ids[r["id"]]] = (r["status"], r["triangles"])
+    assert statuses[bad_k][0] == tc.TC_ERR_OUT_OF_RANGE
+    for k in order:
+        if k != bad_k:
+            assert statuses[k] == (0, solo[k])
+
+
+@pytest.mark.parametrize("batching", [True, "pipeline"])
+def test_tight_memory_budget(tc, requests_and_solo, batching):
     pool, edges, solo = requests_and_solo
     budget = 48 << 20
     order = [k for k in range(len(pool)) if 32 * pool[k].num_edges + 48 * pool[k].n + (1 << 20) <= budget]
     assert len(order) > 10
-    got, stats = _run(tc, pool, edges, order, hbm_budget_bytes=budget, build_workers=8)
+    got, stats = _run(tc, pool, edges, order, hbm_budget_bytes=budget, build_workers=8, batching=batching)
     for k, counts in got.items():
         assert counts == [solo[k]]
     assert stats["peak_held_bytes"] <= budget
