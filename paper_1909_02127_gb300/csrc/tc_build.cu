@@ -1339,6 +1339,22 @@ int bits_of(int64_t x) {
   return b;
 }
 
+// The read-back sizes of a compact build into the graph.
+void apply_sizes(tc_graph* g, const CompactSizes& hs) {
+  g->m = (int64_t)hs.rc.m;
+  g->csr_entries = hs.entries;
+  g->dense_rows = (int64_t)hs.dense_rows;
+  g->dense_quads = hs.dquads;
+  g->wedges = (int64_t)hs.bc.wedges;
+  g->dense_wedges = g->dense_rows > 0 ? (int64_t)hs.bc.dense_wedges : 0;
+  g->dense_visits = g->dense_rows > 0 ? (int64_t)hs.bc.dense_visits : 0;
+  g->active = (int64_t)hs.bc.active;
+  g->nb = hs.bc.nb;
+  g->nw = hs.bc.nw;
+  g->nt = hs.bc.nt;
+  g->max_out_degree = hs.bc.max_out;
+}
+
 // Scratch of a compact build, all pieces of one allocation.
 struct CompactScratch {
   CompactSizes* sizes;
@@ -1489,18 +1505,7 @@ tc_status build_graph_compact(tc_graph* g, cudaStream_t s) {
       st = TC_ERR_INTERNAL;
       break;
     }
-    g->m = (int64_t)hs->rc.m;
-    g->csr_entries = hs->entries;
-    g->dense_rows = (int64_t)hs->dense_rows;
-    g->dense_quads = hs->dquads;
-    g->wedges = (int64_t)hs->bc.wedges;
-    g->dense_wedges = g->dense_rows > 0 ? (int64_t)hs->bc.dense_wedges : 0;
-    g->dense_visits = g->dense_rows > 0 ? (int64_t)hs->bc.dense_visits : 0;
-    g->active = (int64_t)hs->bc.active;
-    g->nb = hs->bc.nb;
-    g->nw = hs->bc.nw;
-    g->nt = hs->bc.nt;
-    g->max_out_degree = hs->bc.max_out;
+    apply_sizes(g, *hs);
   } while (0);
   buf_release(a, scratch, s);
   buf_release(a, g->keys, s);

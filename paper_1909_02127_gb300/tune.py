@@ -9,6 +9,12 @@ tc_count takes the intersection kernel that minimises the summed time relative t
 The binding installs the table through tc_set_tuning when the device matches.  Counts do not depend on the
 table; only speed does.
 
+It also times the build paths (the compact build with one host synchronisation, and the build that reads each size as
+it becomes known) on graphs of increasing size and keeps the largest size at which the compact build still wins
+(compact_max_pairs); and it times the count with long hop-2 rows
+staged through shared memory against plain loads on graphs too large for L2, keeping the smallest CSR size from which
+staging wins (stage_min_csr_bytes; 0 if it never does).
+
     python -m paper_1909_02127_gb300.tune [--quick]
 """
 from __future__ import annotations
@@ -39,6 +45,98 @@ def time_count(tc, g, d_total, reps):
     torch.cuda.synchronize()
     ms = sorted(a.elapsed_time(b) for a, b in ev)
     return ms[len(ms) // 2]
+
+
+def time_build(tc, ds, dd, n, reps):
+    """Median time (ms, CUDA events) of tc_load_edges + tc_build from device-resident edges."""
+    import torch
+    s = torch.cuda.current_stream()
+    out = []
+    for _ in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        g = tc.tc_load_edges(ds, dd, n, stream=s)
+        tc.tc_build(g, s)
+        e1.record(s)
+        torch.cuda.synchronize()
+        tc.tc_free(g)
+        out.append(e0.elapsed_time(e1))
+    out = sorted(out[1:])
+    return out[len(out) // 2]
+
+
+def largest_winning(rows, fast, slow):
+    """The largest pair count up to which the `fast` path is not slower than `slow` on every measured graph (0 if
+    it loses on the smallest)."""
+    best = 0
+    for r in sorted(rows, key=lambda r: r["pairs"]):
+        if r[fast] <= r[slow] * 1.01:
+            best = r["pairs"]
+        else:
+            break
+    return best
+
+
+def tune_build_paths(tc, graphgen, quick):
+    import torch
+    names = ["er4096", "rmat12", "rmat13", "rmat16", "rmat18", "rmat20"] + ([] if quick else ["rmat21", "rmat22"])
+    rows = []
+    base = tc.tc_get_compact_max_pairs()
+    try:
+        for name in names:
+            spec = graphgen.config(name)
+            ds, dd = spec.edges(device="cuda")
+            row = {"graph": name, "pairs": spec.num_edges, "n": spec.n}
+            for path, cmp in (("compact_ms", 1 << 40), ("sync_ms", 0)):
+                tc.tc_set_tuning(tc.tc_get_tuning(), compact_max_pairs=cmp)
+                row[path] = round(time_build(tc, ds, dd, spec.n, 3 if quick else 7), 4)
+            rows.append(row)
+            print(row, flush=True)
+            del ds, dd
+            torch.cuda.empty_cache()
+    finally:
+        tc.tc_set_tuning(tc.tc_get_tuning(), compact_max_pairs=base)
+    compact = largest_winning(rows, "compact_ms", "sync_ms")
+    if compact and compact == max(r["pairs"] for r in rows):
+        compact = 1 << 25  # won on every graph measured: keep the default bound
+    return rows, compact
+
+
+def tune_staging(tc, graphgen, quick):
+    import torch
+    names = ["rmat22", "rmat24"] + ([] if quick else ["rmat26"])
+    rows = []
+    base = tc.tc_get_stage_min_csr_bytes()
+    d_total = torch.zeros(1, dtype=torch.int64, device="cuda")
+    try:
+        for name in names:
+            spec = graphgen.config(name)
+            ds, dd = spec.edges(device="cuda")
+            g = tc.tc_load_edges(ds, dd, spec.n)
+            try:
+                tc.tc_build(g)
+                del ds, dd
+                torch.cuda.empty_cache()
+                info = tc.tc_graph_get_info(g)
+                row = {"graph": name, "csr_bytes": 8 * (info["num_vertices"] + 1) + 4 * info["csr_entries"]}
+                for key, thr in (("plain_ms", 0), ("staged_ms", 1)):
+                    tc.tc_set_tuning(tc.tc_get_tuning(), stage_min_csr_bytes=thr)
+                    row[key] = round(time_count(tc, g, d_total, 3), 3)
+            finally:
+                tc.tc_free(g)
+            rows.append(row)
+            print(row, flush=True)
+            torch.cuda.empty_cache()
+    finally:
+        tc.tc_set_tuning(tc.tc_get_tuning(), stage_min_csr_bytes=base)
+    wins = [r for r in sorted(rows, key=lambda r: r["csr_bytes"]) if r["staged_ms"] < r["plain_ms"]]
+    if not wins:
+        return rows, 0
+    first = wins[0]
+    below = [r for r in rows if r["csr_bytes"] < first["csr_bytes"]]
+    # between the largest losing size and the smallest winning one (geometric midpoint)
+    thr = int(math.sqrt(max(r["csr_bytes"] for r in below) * first["csr_bytes"])) if below else first["csr_bytes"]
+    return rows, thr
 
 
 def main():
@@ -163,17 +261,24 @@ def main():
     cands = [0] + sorted({r["wedges_milli"] for r in method_rows})
     isect_ratio = min(cands, key=lambda t: (cost(t), t))
     print("isect_max_wedges_milli", isect_ratio, {t: round(cost(t), 3) for t in cands}, flush=True)
+    build_rows, compact_pairs = tune_build_paths(tc, graphgen, args.quick)
+    print("compact_max_pairs", compact_pairs, flush=True)
+    stage_rows, stage_bytes = tune_staging(tc, graphgen, args.quick)
+    print("stage_min_csr_bytes", stage_bytes, flush=True)
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     out = {"device": props.name, "sms": props.multi_processor_count, "cc": f"{props.major}.{props.minor}",
            "classes": classes, "batch_warp_max_edges": batch_warp, "batch_times_ms": batch_times,
            "isect_max_wedges_milli": isect_ratio, "method_measurements": method_rows,
-           "bucket_max_pairs": tc.tc_get_bucket_max_pairs(), "measurements": results}
+           "bucket_max_pairs": tc.tc_get_bucket_max_pairs(), "measurements": results,
+           "compact_max_pairs": compact_pairs, "build_measurements": build_rows,
+           "stage_min_csr_bytes": stage_bytes, "staging_measurements": stage_rows}
     with open(args.out, "w") as f:
         json.dump(out, f, indent=1)
     tc.tc_set_tuning([tuple(c) for c in classes], batch_warp_max_edges=batch_warp,
-                     isect_max_wedges_milli=isect_ratio)
-    print(json.dumps({"classes": classes, "batch_warp_max_edges": batch_warp,
-                      "isect_max_wedges_milli": isect_ratio}))
+                     isect_max_wedges_milli=isect_ratio, compact_max_pairs=compact_pairs,
+                     stage_min_csr_bytes=stage_bytes)
+    print(json.dumps({"classes": classes, "batch_warp_max_edges": batch_warp, "isect_max_wedges_milli": isect_ratio,
+                      "compact_max_pairs": compact_pairs, "stage_min_csr_bytes": stage_bytes}))
 
 
 if __name__ == "__main__":

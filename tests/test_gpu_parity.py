@@ -380,6 +380,50 @@ def test_compact_build_equals_synchronising_build(tc, name, make):
     assert a[4] == b[4] == oracle.count(hs, hd, n)[0]
 
 
+def _hub_and_clique(n, seed):
+    """A hub joined to every vertex, a 90-clique among the top ids, random pairs with repeats and self-loops."""
+    rng = np.random.default_rng(seed)
+    a, b = np.triu_indices(90, 1)
+    s = np.concatenate([np.zeros(n - 1, np.int64), n - 90 + a, rng.integers(0, n, 6000)])
+    d = np.concatenate([np.arange(1, n), n - 90 + b, rng.integers(0, n, 6000)])
+    return s.astype(np.int32), d.astype(np.int32), n
+
+
+TINY_CASES = [("er4096", lambda: (*graphgen.config("er4096").edges(), 4096)),
+              ("k200_dense_rows", lambda: graphs.complete(200)[:3]),
+              ("n8192_m65536", lambda: (*graphgen.er(8192, 65536, 91).edges(), 8192)),
+              ("rmat13_ef7", lambda: (*graphgen.rmat(13, 7, 92).edges(), 1 << 13)),
+              ("gnp_small_dense", lambda: (*graphgen.gnp(300, 0.6, 93).edges(), 300)),
+              ("hub_and_clique", lambda: _hub_and_clique(5000, 94)),
+              ("n1_self_loop", lambda: (np.array([0], np.int32), np.array([0], np.int32), 1)),
+              ("two_vertices", lambda: (np.array([0, 1, 1], np.int32), np.array([1, 0, 1], np.int32), 2)),
+              ("wheel50", lambda: graphs.wheel(50)[:3])]
+
+
+@pytest.mark.parametrize("name,make", TINY_CASES, ids=[c[0] for c in TINY_CASES])
+def test_small_graphs_every_build_path(tc, name, make):
+    """Small graphs at the edges of the compact build's bounds (n up to 8192, up to 65536 pairs, dense rows, a hub,
+    a clique, repeats, self-loops, one and two vertices): the compact build, the build that reads sizes as known and
+    the radix-sort build give the same graph, and its counts and per-vertex counts are the oracle's."""
+    hs, hd, n = make()
+    a = _build_with(tc, "compact", hs, hd, n)
+    for other in ("buckets", "sort"):
+        b = _build_with(tc, other, hs, hd, n)
+        for x, y in zip(a[:3], b[:3]):
+            np.testing.assert_array_equal(x, y)
+        assert a[3] == b[3] and a[4] == b[4]
+    T, _, t = oracle.count(hs, hd, n, per_vertex=True)
+    assert a[4] == T
+    g = tc.tc_load_edges(hs, hd, n)
+    try:
+        tc.tc_build(g)
+        T2, t2 = tc.tc_count_per_vertex(g)
+    finally:
+        tc.tc_free(g)
+    assert T2 == T
+    np.testing.assert_array_equal(t2, t)
+
+
 def test_host_and_device_inputs_and_allocators_agree(tc):
     spec = graphgen.rmat(14, 10, 31)
     hs, hd = spec.edges()
