@@ -96,19 +96,17 @@ def tune_build_paths(tc, graphgen, quick):
             torch.cuda.empty_cache()
     finally:
         tc.tc_set_tuning(tc.tc_get_tuning(), compact_max_pairs=base)
-    compact = largest_winning(rows, "compact_ms", "sync_ms")
-    if compact and compact == max(r["pairs"] for r in rows):
-        compact = 1 << 25  # won on every graph measured: keep the default bound
-    return rows, compact
+    return rows, largest_winning(rows, "compact_ms", "sync_ms")
 
 
 def tune_staging(tc, graphgen, quick):
     import torch
     names = ["rmat22", "rmat24"] + ([] if quick else ["rmat26"])
     rows = []
-    base = tc.tc_get_stage_min_csr_bytes()
+    base = (tc.tc_get_stage_min_csr_bytes(), tc.tc_get_isect_max_wedges_milli())
     d_total = torch.zeros(1, dtype=torch.int64, device="cuda")
     try:
+        tc.tc_set_tuning(tc.tc_get_tuning(), isect_max_wedges_milli=0)  # the fused kernel, whose loads are staged
         for name in names:
             spec = graphgen.config(name)
             ds, dd = spec.edges(device="cuda")
@@ -128,7 +126,7 @@ def tune_staging(tc, graphgen, quick):
             print(row, flush=True)
             torch.cuda.empty_cache()
     finally:
-        tc.tc_set_tuning(tc.tc_get_tuning(), stage_min_csr_bytes=base)
+        tc.tc_set_tuning(tc.tc_get_tuning(), stage_min_csr_bytes=base[0], isect_max_wedges_milli=base[1])
     wins = [r for r in sorted(rows, key=lambda r: r["csr_bytes"]) if r["staged_ms"] < r["plain_ms"]]
     if not wins:
         return rows, 0
@@ -261,6 +259,9 @@ def main():
     cands = [0] + sorted({r["wedges_milli"] for r in method_rows})
     isect_ratio = min(cands, key=lambda t: (cost(t), t))
     print("isect_max_wedges_milli", isect_ratio, {t: round(cost(t), 3) for t in cands}, flush=True)
+    # the table chosen so far is installed before the build and staging sweeps (the method sweep leaves the last
+    # kernel it timed selected)
+    tc.tc_set_tuning([tuple(c) for c in classes], batch_warp_max_edges=batch_warp, isect_max_wedges_milli=isect_ratio)
     build_rows, compact_pairs = tune_build_paths(tc, graphgen, args.quick)
     print("compact_max_pairs", compact_pairs, flush=True)
     stage_rows, stage_bytes = tune_staging(tc, graphgen, args.quick)
