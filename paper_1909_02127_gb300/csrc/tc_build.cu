@@ -45,6 +45,8 @@ static_assert(kPackItems == 4, "k_pack moves a thread's pairs as one int4 per ar
 constexpr int kPackSlots = 4096;
 constexpr int kPackProbe = 8;
 
+// The slot's claim counts the vertex's first occurrence in the tile (the flush adds it), so a first occurrence costs
+// one shared atomic (the claiming CAS) and a repeat one (the add).
 __device__ __forceinline__ void pack_count(int32_t* skey, int32_t* scnt, int32_t* indeg, int32_t x) {
   uint32_t s = ((uint32_t)x * 2654435761u) >> 20;  // 12 bits
   for (int p = 0; p < kPackProbe; ++p) {
@@ -55,10 +57,7 @@ __device__ __forceinline__ void pack_count(int32_t* skey, int32_t* scnt, int32_t
     }
     if (k < 0) {
       const int32_t prev = atomicCAS(&skey[s], -1, x);
-      if (prev == -1) {
-        atomicAdd(&scnt[s], 1);
-        return;
-      }
+      if (prev == -1) return;  // claimed: this occurrence is the slot's implicit first count
       if (prev == x) {
         atomicAdd(&scnt[s], 1);
         return;
@@ -141,7 +140,7 @@ __global__ void __launch_bounds__(kPackThreads) k_pack(const int32_t* __restrict
     for (int slot = threadIdx.x; slot < kPackSlots; slot += kPackThreads) {
       const int32_t k = skey[slot];
       if (k >= 0) {
-        atomicAdd(&indeg[k], scnt[slot]);
+        atomicAdd(&indeg[k], scnt[slot] + 1);  // + the claiming occurrence
         skey[slot] = -1;
         scnt[slot] = 0;
       }
@@ -208,7 +207,7 @@ __global__ void __launch_bounds__(kPackThreads) k_pack_many(ManyInput in, int64_
     for (int slot = threadIdx.x; slot < kPackSlots; slot += kPackThreads) {
       const int32_t key = skey[slot];
       if (key >= 0) {
-        atomicAdd(&indeg[key], scnt[slot]);
+        atomicAdd(&indeg[key], scnt[slot] + 1);  // + the claiming occurrence
         skey[slot] = -1;
         scnt[slot] = 0;
       }
@@ -398,17 +397,44 @@ struct RowCounters {
 // Each pair {a, b} goes to the bucket of its lower-ranked endpoint as the higher rank.  Bucket s has room for the
 // input-pair count of s (an upper bound on its size) starting at pstart[s]; its cursor cur[s] starts there and ends
 // one past its last pair (the order in a bucket is free).
+// Each pair is a chain of dependent accesses (its key, two rank lookups, the slot claim, the store), so a thread
+// takes four consecutive pairs and runs their chains side by side: four times the accesses in flight.
+constexpr int kBucketItems = 4;
+
 __global__ void k_bucket(const uint64_t* __restrict__ keys, int64_t npairs, int B, const int32_t* __restrict__ rank,
                          unsigned long long* __restrict__ cur, int32_t* __restrict__ tgt) {
   const uint64_t mask = (1ull << B) - 1ull;
   const uint64_t sentinel = (1ull << (2 * B)) - 1ull;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npairs;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t k = keys[i];
-    if (k == sentinel) continue;
-    const int32_t ra = rank[k >> B], rb = rank[k & mask];
-    const int32_t lo = ra < rb ? ra : rb, hi = ra < rb ? rb : ra;
-    tgt[atomicAdd(&cur[lo], 1ull)] = hi;
+  const bool vec = (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
+  for (int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * kBucketItems; i0 < npairs;
+       i0 += (int64_t)gridDim.x * blockDim.x * kBucketItems) {
+    uint64_t k[kBucketItems];
+    if (vec && i0 + kBucketItems <= npairs) {
+      const ulonglong2 x = *reinterpret_cast<const ulonglong2*>(keys + i0);
+      const ulonglong2 y = *reinterpret_cast<const ulonglong2*>(keys + i0 + 2);
+      k[0] = x.x;
+      k[1] = x.y;
+      k[2] = y.x;
+      k[3] = y.y;
+    } else {
+#pragma unroll
+      for (int j = 0; j < kBucketItems; ++j) k[j] = i0 + j < npairs ? keys[i0 + j] : sentinel;
+    }
+    int32_t ra[kBucketItems], rb[kBucketItems];
+#pragma unroll
+    for (int j = 0; j < kBucketItems; ++j) {
+      if (k[j] != sentinel) {
+        ra[j] = __ldg(&rank[k[j] >> B]);
+        rb[j] = __ldg(&rank[k[j] & mask]);
+      }
+    }
+    unsigned long long pos[kBucketItems];
+#pragma unroll
+    for (int j = 0; j < kBucketItems; ++j)
+      if (k[j] != sentinel) pos[j] = atomicAdd(&cur[ra[j] < rb[j] ? ra[j] : rb[j]], 1ull);
+#pragma unroll
+    for (int j = 0; j < kBucketItems; ++j)
+      if (k[j] != sentinel) tgt[pos[j]] = ra[j] < rb[j] ? rb[j] : ra[j];
   }
 }
 
@@ -769,8 +795,20 @@ __global__ void k_bins(const int64_t* __restrict__ off, const int32_t* __restric
       b = off[u];
     }
     RowWork w;
-    if (d <= 32)
-      for (int64_t j = b; j < b + d; ++j) w.add(rowinfo[col[j]]);
+    if (d <= 32) {  // the row as 16-byte quads (rows start on 16-byte boundaries), four row-info loads at a time
+      const int4* r4 = reinterpret_cast<const int4*>(col + b);
+      const int32_t nq = (d + 3) >> 2;
+      for (int32_t k = 0; k < nq; ++k) {
+        const int4 q = __ldg(&r4[k]);
+        const int2 zero = make_int2(0, 0);
+        const int2 i0 = q.x < n ? __ldg(&rowinfo[q.x]) : zero, i1 = q.y < n ? __ldg(&rowinfo[q.y]) : zero;
+        const int2 i2 = q.z < n ? __ldg(&rowinfo[q.z]) : zero, i3 = q.w < n ? __ldg(&rowinfo[q.w]) : zero;
+        w.add(i0);
+        w.add(i1);
+        w.add(i2);
+        w.add(i3);
+      }
+    }
     unsigned longs = __ballot_sync(kFull, d > 32);
     while (longs) {
       const int k = __ffs(longs) - 1;
@@ -1046,8 +1084,8 @@ tc_status bucket_csr(tc_graph* g, const int32_t* rank, const int32_t* rcount, Bu
                           "copy cursors")))
       break;
     if (M > 0) {
-      k_bucket<<<grid_for(M, 256), 256, 0, s>>>(g->keys.as<uint64_t>(), M, B, rank,
-                                                cur.as<unsigned long long>(), tgt.as<int32_t>());
+      k_bucket<<<grid_for((M + kBucketItems - 1) / kBucketItems, 256), 256, 0, s>>>(
+          g->keys.as<uint64_t>(), M, B, rank, cur.as<unsigned long long>(), tgt.as<int32_t>());
       if ((st = launched("k_bucket"))) break;
     }
     buf_release(a, g->keys, s);
@@ -1452,8 +1490,8 @@ tc_status build_graph_compact(tc_graph* g, cudaStream_t s) {
     if ((st = cuda_status(cudaMemcpyAsync(c.cur, c.pstart, (size_t)n * 8, cudaMemcpyDeviceToDevice, s),
                           "copy cursors")))
       break;
-    k_bucket<<<grid_for(M, 256), 256, 0, s>>>(g->keys.as<uint64_t>(), M, B, c.rank,
-                                              reinterpret_cast<unsigned long long*>(c.cur), c.tgt);
+    k_bucket<<<grid_for((M + kBucketItems - 1) / kBucketItems, 256), 256, 0, s>>>(
+        g->keys.as<uint64_t>(), M, B, c.rank, reinterpret_cast<unsigned long long*>(c.cur), c.tgt);
     if ((st = launched("k_bucket"))) break;
     RowCounters* rc = &ds->rc;
     k_rows_small<<<grid_for(n, 256), 256, 0, s>>>(c.pstart, c.cur, n, c.tgt, c.odeg, c.lists, rc);
