@@ -397,6 +397,11 @@ typedef struct tc_tuning {
                                                           (cp.async) for graphs whose CSR (8(n+1) + 4 csr_entries
                                                           bytes) is at least this large, i.e. read from DRAM rather
                                                           than L2.  0: never.  >= 0 */
+  int64_t tiny_max_pairs;                              /* tc_build of a graph with at most 16384 vertices and at most
+                                                          this many input pairs (and fewer than 2^18) on the bucketed
+                                                          path runs as one cooperative kernel launch, its steps
+                                                          separated by grid-wide barriers, instead of about 25
+                                                          launches.  0: never.  >= 0 */
 } tc_tuning;
 
 /* tc_set_tuning — replace the table (TC_ERR_INVALID_ARG if malformed).  Applies to graphs built afterwards. */

@@ -14,7 +14,7 @@ BUILD_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libtc.so")
 
 SOURCES = ["tc_capi.cu", "tc_prims.cu", "tc_build.cu", "tc_count.cu", "tc_batch.cu", "tc_noalloc.cu", "tc_serve.cu",
-           "tc_unfused.cu", "tc_isect.cu", "tc_many.cu"]
+           "tc_unfused.cu", "tc_isect.cu", "tc_many.cu", "tc_tiny.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden", "--expt-relaxed-constexpr",
               "-I", INCLUDE, "-I", CSRC] + ARCH

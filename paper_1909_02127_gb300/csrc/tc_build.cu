@@ -386,14 +386,6 @@ constexpr int kRowThreads = 256;         // block size of k_rows_warp
 constexpr int kBigThreads = 1024;        // other buckets: one block, bitmap (<= kBigBits ids) or bitonic sort
 constexpr int kBigBits = 1 << 20;        // block bitmap capacity (128 KB)
 
-struct RowCounters {
-  unsigned long long m;  // distinct edges
-  unsigned int nwarp;    // buckets for k_rows_warp
-  unsigned int nblock;   // buckets for k_rows_block
-  unsigned int err;      // a bucket broke the size bound (cannot happen for consistent counts)
-  unsigned int pad;
-};
-
 // Each pair {a, b} goes to the bucket of its lower-ranked endpoint as the higher rank.  Bucket s has room for the
 // input-pair count of s (an upper bound on its size) starting at pstart[s]; its cursor cur[s] starts there and ends
 // one past its last pair (the order in a bucket is free).
@@ -749,35 +741,11 @@ __global__ void k_rows_copy(const int64_t* __restrict__ pstart, const int32_t* _
 }
 
 // ---- work estimate and binning ----------------------------------------------------------------------------------
-struct BinCounters {
-  unsigned long long wedges;
-  unsigned long long active;
-  unsigned int nb;
-  unsigned int nw;
-  int max_out;
-  unsigned int nt;
-  unsigned long long dense_wedges;  // 2-paths through dense rows
-  unsigned long long dense_visits;  // quads of dense rows read per count
-};
 
 // w(u) = the hop-2 work of source u: the padded length of each id row of N+(u), and four ids' worth per quad of
 // each dense row (see k_dense_select); plus the true 2-path count.  Sources with d+(u) >= 2 and a 2-path go to
 // the block bin (w above the threshold) or the warp bin.  Rows of up to 32 entries are summed by their own lane,
 // longer ones by the whole warp.  rowinfo[v] = {d+(v), padded length or minus dense quads}.
-struct RowWork {
-  int64_t pad = 0, wtrue = 0, wdense = 0, qdense = 0;
-  __device__ __forceinline__ void add(int2 ri) {
-    wtrue += ri.x;
-    if (ri.y >= 0) {
-      pad += ri.y;
-    } else {
-      pad += -4 * (int64_t)ri.y;
-      wdense += ri.x;
-      qdense += -ri.y;
-    }
-  }
-};
-
 __global__ void k_bins(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
                        const int2* __restrict__ rowinfo, int64_t n, int64_t block_min_work,
                        int32_t* __restrict__ list, int32_t* __restrict__ tlist, BinCounters* __restrict__ bc) {
@@ -1147,6 +1115,7 @@ tc_status bucket_csr(tc_graph* g, const int32_t* rank, const int32_t* rcount, Bu
 }
 
 tc_status build_graph(tc_graph* g, cudaStream_t s) {
+  if (g->tiny || (use_buckets(g->num_pairs) && tiny_eligible(g->n, g->num_pairs))) return build_graph_tiny(g, s);
   if (g->n > 0 && g->num_pairs > 0 && g->num_pairs <= compact_max_pairs() && use_buckets(g->num_pairs))
     return build_graph_compact(g, s);
   return build_graph_pruned(g, -1, nullptr, s);
@@ -1357,19 +1326,6 @@ tc_status build_graph_pruned(tc_graph* g, int32_t peel_rounds, tc_prune_stats* p
 }  // namespace tc
 
 namespace tc {
-namespace {
-
-// What a compact build reads back once, at its end (it lands in the graph's pinned slot after the count word).
-struct CompactSizes {
-  RowCounters rc;
-  BinCounters bc;
-  int64_t entries;              // padded column entries: off[n]
-  int64_t dquads;               // quads of the dense rows
-  unsigned long long dense_rows;
-  int32_t maxdeg;               // (written by k_rank_keys; unused)
-  int32_t pad;
-};
-static_assert(sizeof(CompactSizes) + 8 <= kHostSlotBytes, "the compact build's sizes must fit the landing slot");
 
 int bits_of(int64_t x) {
   int b = 0;
@@ -1377,7 +1333,6 @@ int bits_of(int64_t x) {
   return b;
 }
 
-// The read-back sizes of a compact build into the graph.
 void apply_sizes(tc_graph* g, const CompactSizes& hs) {
   g->m = (int64_t)hs.rc.m;
   g->csr_entries = hs.entries;
@@ -1392,6 +1347,8 @@ void apply_sizes(tc_graph* g, const CompactSizes& hs) {
   g->nt = hs.bc.nt;
   g->max_out_degree = hs.bc.max_out;
 }
+
+namespace {
 
 // Scratch of a compact build, all pieces of one allocation.
 struct CompactScratch {
@@ -1424,8 +1381,8 @@ CompactScratch compact_scratch(Arena& ar, int64_t n, int64_t M, int64_t wn) {
   return c;
 }
 
-// The graph's arrays of a compact build as views into one block: off, col (at the column bound), perm, the source
-// lists, the dense-row index and store (at the dense bound).
+}  // namespace
+
 void csr_views(Arena& ar, tc_graph* g, int64_t n, int64_t bound_entries, int64_t wn, int64_t dense_quads) {
   g->off = ar.view((size_t)(n + 1) * 8);
   g->col = ar.view((size_t)(bound_entries + 4) * 4);
@@ -1435,8 +1392,6 @@ void csr_views(Arena& ar, tc_graph* g, int64_t n, int64_t bound_entries, int64_t
   g->dq0 = ar.view((size_t)(wn > 0 ? wn : 1) * 4);
   g->dense = ar.view((size_t)dense_quads * 16);
 }
-
-}  // namespace
 
 // tc_build for inputs of up to compact_max_pairs() pairs, on the bucketed path, with one host synchronisation and
 // few host calls: the same kernels as build_graph_pruned, launched back to back; every buffer whose size depends on

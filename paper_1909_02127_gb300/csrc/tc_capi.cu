@@ -62,6 +62,7 @@ tc_tuning g_tuning = [] {
   t.compact_max_pairs = int64_t(1) << 25;  // measured faster than reading sizes as known, R-MAT 12-20
   // measured: staged long rows 1.5% faster at R-MAT 26 (5 GB CSR), 2-7% slower at R-MAT 20-24 (up to 1.2 GB)
   t.stage_min_csr_bytes = int64_t(4) << 30;
+  t.tiny_max_pairs = kTinyMaxPairs;
   return t;
 }();
 }  // namespace
@@ -90,6 +91,11 @@ int64_t stage_min_csr_bytes() {
 int64_t compact_max_pairs() {
   std::lock_guard<std::mutex> lk(g_tuning_mutex);
   return g_tuning.compact_max_pairs;
+}
+
+int64_t tiny_max_pairs() {
+  std::lock_guard<std::mutex> lk(g_tuning_mutex);
+  return g_tuning.tiny_max_pairs;
 }
 
 bool use_buckets(int64_t pairs) {
@@ -316,9 +322,9 @@ TC_API tc_status tc_set_tuning(const tc_tuning* t) {
     return TC_ERR_INVALID_ARG;
   }
   if (t->isect_max_wedges_milli < 0 || t->bucket_max_pairs < 0 || t->compact_max_pairs < 0 ||
-      t->stage_min_csr_bytes < 0) {
-    set_error("tc_set_tuning: isect_max_wedges_milli, bucket_max_pairs, compact_max_pairs and stage_min_csr_bytes "
-              "must be >= 0");
+      t->stage_min_csr_bytes < 0 || t->tiny_max_pairs < 0) {
+    set_error("tc_set_tuning: isect_max_wedges_milli, bucket_max_pairs, compact_max_pairs, stage_min_csr_bytes and "
+              "tiny_max_pairs must be >= 0");
     return TC_ERR_INVALID_ARG;
   }
   for (int i = 0; i < t->num_classes; ++i) {
@@ -402,16 +408,22 @@ TC_API tc_status tc_load_edges(const int32_t* src, const int32_t* dst, int64_t n
   Buf err, stage;
   uint32_t h_err = 0;
   do {
-    if ((st = buf_alloc(g->alloc, g->acc, 64, s))) break;
     if (!(g->host_total = slot_acquire())) {
       set_error("tc_load_edges: pinned host allocation failed");
       st = TC_ERR_NO_MEMORY;
       break;
     }
     const size_t n4 = (size_t)(num_vertices > 0 ? num_vertices : 1) * 4;
-    if (num_edges > 0 && num_vertices > 0 && num_edges <= compact_max_pairs() && use_buckets(num_edges)) {
-      // a graph that tc_build will build compactly: the error word, the counts and the keys in one block,
-      // cleared up to the keys with one call
+    if (num_edges > 0 && num_vertices > 0 && use_buckets(num_edges) && tiny_eligible(num_vertices, num_edges)) {
+      // a small graph: one block from here on (error word, counts, keys, count words, build scratch, CSR)
+      uint32_t* e = nullptr;
+      if ((st = tiny_ingest(g, &e, s))) break;
+      err.p = e;
+      err.owned = false;
+    } else if (num_edges > 0 && num_vertices > 0 && use_buckets(num_edges) && num_edges <= compact_max_pairs()) {
+      if ((st = buf_alloc(g->alloc, g->acc, 64, s))) break;
+      // a graph that tc_build will build with one synchronisation: the error word, the counts and the keys in one
+      // block, cleared up to the keys with one call
       Arena sizing;
       sizing.take<uint32_t>(4);
       sizing.view(n4);
@@ -425,6 +437,7 @@ TC_API tc_status tc_load_edges(const int32_t* src, const int32_t* dst, int64_t n
       g->keys = ar.view((size_t)num_edges * 8);
       if ((st = cuda_status(cudaMemsetAsync(g->ingest.p, 0, clear, s), "memset counts"))) break;
     } else {
+      if ((st = buf_alloc(g->alloc, g->acc, 64, s))) break;
       if ((st = buf_alloc(g->alloc, g->indeg, n4, s))) break;
       if ((st = cuda_status(cudaMemsetAsync(g->indeg.p, 0, n4, s), "memset indeg"))) break;
       if (num_edges == 0) break;

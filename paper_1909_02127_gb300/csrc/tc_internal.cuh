@@ -180,6 +180,7 @@ struct tc_graph {
   tc::Buf indeg;             // int32[n]: input pairs at each vertex (self-loops excluded), until tc_build
   tc::Buf ingest;            // small graphs: one block holding keys and indeg (then views), until tc_build
   tc::Buf block;             // compact builds: one block holding off, col, perm, list, tlist, dq0, dense (views)
+  bool tiny = false;         // a small graph laid out in `block` from ingest on (keys, counts, scratch, CSR)
   bool built = false;
   // built state
   int64_t m = 0;

@@ -11,7 +11,8 @@ table; only speed does.
 
 It also times the build paths (the compact build with one host synchronisation, and the build that reads each size as
 it becomes known) on graphs of increasing size and keeps the largest size at which the compact build still wins
-(compact_max_pairs); and it times the count with long hop-2 rows
+(compact_max_pairs), and likewise for the one-launch build against the compact build on the graphs within its bounds
+(tiny_max_pairs); and it times the count with long hop-2 rows
 staged through shared memory against plain loads on graphs too large for L2, keeping the smallest CSR size from which
 staging wins (stage_min_csr_bytes; 0 if it never does).
 
@@ -78,25 +79,32 @@ def largest_winning(rows, fast, slow):
 
 
 def tune_build_paths(tc, graphgen, quick):
+    """Build times of the compact build against the one that reads sizes as known (compact_max_pairs), and on the
+    graphs small enough for it, of the one-launch build against the compact build (tiny_max_pairs)."""
     import torch
-    names = ["er4096", "rmat12", "rmat13", "rmat16", "rmat18", "rmat20"] + ([] if quick else ["rmat21", "rmat22"])
+    names = ["rmat10", "er4096", "rmat12", "rmat13", "rmat16", "rmat18", "rmat20"] + ([] if quick else
+                                                                                       ["rmat21", "rmat22"])
     rows = []
-    base = tc.tc_get_compact_max_pairs()
+    base = (tc.tc_get_compact_max_pairs(), tc.tc_get_tiny_max_pairs())
     try:
         for name in names:
             spec = graphgen.config(name)
             ds, dd = spec.edges(device="cuda")
             row = {"graph": name, "pairs": spec.num_edges, "n": spec.n}
-            for path, cmp in (("compact_ms", 1 << 40), ("sync_ms", 0)):
-                tc.tc_set_tuning(tc.tc_get_tuning(), compact_max_pairs=cmp)
+            paths = [("compact_ms", 1 << 40, 0), ("sync_ms", 0, 0)]
+            if spec.n <= tc.TINY_MAX_VERTICES and spec.num_edges <= tc.TINY_MAX_PAIRS:
+                paths.append(("tiny_ms", 0, tc.TINY_MAX_PAIRS))
+            for path, cmp, tiny in paths:
+                tc.tc_set_tuning(tc.tc_get_tuning(), compact_max_pairs=cmp, tiny_max_pairs=tiny)
                 row[path] = round(time_build(tc, ds, dd, spec.n, 3 if quick else 7), 4)
             rows.append(row)
             print(row, flush=True)
             del ds, dd
             torch.cuda.empty_cache()
     finally:
-        tc.tc_set_tuning(tc.tc_get_tuning(), compact_max_pairs=base)
-    return rows, largest_winning(rows, "compact_ms", "sync_ms")
+        tc.tc_set_tuning(tc.tc_get_tuning(), compact_max_pairs=base[0], tiny_max_pairs=base[1])
+    tiny_rows = [r for r in rows if "tiny_ms" in r]
+    return rows, largest_winning(rows, "compact_ms", "sync_ms"), largest_winning(tiny_rows, "tiny_ms", "compact_ms")
 
 
 def tune_staging(tc, graphgen, quick):
@@ -262,8 +270,8 @@ def main():
     # the table chosen so far is installed before the build and staging sweeps (the method sweep leaves the last
     # kernel it timed selected)
     tc.tc_set_tuning([tuple(c) for c in classes], batch_warp_max_edges=batch_warp, isect_max_wedges_milli=isect_ratio)
-    build_rows, compact_pairs = tune_build_paths(tc, graphgen, args.quick)
-    print("compact_max_pairs", compact_pairs, flush=True)
+    build_rows, compact_pairs, tiny_pairs = tune_build_paths(tc, graphgen, args.quick)
+    print("compact_max_pairs", compact_pairs, "tiny_max_pairs", tiny_pairs, flush=True)
     stage_rows, stage_bytes = tune_staging(tc, graphgen, args.quick)
     print("stage_min_csr_bytes", stage_bytes, flush=True)
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
@@ -271,15 +279,16 @@ def main():
            "classes": classes, "batch_warp_max_edges": batch_warp, "batch_times_ms": batch_times,
            "isect_max_wedges_milli": isect_ratio, "method_measurements": method_rows,
            "bucket_max_pairs": tc.tc_get_bucket_max_pairs(), "measurements": results,
-           "compact_max_pairs": compact_pairs, "build_measurements": build_rows,
+           "compact_max_pairs": compact_pairs, "tiny_max_pairs": tiny_pairs, "build_measurements": build_rows,
            "stage_min_csr_bytes": stage_bytes, "staging_measurements": stage_rows}
     with open(args.out, "w") as f:
         json.dump(out, f, indent=1)
     tc.tc_set_tuning([tuple(c) for c in classes], batch_warp_max_edges=batch_warp,
                      isect_max_wedges_milli=isect_ratio, compact_max_pairs=compact_pairs,
-                     stage_min_csr_bytes=stage_bytes)
+                     stage_min_csr_bytes=stage_bytes, tiny_max_pairs=tiny_pairs)
     print(json.dumps({"classes": classes, "batch_warp_max_edges": batch_warp, "isect_max_wedges_milli": isect_ratio,
-                      "compact_max_pairs": compact_pairs, "stage_min_csr_bytes": stage_bytes}))
+                      "compact_max_pairs": compact_pairs, "stage_min_csr_bytes": stage_bytes,
+                      "tiny_max_pairs": tiny_pairs}))
 
 
 if __name__ == "__main__":

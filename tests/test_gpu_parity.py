@@ -285,26 +285,36 @@ CSR_CASES = [("rmat13", lambda: (*graphgen.rmat(13, 12, 21).edges(), 1 << 13)),
              ("er_sparse", lambda: (*graphgen.er(30000, 20000, 22).edges(), 30000))]
 
 
-BUILD_PATHS = {"compact": dict(bucket_max_pairs=0, compact_max_pairs=1 << 40),   # buckets, one host sync
-               "buckets": dict(bucket_max_pairs=0, compact_max_pairs=0),         # buckets, sizes read as known
-               "sort": dict(bucket_max_pairs=1, compact_max_pairs=0)}            # radix sort of all pairs
+BUILD_PATHS = {"compact": dict(bucket_max_pairs=0, compact_max_pairs=1 << 40, tiny_max_pairs=0),  # one host sync
+               "buckets": dict(bucket_max_pairs=0, compact_max_pairs=0, tiny_max_pairs=0),        # sizes as known
+               "sort": dict(bucket_max_pairs=1, compact_max_pairs=0, tiny_max_pairs=0),           # radix sort
+               "tiny": dict(bucket_max_pairs=0, compact_max_pairs=0, tiny_max_pairs=(1 << 18) - 1)}  # one launch
 
 
-def _build_with(tc, path, hs, hd, n):
-    """(off, col, perm, info, T) of the graph built on the given path."""
-    saved = (tc.tc_get_bucket_max_pairs(), tc.tc_get_compact_max_pairs())
+def _tiny_eligible(tc, n, pairs):
+    return 0 < n <= tc.TINY_MAX_VERTICES and 0 < pairs <= tc.TINY_MAX_PAIRS
+
+
+def _build_with(tc, path, hs, hd, n, launches=None):
+    """(off, col, perm, info, T) of the graph built on the given path; launches (a list) receives the number of
+    kernels tc_build launched."""
+    saved = dict(bucket_max_pairs=tc.tc_get_bucket_max_pairs(), compact_max_pairs=tc.tc_get_compact_max_pairs(),
+                 tiny_max_pairs=tc.tc_get_tiny_max_pairs())
     tc.tc_set_tuning(tc.tc_get_tuning(), **BUILD_PATHS[path])
     try:
         g = tc.tc_load_edges(hs, hd, n)
         try:
+            k0 = tc.tc_kernel_launches()
             tc.tc_build(g)
+            if launches is not None:
+                launches.append(tc.tc_kernel_launches() - k0)
             off, col, perm = tc.tc_copy_csr(g)
             info = tc.tc_graph_get_info(g)
             T = tc.tc_count(g)
         finally:
             tc.tc_free(g)
     finally:
-        tc.tc_set_tuning(tc.tc_get_tuning(), bucket_max_pairs=saved[0], compact_max_pairs=saved[1])
+        tc.tc_set_tuning(tc.tc_get_tuning(), **saved)
     return off, col, perm, info, T
 
 
@@ -313,9 +323,11 @@ def _build_with(tc, path, hs, hd, n):
 def test_csr_structure(tc, name, make, path):
     """The oriented CSR: vertices relabelled by rank in the (count, id) order, each undirected edge stored once
     from its lower to its higher rank, rows ascending, 16-byte aligned and padded with the id n.  The three ways of
-    building it (per-source buckets with one host synchronisation or with sizes read as they become known, and a
-    radix sort of all pairs) give this same CSR."""
+    building it (per-source buckets with one host synchronisation or with sizes read as they become known, a
+    radix sort of all pairs, and for small graphs one cooperative launch) give this same CSR."""
     hs, hd, n = make()
+    if path == "tiny" and not _tiny_eligible(tc, n, hs.size):
+        pytest.skip("beyond the one-launch build's bounds")
     off, col, perm, info, T = _build_with(tc, path, hs, hd, n)
     assert T == oracle.count(hs, hd, n)[0]
     lo = np.minimum(hs, hd)
@@ -403,11 +415,12 @@ TINY_CASES = [("er4096", lambda: (*graphgen.config("er4096").edges(), 4096)),
 @pytest.mark.parametrize("name,make", TINY_CASES, ids=[c[0] for c in TINY_CASES])
 def test_small_graphs_every_build_path(tc, name, make):
     """Small graphs at the edges of the compact build's bounds (n up to 8192, up to 65536 pairs, dense rows, a hub,
-    a clique, repeats, self-loops, one and two vertices): the compact build, the build that reads sizes as known and
-    the radix-sort build give the same graph, and its counts and per-vertex counts are the oracle's."""
+    a clique, repeats, self-loops, one and two vertices): the compact build, the build that reads sizes as known,
+    the radix-sort build and the one-launch build give the same graph, and its counts and per-vertex counts are the
+    oracle's."""
     hs, hd, n = make()
     a = _build_with(tc, "compact", hs, hd, n)
-    for other in ("buckets", "sort"):
+    for other in ("buckets", "sort", "tiny"):
         b = _build_with(tc, other, hs, hd, n)
         for x, y in zip(a[:3], b[:3]):
             np.testing.assert_array_equal(x, y)
@@ -422,6 +435,48 @@ def test_small_graphs_every_build_path(tc, name, make):
         tc.tc_free(g)
     assert T2 == T
     np.testing.assert_array_equal(t2, t)
+
+
+def _star_and_repeats(n, seed):
+    """A star over all n vertices, one pair repeated 70000 times (an input-pair count above 2^16: three passes of the
+    rank sort), and random pairs."""
+    rng = np.random.default_rng(seed)
+    s = np.concatenate([np.zeros(n - 1, np.int64), np.full(70000, 5), rng.integers(0, n, 20000)])
+    d = np.concatenate([np.arange(1, n), np.full(70000, 9), rng.integers(0, n, 20000)])
+    return s.astype(np.int32), d.astype(np.int32), n
+
+
+def _at_the_bounds(seed):
+    """n = 2^14 and 2^18 - 1 pairs (the one-launch build's largest input): an R-MAT-like skew with long buckets."""
+    spec = graphgen.rmat(14, 16, seed)
+    hs, hd = spec.edges()
+    k = (1 << 18) - 1
+    assert hs.size >= k
+    return hs[:k].copy(), hd[:k].copy(), 1 << 14
+
+
+ONE_LAUNCH_CASES = [("n16384_max_pairs", lambda: _at_the_bounds(95)),
+                    ("star_and_repeats", lambda: _star_and_repeats(16384, 96)),
+                    ("rmat14_ef8", lambda: (*graphgen.rmat(14, 8, 97).edges(), 1 << 14)),
+                    ("gnp_2000_dense", lambda: (*graphgen.gnp(2000, 0.05, 98).edges(), 2000)),
+                    ("isolated_vertices", lambda: (np.array([100, 200, 300], np.int32),
+                                                   np.array([200, 300, 100], np.int32), 16384))]
+
+
+@pytest.mark.parametrize("name,make", ONE_LAUNCH_CASES, ids=[c[0] for c in ONE_LAUNCH_CASES])
+def test_one_launch_build(tc, name, make):
+    """The one-launch build at its bounds (16384 vertices, 2^18 - 1 pairs, an input-pair count above 2^16, a star,
+    isolated vertices): one kernel launch, the compact build's graph, and the oracle's count."""
+    hs, hd, n = make()
+    assert _tiny_eligible(tc, n, hs.size)
+    launches = []
+    a = _build_with(tc, "tiny", hs, hd, n, launches)
+    assert launches == [1]
+    b = _build_with(tc, "compact", hs, hd, n)
+    for x, y in zip(a[:3], b[:3]):
+        np.testing.assert_array_equal(x, y)
+    assert a[3] == b[3]
+    assert a[4] == b[4] == oracle.count(hs, hd, n)[0]
 
 
 def test_host_and_device_inputs_and_allocators_agree(tc):
