@@ -85,7 +85,7 @@ struct CompactSizes {
   int32_t maxdeg;               // (written by k_rank_keys; unused)
   int32_t pad;
 };
-static_assert(sizeof(CompactSizes) + 8 <= kHostSlotBytes, "the compact build's sizes must fit the landing slot");
+static_assert(sizeof(CompactSizes) + 8 <= kHostErrOffset, "the compact build's sizes must fit the landing slot");
 
 // Bits needed for x (0 for x = 0).
 int bits_of(int64_t x);

@@ -406,7 +406,7 @@ TC_API tc_status tc_load_edges(const int32_t* src, const int32_t* dst, int64_t n
   g->last_stream = s;
   tc_status st = TC_OK;
   Buf err, stage;
-  uint32_t h_err = 0;
+  uint32_t* h_err = nullptr;
   do {
     if (!(g->host_total = slot_acquire())) {
       set_error("tc_load_edges: pinned host allocation failed");
@@ -458,9 +458,11 @@ TC_API tc_status tc_load_edges(const int32_t* src, const int32_t* dst, int64_t n
         break;
       }
     }
-    if ((st = cuda_status(cudaMemcpyAsync(&h_err, err.p, 4, cudaMemcpyDeviceToHost, s), "copy err"))) break;
+    // the error word lands in the graph's page-locked slot: a copy to pageable memory would wait for the stream
+    h_err = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(g->host_total) + kHostErrOffset);
+    if ((st = cuda_status(cudaMemcpyAsync(h_err, err.p, 4, cudaMemcpyDeviceToHost, s), "copy err"))) break;
     if ((st = cuda_status(cudaStreamSynchronize(s), "tc_load_edges sync"))) break;
-    if (h_err) {
+    if (*h_err) {
       set_error("tc_load_edges: an edge endpoint lies outside [0, num_vertices)");
       st = TC_ERR_OUT_OF_RANGE;
     }

@@ -13,6 +13,7 @@ namespace tc {
 
 // Bytes of a graph's page-locked landing slot (see tc_graph::host_total).
 constexpr size_t kHostSlotBytes = 256;
+constexpr size_t kHostErrOffset = kHostSlotBytes - 8;  // an error word's place in the slot (after the build sizes)
 
 // Streaming multiprocessors of the current device (queried once per device, cached).  Persistent grids are sized
 // in multiples of it.

@@ -157,7 +157,7 @@ tc_status count_many(const int32_t* const* srcs, const int32_t* const* dsts, con
     if ((st = cuda_status(cudaMemsetAsync(g->ingest.p, 0, clear, s), "tc_count_many counts"))) break;
     if ((st = pack_edges_many(g, d_ptrs, d_ptrs + k, d_off, d_off + k + 1, k, d_words, s))) break;
     // the error word lands with the build's synchronisation
-    uint32_t* h_err = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(g->host_total) + kHostSlotBytes - 8);
+    uint32_t* h_err = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(g->host_total) + kHostErrOffset);
     *h_err = 0;
     if ((st = cuda_status(cudaMemcpyAsync(h_err, d_words, 4, cudaMemcpyDeviceToHost, s), "tc_count_many error")))
       break;

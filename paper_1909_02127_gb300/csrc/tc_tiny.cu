@@ -2,16 +2,18 @@
 //
 // For a graph of a few thousand vertices the bucketed build's kernels do little work each, and their launches and
 // the gaps between them set the time (ER-4096: about 25 launches).  Here the same steps run in one launch whose
-// CTAs are all resident (a cooperative launch), separated by grid-wide barriers:
-//   0  rank      one CTA: a stable LSD radix sort of (count << 14) | id in shared memory on the count bits, giving
-//                rank(x) and perm; the bucket starts as the exclusive scan of the counts in rank order  (Sec. III-A)
+// CTAs are all resident (a cooperative launch), separated by grid-wide barriers, and no step is left to one CTA:
+//   0  rank      with every key (count << 14) | id in shared memory, each CTA counts for 32 vertices at a time the
+//                keys below theirs, the key range split over its warps: rank(x) and perm, the (count, id) order
+//                (Sec. III-A).  Bucket starts are claimed in any order, a warp's 32 vertices with one atomic add.
 //   1  bucket    every pair into the bucket of its lower-ranked endpoint as the higher rank        (Sec. III-A/C)
 //   2  rows      one warp per bucket: sorted and de-duplicated in place (a bitonic sort in registers up to 32
 //                pairs, else a bitmap over the target range in the warp's shared memory); d+(u), and the row's
 //                hop-2 cost code and dense quads as k_dense_select decides them                 (Def. 1, Sec. III-B)
-//   3  offsets   one CTA: the exclusive scans of the padded lengths (off) and of the dense quads (dq0)
-//   4  CSR, bins one warp per row: the row into the CSR with its padding, w(u) from its out-neighbours' codes and
-//                the bin it goes to (as k_bins decides), and its dense bitmap when it has one      (Sec. III-C)
+//   3  CSR, bins each CTA takes a contiguous range of ranks: the padded lengths and dense quads of all ranks below
+//                it summed (each CTA for itself), then scanned over its own rows to give off and dq0; one warp per
+//                row writes the row with its padding, w(u) from its out-neighbours' codes and the bin it goes to
+//                (as k_bins decides), and its dense bitmap when it has one                       (Sec. III-C)
 // The result is the CSR of build_graph_compact, the bin lists up to their order.  Ids fit 14 bits and input-pair
 // counts 18, so a rank key is one 32-bit word and every target range fits a warp's 2 KB bitmap.
 //
@@ -27,17 +29,16 @@
 namespace tc {
 namespace {
 
-constexpr int kTinyThreads = 512;
+constexpr int kTinyThreads = 1024;
 constexpr int kTinyWarps = kTinyThreads / 32;
-constexpr int kTinyDigits = 256;                                 // radix sort digit: 8 bits
 constexpr int kTinyRowWords = (int)(kTinyMaxVertices / 32);      // a warp's bitmap: 512 words
 constexpr unsigned kTinySpinLimit = 1u << 20;                    // barrier polls before giving up (~1 s)
-constexpr uint32_t kTinyIdMask = (1u << kTinyIdBits) - 1u;
 
 struct TinyCtl {
   unsigned arrive;  // CTA arrivals at the barriers so far: barrier k is passed at (k + 1) * gridDim.x
   unsigned err;     // 1: a barrier gave up waiting
-  unsigned pad[2];
+  unsigned alloc;   // bucket entries claimed so far
+  unsigned pad;
 };
 
 // What the host clears before the launch and reads back after it: the sizes and the barrier word.
@@ -45,7 +46,7 @@ struct TinyHead {
   CompactSizes sz;
   TinyCtl ctl;
 };
-static_assert(sizeof(TinyHead) + 8 <= kHostSlotBytes, "the one-launch build's read-back must fit the landing slot");
+static_assert(sizeof(TinyHead) + 8 <= kHostErrOffset, "the one-launch build's read-back must fit the landing slot");
 
 struct TinyArgs {
   const uint64_t* keys;   // M pair keys (lo << B) | hi, or the sentinel
@@ -56,12 +57,12 @@ struct TinyArgs {
   int32_t wtopq;          // quads of the top bitmap window row (the window is every vertex: n <= 32768)
   int32_t pad_;
   int64_t block_min_work;
-  int32_t* rank;          // [n]
-  uint32_t* pstart;       // [n + 1] bucket starts, by rank
-  uint32_t* cur;          // [n] bucket cursors
+  int32_t* rank;          // [n] by id
+  uint32_t* bstart;       // [n] bucket start, by id (buckets in any order)
+  uint32_t* cur;          // [n] bucket cursor, by id
+  uint32_t* rstart;       // [n] the de-duplicated row's start in tgt, by rank
   int32_t* tgt;           // [sum of counts] bucket targets, rows de-duplicated in place
-  int32_t* odeg;          // [n] d+(u)
-  int2* rowinfo;          // [n] {d+(u), padded length or minus dense quads}
+  int2* rowinfo;          // [n] {d+(u), padded length or minus dense quads}, by rank
   // the graph
   int64_t* off;           // [n + 1]
   int32_t* col;
@@ -113,100 +114,15 @@ __device__ bool grid_barrier(TinyCtl* ctl, unsigned k) {
   return s_ok != 0;
 }
 
-// Exclusive scan by one CTA of get(i) for i in [0, n), handed to emit(i, prefix, value); returns the total.  Warp w
-// takes a contiguous chunk, 32 consecutive values per step (coalesced, and conflict-free in shared memory): its
-// total first, then its offset from the warps before it, then a warp scan per step.
-template <class T, class Get, class Emit>
-__device__ T cta_scan(int n, T* ws, Get get, Emit emit) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int chunk = ((n + kTinyThreads - 1) / kTinyThreads) * 32;
-  const int beg = min(n, warp * chunk), end = min(n, beg + chunk);
-  T sum = 0;
-  for (int j = beg; j < end; j += 32) sum += j + lane < end ? get(j + lane) : T(0);
-  sum = warp_sum(sum);
-  if (lane == 0) ws[warp] = sum;
-  __syncthreads();
-  T base = 0, total = 0;
-  for (int w = 0; w < kTinyWarps; ++w) {
-    const T t = ws[w];
-    base += w < warp ? t : T(0);
-    total += t;
-  }
-  __syncthreads();
-  for (int j = beg; j < end; j += 32) {
-    const int i = j + lane;
-    const T x = i < end ? get(i) : T(0);
-    const T incl = warp_inclusive_scan(x);
-    if (i < end) emit(i, base + incl - x, x);
-    base += __shfl_sync(kFull, incl, 31);
-  }
-  return total;
-}
-
-// The lanes of the warp whose 8-bit digit equals this lane's (among the lanes in `valid`), by one ballot per bit.
-__device__ __forceinline__ unsigned digit_peers(uint32_t d, unsigned valid) {
-  unsigned peers = valid;
-#pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    const unsigned set = __ballot_sync(kFull, (d >> b) & 1u);
-    peers &= ((d >> b) & 1u) ? set : ~set;
-  }
-  return peers;
-}
-
-// One stable counting pass of the rank sort (one CTA) on the 8-bit digit at `shift`: warp w takes a contiguous
-// chunk of the keys, counts its digits (the lanes sharing a digit found by ballots; the first of them adds), the
-// counts are scanned in digit-major, warp-minor order, and a second sweep writes each key to its place.
-__device__ void tiny_sort_pass(const uint32_t* in, uint32_t* out, int n, int shift, uint32_t* wc, uint32_t* ws) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned lt = lanemask_lt();
-  const int chunk = ((n + kTinyThreads - 1) / kTinyThreads) * 32;
-  const int beg = min(n, warp * chunk), end = min(n, beg + chunk);
-  uint32_t* mine = wc + warp * kTinyDigits;
-  for (int d = lane; d < kTinyDigits; d += 32) mine[d] = 0u;
-  __syncwarp();
-  for (int j = beg; j < end; j += 32) {
-    const int i = j + lane;
-    const uint32_t d = i < end ? (in[i] >> shift) & 255u : 0u;
-    const unsigned peers = digit_peers(d, __ballot_sync(kFull, i < end));
-    if (i < end && lane == __ffs(peers) - 1) mine[d] += (uint32_t)__popc(peers);
-    __syncwarp();
-  }
-  __syncthreads();
-  constexpr int per = kTinyDigits * kTinyWarps / kTinyThreads;  // 8 entries per thread
-  uint32_t v[per];
-  uint32_t sum = 0;
-#pragma unroll
-  for (int k = 0; k < per; ++k) {
-    const int idx = threadIdx.x * per + k;  // digit idx / kTinyWarps, warp idx % kTinyWarps
-    v[k] = wc[(idx % kTinyWarps) * kTinyDigits + idx / kTinyWarps];
-    sum += v[k];
-  }
-  uint32_t total;
-  uint32_t run = block_exclusive_scan<uint32_t>(sum, ws, &total);
-#pragma unroll
-  for (int k = 0; k < per; ++k) {
-    const int idx = threadIdx.x * per + k;
-    wc[(idx % kTinyWarps) * kTinyDigits + idx / kTinyWarps] = run;
-    run += v[k];
-  }
-  __syncthreads();
-  for (int j = beg; j < end; j += 32) {
-    const int i = j + lane;
-    const uint32_t key = i < end ? in[i] : 0u;
-    const uint32_t d = (key >> shift) & 255u;
-    const unsigned peers = digit_peers(d, __ballot_sync(kFull, i < end));
-    if (i < end) out[mine[d] + __popc(peers & lt)] = key;
-    __syncwarp();
-    if (i < end && lane == __ffs(peers) - 1) mine[d] += (uint32_t)__popc(peers);
-    __syncwarp();
-  }
-  __syncthreads();
+// (padded length << 32) | dense quads of a row from its code: summed over rows, the low half never carries into the
+// high one (the quads total below 2^32).
+__device__ __forceinline__ unsigned long long row_sizes(int2 ri) {
+  return ((unsigned long long)(uint32_t)((ri.x + 3) & ~3) << 32) | (uint32_t)(ri.y < 0 ? -ri.y : 0);
 }
 
 __global__ void __launch_bounds__(kTinyThreads, 1) k_tiny_build(TinyArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ uint32_t ws[32];
+  __shared__ unsigned long long ws64[kTinyWarps];
   __shared__ unsigned long long s_acc[6];  // m, wedges, active, dense wedges, dense visits, max d+
   __shared__ uint32_t s_cnt[3];            // block, warp, thread bin entries of this CTA
   __shared__ uint32_t s_base[3];
@@ -217,15 +133,13 @@ __global__ void __launch_bounds__(kTinyThreads, 1) k_tiny_build(TinyArgs a) {
   if (tid < 6) s_acc[tid] = 0ull;
   if (tid < 3) s_cnt[tid] = 0u;
 
-  // ---- 0: rank (one CTA) ----
-  if (blockIdx.x == 0) {
-    const int npad = (n + 3) & ~3;
-    uint32_t* ka = smem;
-    uint32_t* kb = smem + npad;
-    uint32_t* wc = kb + npad;
-    int mx = 0;
+  // ---- 0: ranks (every CTA for its own vertices) and bucket starts ----
+  {
+    const int npad = (n + 4 * kTinyWarps - 1) & ~(4 * kTinyWarps - 1);  // whole uint4 steps for every warp
+    uint32_t* key = smem;                                              // [npad]; the padding is above every key
+    uint32_t* part = smem + npad;                                      // [kTinyWarps][32] partial counts
     constexpr int kLoads = 8;  // counts loaded side by side before they are stored
-    for (int i0 = tid; i0 < n; i0 += kLoads * kTinyThreads) {
+    for (int i0 = tid; i0 < npad; i0 += kLoads * kTinyThreads) {
       int c[kLoads];
 #pragma unroll
       for (int k = 0; k < kLoads; ++k) {
@@ -235,34 +149,45 @@ __global__ void __launch_bounds__(kTinyThreads, 1) k_tiny_build(TinyArgs a) {
 #pragma unroll
       for (int k = 0; k < kLoads; ++k) {
         const int i = i0 + k * kTinyThreads;
-        if (i < n) ka[i] = ((uint32_t)c[k] << kTinyIdBits) | (uint32_t)i;
-        mx = max(mx, c[k]);
+        if (i < npad) key[i] = i < n ? ((uint32_t)c[k] << kTinyIdBits) | (uint32_t)i : 0xffffffffu;
       }
     }
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
-    if (lane == 0) ws[warp] = (uint32_t)mx;
     __syncthreads();
-    uint32_t all = 0;
-    for (int w = 0; w < kTinyWarps; ++w) all = max(all, ws[w]);
-    __syncthreads();
-    const int cbits = 32 - __clz((int)all);
-    for (int shift = kTinyIdBits; shift - kTinyIdBits < cbits; shift += 8) {
-      tiny_sort_pass(ka, kb, n, shift, wc, ws);
-      uint32_t* t = ka;
-      ka = kb;
-      kb = t;
+    // rank(x) = #{y : key(y) < key(x)}: lane l takes vertex xb + l, warp w the keys [w * per, (w + 1) * per)
+    const int per4 = npad / (4 * kTinyWarps);
+    const uint4* mine = reinterpret_cast<const uint4*>(key) + warp * per4;
+    for (int xb = blockIdx.x * 32; xb < n; xb += gridDim.x * 32) {
+      const int x = xb + lane;
+      const uint32_t kx = x < n ? key[x] : 0u;
+      uint32_t c0 = 0, c1 = 0;
+      for (int j = 0; j < per4; ++j) {
+        const uint4 v = mine[j];
+        c0 += (v.x < kx ? 1u : 0u) + (v.y < kx ? 1u : 0u);
+        c1 += (v.z < kx ? 1u : 0u) + (v.w < kx ? 1u : 0u);
+      }
+      part[warp * 32 + lane] = c0 + c1;
+      __syncthreads();
+      if (warp == 0 && x < n) {
+        uint32_t r = 0;
+        for (int w = 0; w < kTinyWarps; ++w) r += part[w * 32 + lane];
+        a.rank[x] = (int32_t)r;
+        a.perm[r] = x;
+      }
+      __syncthreads();
     }
-    const uint32_t* sorted = ka;
-    const uint32_t total = cta_scan<uint32_t>(
-        n, ws, [&](int r) { return sorted[r] >> kTinyIdBits; },
-        [&](int r, uint32_t pos, uint32_t) {
-          const int32_t id = (int32_t)(sorted[r] & kTinyIdMask);
-          a.rank[id] = r;
-          a.perm[r] = id;
-          a.pstart[r] = pos;
-          a.cur[r] = pos;
-        });
-    if (tid == 0) a.pstart[n] = total;
+    // bucket starts: room for each vertex's input-pair count, one atomic claim per warp of 32 vertices
+    for (int xb = gwarp * 32; xb < n; xb += nwarps * 32) {
+      const int x = xb + lane;
+      const uint32_t c = x < n ? key[x] >> kTinyIdBits : 0u;
+      const uint32_t incl = warp_inclusive_scan(c);
+      uint32_t base = 0;
+      if (lane == 31 && incl) base = atomicAdd(&a.ctl->alloc, incl);
+      base = __shfl_sync(kFull, base, 31) + incl - c;
+      if (x < n) {
+        a.bstart[x] = base;
+        a.cur[x] = base;
+      }
+    }
   }
   if (!grid_barrier(a.ctl, 0)) return;
 
@@ -285,7 +210,7 @@ __global__ void __launch_bounds__(kTinyThreads, 1) k_tiny_build(TinyArgs a) {
       uint32_t slot[kItems];
 #pragma unroll
       for (int j = 0; j < kItems; ++j)
-        if (k[j] != sentinel) slot[j] = atomicAdd(&a.cur[ra[j] < rb[j] ? ra[j] : rb[j]], 1u);
+        if (k[j] != sentinel) slot[j] = atomicAdd(&a.cur[ra[j] < rb[j] ? k[j] >> a.B : k[j] & mask], 1u);
 #pragma unroll
       for (int j = 0; j < kItems; ++j)
         if (k[j] != sentinel) a.tgt[slot[j]] = ra[j] < rb[j] ? rb[j] : ra[j];
@@ -298,27 +223,28 @@ __global__ void __launch_bounds__(kTinyThreads, 1) k_tiny_build(TinyArgs a) {
     const unsigned lt = lanemask_lt();
     uint32_t* bm = smem + warp * kTinyRowWords;
     unsigned long long msum = 0;
-    for (int u = gwarp; u < n; u += nwarps) {
-      const uint32_t ps = a.pstart[u];
-      const int L = (int)(a.cur[u] - ps);
+    for (int x = gwarp; x < n; x += nwarps) {
+      const uint32_t ps = a.bstart[x];
+      const int L = (int)(a.cur[x] - ps);
+      const int u = a.rank[x];
       int32_t* row = a.tgt + ps;
       int dd;
       if (L <= 1) {
         dd = L;
       } else if (L <= 32) {
-        int32_t x = lane < L ? row[lane] : INT_MAX;
+        int32_t v = lane < L ? row[lane] : INT_MAX;
 #pragma unroll
         for (int kk = 2; kk <= 32; kk <<= 1) {
 #pragma unroll
           for (int j = kk >> 1; j > 0; j >>= 1) {
-            const int32_t y = __shfl_xor_sync(kFull, x, j);
-            x = (((lane & j) == 0) == ((lane & kk) == 0)) ? min(x, y) : max(x, y);
+            const int32_t y = __shfl_xor_sync(kFull, v, j);
+            v = (((lane & j) == 0) == ((lane & kk) == 0)) ? min(v, y) : max(v, y);
           }
         }
-        const int32_t prev = __shfl_up_sync(kFull, x, 1);
-        const bool keep = x != INT_MAX && (lane == 0 || x != prev);
+        const int32_t prev = __shfl_up_sync(kFull, v, 1);
+        const bool keep = v != INT_MAX && (lane == 0 || v != prev);
         const unsigned km = __ballot_sync(kFull, keep);
-        if (keep) row[__popc(km & lt)] = x;
+        if (keep) row[__popc(km & lt)] = v;
         dd = __popc(km);
       } else {  // targets lie in (u, n): a bitmap over that range
         const int range = n - 1 - u;
@@ -352,8 +278,8 @@ __global__ void __launch_bounds__(kTinyThreads, 1) k_tiny_build(TinyArgs a) {
         int32_t code = (dd + 3) & ~3;
         const int32_t q = a.wtopq - (int32_t)((u + 1) >> 7);
         if (dd >= kDenseMinDegree && 4 * (int64_t)q <= dd) code = -q;
-        a.odeg[u] = dd;
         a.rowinfo[u] = make_int2(dd, code);
+        a.rstart[u] = ps;
         msum += (unsigned long long)dd;
       }
     }
@@ -361,60 +287,56 @@ __global__ void __launch_bounds__(kTinyThreads, 1) k_tiny_build(TinyArgs a) {
   }
   if (!grid_barrier(a.ctl, 2)) return;
 
-  // ---- 3: offsets and dense-row quads (one CTA): one scan of (padded length << 32) | dense quads, whose low half
-  // never carries (the quads total below 2^32) ----
-  if (blockIdx.x == 0) {
-    uint64_t* both = reinterpret_cast<uint64_t*>(smem);  // [n]
-    unsigned long long* ws64 = reinterpret_cast<unsigned long long*>(smem + 2 * ((n + 1) & ~1));
-    constexpr int kLoads = 8;
-    for (int i0 = tid; i0 < n; i0 += kLoads * kTinyThreads) {
-      int2 ri[kLoads];
-#pragma unroll
-      for (int k = 0; k < kLoads; ++k) {
-        const int i = i0 + k * kTinyThreads;
-        ri[k] = i < n ? a.rowinfo[i] : make_int2(0, 0);
-      }
-#pragma unroll
-      for (int k = 0; k < kLoads; ++k) {
-        const int i = i0 + k * kTinyThreads;
-        if (i < n)
-          both[i] = ((uint64_t)(uint32_t)((ri[k].x + 3) & ~3) << 32) | (uint32_t)(ri[k].y < 0 ? -ri[k].y : 0);
+  // ---- 3: the CSR rows, bins and dense bitmaps of this CTA's ranks [r0, r1) ----
+  {
+    const int R = (n + gridDim.x - 1) / gridDim.x;
+    const int r0 = min(n, (int)blockIdx.x * R), r1 = min(n, r0 + R);
+    uint32_t* s_off = smem;                                       // [R] row offsets
+    int32_t* s_dq = reinterpret_cast<int32_t*>(smem + R);         // [R] dense row starts, or -1
+    int32_t* lb = reinterpret_cast<int32_t*>(smem + 2 * R);       // [3][R] bin entries: block, warp, thread
+    // the sizes of every row below r0, then a scan over this CTA's rows (R <= kTinyThreads)
+    unsigned long long below = 0;
+    for (int r = tid; r < r0; r += kTinyThreads) below += row_sizes(a.rowinfo[r]);
+    below = warp_sum(below);
+    if (lane == 0) ws64[warp] = below;
+    __syncthreads();
+    unsigned long long prefix = 0;
+    for (int w = 0; w < kTinyWarps; ++w) prefix += ws64[w];
+    __syncthreads();
+    const int r = r0 + tid;
+    const unsigned long long mine = r < r1 ? row_sizes(a.rowinfo[r]) : 0ull;
+    unsigned long long total;
+    const unsigned long long pos = prefix + block_exclusive_scan<unsigned long long>(mine, ws64, &total);
+    uint32_t dense_here = 0;
+    if (r < r1) {
+      s_off[tid] = (uint32_t)(pos >> 32);
+      const bool dense = (uint32_t)mine != 0u;
+      s_dq[tid] = dense ? (int32_t)(uint32_t)pos : -1;
+      a.off[r] = (int64_t)(pos >> 32);
+      a.dq0[r] = dense ? (int32_t)(uint32_t)pos : -1;
+      dense_here = dense ? 1u : 0u;
+    }
+    dense_here = warp_sum(dense_here);
+    if (lane == 0 && dense_here) atomicAdd(&a.sizes->dense_rows, (unsigned long long)dense_here);
+    if (r0 < r1 && r1 == n) {  // the CTA holding the last rank: the totals and the spare quad after the last row
+      const unsigned long long all = prefix + total;
+      const uint32_t tp = (uint32_t)(all >> 32);
+      if (tid < 4) a.col[tp + tid] = n;
+      if (tid == 0) {
+        a.off[n] = tp;
+        a.sizes->entries = tp;
+        a.sizes->dquads = (uint32_t)all;
       }
     }
     __syncthreads();
-    uint32_t rows = 0;
-    const unsigned long long tot = cta_scan<unsigned long long>(
-        n, ws64, [&](int r) { return (unsigned long long)both[r]; },
-        [&](int r, unsigned long long pos, unsigned long long v) {
-          a.off[r] = (int64_t)(pos >> 32);
-          const bool dense = (uint32_t)v != 0u;
-          a.dq0[r] = dense ? (int32_t)(uint32_t)pos : -1;
-          rows += dense ? 1u : 0u;
-        });
-    const uint32_t tp = (uint32_t)(tot >> 32), tq = (uint32_t)tot;
-    rows = warp_sum(rows);
-    if (lane == 0 && rows) atomicAdd(&a.sizes->dense_rows, (unsigned long long)rows);
-    if (tid < 4) a.col[tp + tid] = n;  // the spare quad after the last row
-    if (tid == 0) {
-      a.off[n] = tp;
-      a.sizes->entries = tp;
-      a.sizes->dquads = tq;
-    }
-  }
-  if (!grid_barrier(a.ctl, 3)) return;
-
-  // ---- 4: rows into the CSR, bins, dense bitmaps ----
-  {
-    int32_t* lb = reinterpret_cast<int32_t*>(smem);  // this CTA's bin entries: block, warp, thread
-    const int cap = kTinyWarps * ((n + nwarps - 1) / nwarps);  // rows of this CTA at most
     unsigned long long wsum = 0, act = 0, dw = 0, dv = 0;
     int dmax = 0;
-    for (int u = gwarp; u < n; u += nwarps) {
-      const uint32_t ps = a.pstart[u];
+    for (int u = r0 + warp; u < r1; u += kTinyWarps) {
+      const uint32_t ps = a.rstart[u];
       const int2 ri = a.rowinfo[u];
       const int d = ri.x;
       const int pl = (d + 3) & ~3;
-      const int64_t o = a.off[u];
+      const int64_t o = s_off[u - r0];
       RowWork w;
       for (int j = lane; j < pl; j += 32) {
         int32_t v = n;
@@ -427,7 +349,7 @@ __global__ void __launch_bounds__(kTinyThreads, 1) k_tiny_build(TinyArgs a) {
       const int64_t wpad = warp_sum(w.pad), wtrue = warp_sum(w.wtrue);
       const int64_t wdense = warp_sum(w.wdense), qdense = warp_sum(w.qdense);
       if (ri.y < 0) {  // its dense row: zeroed, then its bits
-        const int32_t q0 = a.dq0[u], nq = -ri.y;
+        const int32_t q0 = s_dq[u - r0], nq = -ri.y;
         uint4* qz = reinterpret_cast<uint4*>(a.dense) + q0;
         for (int j = lane; j < nq; j += 32) qz[j] = make_uint4(0u, 0u, 0u, 0u);
         __syncwarp();
@@ -448,7 +370,7 @@ __global__ void __launch_bounds__(kTinyThreads, 1) k_tiny_build(TinyArgs a) {
         act += keep ? 1 : 0;
         if (keep) {
           const int which = blk ? 0 : (tny ? 2 : 1);
-          lb[which * cap + atomicAdd(&s_cnt[which], 1u)] = u;
+          lb[which * R + atomicAdd(&s_cnt[which], 1u)] = u;
         }
       }
     }
@@ -474,24 +396,23 @@ __global__ void __launch_bounds__(kTinyThreads, 1) k_tiny_build(TinyArgs a) {
     }
     __syncthreads();
     for (uint32_t i = tid; i < s_cnt[0]; i += kTinyThreads) a.list[s_base[0] + i] = lb[i];
-    for (uint32_t i = tid; i < s_cnt[1]; i += kTinyThreads) a.list[n - 1 - (s_base[1] + i)] = lb[cap + i];
-    for (uint32_t i = tid; i < s_cnt[2]; i += kTinyThreads) a.tlist[s_base[2] + i] = lb[2 * cap + i];
+    for (uint32_t i = tid; i < s_cnt[1]; i += kTinyThreads) a.list[n - 1 - (s_base[1] + i)] = lb[R + i];
+    for (uint32_t i = tid; i < s_cnt[2]; i += kTinyThreads) a.tlist[s_base[2] + i] = lb[2 * R + i];
   }
 }
 
-// Dynamic shared memory of a launch: the rank sort's two key arrays and digit counts (CTA 0), the warps' bitmaps,
-// and a CTA's bin entries, whichever is largest.
+// Dynamic shared memory of a launch: every key and the warps' partial counts (step 0), the warps' bitmaps (step 2),
+// a CTA's offsets, dense starts and bin entries (step 3), whichever is largest.
 size_t tiny_smem_bytes(int64_t n, int grid) {
-  const size_t npad = (size_t)((n + 3) & ~int64_t(3));
-  const size_t sort = (2 * npad + (size_t)kTinyWarps * kTinyDigits) * 4;
+  const size_t npad = (size_t)((n + 4 * kTinyWarps - 1) & ~int64_t(4 * kTinyWarps - 1));
+  const size_t ranks = (npad + (size_t)kTinyWarps * 32) * 4;
   const size_t bitmaps = (size_t)kTinyWarps * kTinyRowWords * 4;
-  const int64_t nwarps = (int64_t)grid * kTinyWarps;
-  const size_t lists = 3 * (size_t)(kTinyWarps * ((n + nwarps - 1) / nwarps)) * 4;
-  size_t b = sort > bitmaps ? sort : bitmaps;
-  return b > lists ? b : lists;
+  const size_t rows = 5 * (size_t)((n + grid - 1) / grid) * 4;
+  size_t b = ranks > bitmaps ? ranks : bitmaps;
+  return b > rows ? b : rows;
 }
 
-constexpr size_t kTinySmemMax = (2 * kTinyMaxVertices + kTinyWarps * kTinyDigits) * 4;  // 144 KB
+constexpr size_t kTinySmemMax = (kTinyMaxVertices + kTinyWarps * 32) * 4;  // 68 KB
 
 // CTAs of a launch: a warp per row and a thread per pair at most, no more than can be resident at once.
 int tiny_grid(int64_t n, int64_t M) {
@@ -511,7 +432,9 @@ int tiny_grid(int64_t n, int64_t M) {
   int64_t g = want_rows > want_pairs ? want_rows : want_pairs;
   const int64_t cap = (int64_t)per_sm * num_sms();
   if (g > cap) g = cap;
-  return (int)(g < 1 ? 1 : g);
+  if (g < 1) g = 1;
+  // step 3 scans a CTA's ranks with one per thread
+  return (n + g - 1) / g <= kTinyThreads ? (int)g : 0;
 }
 
 }  // namespace
@@ -537,6 +460,16 @@ struct TinyLayout {
   TinyArgs a;          // scratch and CSR pointers filled in
 };
 
+// The build's scratch: ranks, bucket starts and cursors by id, row starts and codes by rank, bucket targets.
+void tiny_scratch(Arena& ar, TinyArgs& a, int64_t n, int64_t M) {
+  a.rank = ar.take<int32_t>(n);
+  a.bstart = ar.take<uint32_t>(n);
+  a.cur = ar.take<uint32_t>(n);
+  a.rstart = ar.take<uint32_t>(n);
+  a.rowinfo = ar.take<int2>(n);
+  a.tgt = ar.take<int32_t>(2 * M);
+}
+
 TinyLayout tiny_layout(Arena& ar, tc_graph* g, int64_t n, int64_t M) {
   TinyLayout L{};
   L.head = ar.take<TinyHead>(1);
@@ -545,12 +478,7 @@ TinyLayout tiny_layout(Arena& ar, tc_graph* g, int64_t n, int64_t M) {
   L.clear_bytes = ar.used;
   g->keys = ar.view((size_t)M * 8);
   g->acc = ar.view(64);
-  L.a.rank = ar.take<int32_t>(n);
-  L.a.pstart = ar.take<uint32_t>(n + 1);
-  L.a.cur = ar.take<uint32_t>(n);
-  L.a.tgt = ar.take<int32_t>(2 * M);
-  L.a.odeg = ar.take<int32_t>(n);
-  L.a.rowinfo = ar.take<int2>(n);
+  tiny_scratch(ar, L.a, n, M);
   csr_views(ar, g, n, M + 3 * (n < M ? n : M), n, M / 4 + 1);
   L.a.sizes = L.head ? &L.head->sz : nullptr;
   L.a.ctl = L.head ? &L.head->ctl : nullptr;
@@ -598,23 +526,13 @@ tc_status build_graph_tiny(tc_graph* g, cudaStream_t s) {
     } else {  // keys and counts from elsewhere (tc_count_many): the scratch and the CSR block allocated here
       Arena sizing;
       sizing.take<TinyHead>(1);
-      sizing.take<int32_t>(n);       // rank
-      sizing.take<uint32_t>(n + 1);  // pstart
-      sizing.take<uint32_t>(n);      // cur
-      sizing.take<int32_t>(2 * M);   // tgt
-      sizing.take<int32_t>(n);       // odeg
-      sizing.take<int2>(n);          // rowinfo
+      tiny_scratch(sizing, a, n, M);
       if ((st = buf_alloc(al, scratch, sizing.used, s))) break;
       Arena sa{scratch.as<char>()};
       head = sa.take<TinyHead>(1);
       a.sizes = &head->sz;
       a.ctl = &head->ctl;
-      a.rank = sa.take<int32_t>(n);
-      a.pstart = sa.take<uint32_t>(n + 1);
-      a.cur = sa.take<uint32_t>(n);
-      a.tgt = sa.take<int32_t>(2 * M);
-      a.odeg = sa.take<int32_t>(n);
-      a.rowinfo = sa.take<int2>(n);
+      tiny_scratch(sa, a, n, M);
       Arena bsizing;
       csr_views(bsizing, g, n, bound_entries, n, bound_quads);
       if ((st = buf_alloc(al, g->block, bsizing.used, s))) break;
