@@ -82,13 +82,14 @@ def tune_build_paths(tc, graphgen, quick):
     """Build times of the compact build against the one that reads sizes as known (compact_max_pairs), and on the
     graphs small enough for it, of the one-launch build against the compact build (tiny_max_pairs)."""
     import torch
-    names = ["rmat10", "er4096", "rmat12", "rmat13", "rmat16", "rmat18", "rmat20"] + ([] if quick else
-                                                                                       ["rmat21", "rmat22"])
+    names = ["rmat10", "er4096", "rmat12", "rmat13", "rmat14_ef15", "rmat16", "rmat18", "rmat20"] + (
+        [] if quick else ["rmat21", "rmat22"])
     rows = []
     base = (tc.tc_get_compact_max_pairs(), tc.tc_get_tiny_max_pairs())
     try:
         for name in names:
-            spec = graphgen.config(name)
+            # R-MAT 14 with edge factor 15: 245,760 pairs, near the one-launch build's bound of 2^18 - 1
+            spec = graphgen.rmat(14, 15, graphgen.BASE_SEED + 114) if name == "rmat14_ef15" else graphgen.config(name)
             ds, dd = spec.edges(device="cuda")
             row = {"graph": name, "pairs": spec.num_edges, "n": spec.n}
             paths = [("compact_ms", 1 << 40, 0), ("sync_ms", 0, 0)]
