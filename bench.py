@@ -807,7 +807,7 @@ def run_list(args, dist: Dist):
     # what listing must move: one traversal (the counting pass's bytes, dense rows as bitmaps) and per triangle its
     # 12-byte triple and the 4-byte rank -> id lookup of its third vertex.  The second traversal of the two-pass
     # design (per-source counts, then the triples) is not counted: it shows as a lower fraction.
-    list_bytes = algorithmic_bytes(info, 2 * 152) + 16.0 * T
+    list_bytes = algorithmic_bytes(info, count_grid(info)) + 16.0 * T
     return {
         "metric": "triangles listed per second (ascending original-id triples into device memory)",
         "value": round(units / secs, 1), "unit": "triangles/s", "n_gpus": dist.world, "steps": args.steps,
