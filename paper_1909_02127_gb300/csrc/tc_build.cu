@@ -736,7 +736,31 @@ __global__ void k_rows_copy(const int64_t* __restrict__ pstart, const int32_t* _
       if (dd > 3) q.w = tgt[ps + 3];
       *reinterpret_cast<int4*>(col + o) = q;
     }
-    unsigned todo = __ballot_sync(kFull, pl > 4);
+    // rows of two to eight quads, four at a time: their loads are issued together before any store waits on them
+    unsigned todo = __ballot_sync(kFull, pl > 4 && pl <= 32);
+    while (todo) {
+      int32_t v[4], rpl[4];
+      int64_t ro[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        rpl[r] = 0;
+        ro[r] = 0;
+        v[r] = pad;
+        if (todo) {
+          const int k = __ffs(todo) - 1;
+          todo &= todo - 1;
+          const int64_t rps = __shfl_sync(kFull, ps, k);
+          ro[r] = __shfl_sync(kFull, o, k);
+          const int32_t rd = __shfl_sync(kFull, dd, k);
+          rpl[r] = __shfl_sync(kFull, pl, k);
+          if (lane < rd) v[r] = tgt[rps + lane];
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (lane < rpl[r]) col[ro[r] + lane] = v[r];
+    }
+    todo = __ballot_sync(kFull, pl > 32);
     while (todo) {
       const int k = __ffs(todo) - 1;
       todo &= todo - 1;
@@ -770,11 +794,14 @@ __global__ void k_bins(const int64_t* __restrict__ off, const int32_t* __restric
       b = off[u];
     }
     RowWork w;
-    if (d <= 32) {  // the row as 16-byte quads (rows start on 16-byte boundaries), four row-info loads at a time
+    if (d <= 32) {  // the row as 16-byte quads (rows start on 16-byte boundaries), four row-info loads at a time,
+                    // the next quad's load in flight with them
       const int4* r4 = reinterpret_cast<const int4*>(col + b);
       const int32_t nq = (d + 3) >> 2;
+      const int4 none = make_int4(INT_MAX, INT_MAX, INT_MAX, INT_MAX);
+      int4 q = nq > 0 ? __ldg(&r4[0]) : none;
       for (int32_t k = 0; k < nq; ++k) {
-        const int4 q = __ldg(&r4[k]);
+        const int4 qn = k + 1 < nq ? __ldg(&r4[k + 1]) : none;
         const int2 zero = make_int2(0, 0);
         const int2 i0 = q.x < n ? __ldg(&rowinfo[q.x]) : zero, i1 = q.y < n ? __ldg(&rowinfo[q.y]) : zero;
         const int2 i2 = q.z < n ? __ldg(&rowinfo[q.z]) : zero, i3 = q.w < n ? __ldg(&rowinfo[q.w]) : zero;
@@ -782,6 +809,7 @@ __global__ void k_bins(const int64_t* __restrict__ off, const int32_t* __restric
         w.add(i1);
         w.add(i2);
         w.add(i3);
+        q = qn;
       }
     }
     unsigned longs = __ballot_sync(kFull, d > 32);
