@@ -87,9 +87,15 @@ tc_status launch_count(const tc_graph* g, uint64_t* d_total, uint64_t* d_per_ver
 namespace tc {
 namespace {
 
-// A warp-bin source closing at least this many triangles is listed by a whole CTA: listing costs per triangle,
-// and the bins were cut by 2-paths, which dense rows make cheap to test but not to write out.
-constexpr uint32_t kListBlockMin = 16384;
+// A warp-bin source closing many triangles is listed by a whole CTA: listing costs per triangle, and the bins were
+// cut by 2-paths, which dense rows make cheap to test but not to write out.  "Many" is 1/kListShare of a CTA's
+// average share of the range's triangles, within [kListBlockMinLo, kListBlockMinHi]: a warp-bin source at the end of
+// the queue then finishes in a small fraction of the pass, while the CTAs' per-chunk barriers are paid only where a
+// source has that much to write (measured on R-MAT 16, 18 and 20: the best fixed thresholds were 1024, 4096 and
+// 16384).
+constexpr uint32_t kListBlockMinLo = 1024;
+constexpr uint32_t kListBlockMinHi = 16384;
+constexpr uint64_t kListShare = 64;
 
 // Triangles whose first vertex in the visiting order lies in ranks [first, first + count), taken by the counting
 // kernel's bins: CTAs take the sources of blist one at a time, then warps take warp-bin sources four at a time,
@@ -97,20 +103,21 @@ constexpr uint32_t kListBlockMin = 16384;
 // bin) writes each source's number of triangles to cnt[u - first] (zeroed beforehand: a source in no bin closes no
 // 2-path).  kModeList (blist: k_list_heavy's list) writes them as triples from offs[u - first] on (the exclusive
 // scan of those counts), so each source fills its own range of the output and no global cursor is contended; it
-// skips sources with no triangle and leaves warp-bin sources with kListBlockMin or more to the CTAs.  The output
+// skips sources with no triangle and leaves warp-bin sources with *list_min or more to the CTAs.  The output
 // position of a source lives in shared memory (one per warp; one per CTA for a source of blist, whose warps
 // reserve runs of it with shared atomics).
 template <int MODE>
 __global__ void __launch_bounds__(kCountThreads, 2)
     k_list(CsrView g, int64_t first, int64_t count, dev::Sink sk, uint32_t* __restrict__ cursors,
            uint32_t* __restrict__ cnt, const int64_t* __restrict__ offs, const int32_t* __restrict__ blist,
-           const uint32_t* __restrict__ nblist) {
+           const uint32_t* __restrict__ nblist, const uint32_t* __restrict__ list_min) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint32_t ws[32];
   __shared__ unsigned long long pos[kWarpsPerCTA + 1];  // [warp]: warp-bin sources; [kWarpsPerCTA]: block bin
   __shared__ int s_idx;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t last = first + count;
+  const uint32_t block_min = list_min ? *list_min : kListBlockMinHi;
   const int nb = nblist ? (int)*nblist : g.nb;
   if (nb > 0) {
     const dev::BlockRows br = dev::block_rows(smem);
@@ -161,7 +168,7 @@ __global__ void __launch_bounds__(kCountThreads, 2)
         if (u < first || u >= last) continue;
         if (MODE == dev::kModeList) {
           const uint32_t c = __ldg(&cnt[u - first]);
-          if (c == 0 || c >= kListBlockMin) continue;
+          if (c == 0 || c >= block_min) continue;
           if (lane == 0) pos[warp] = (unsigned long long)offs[u - first];
           __syncwarp();
         }
@@ -193,16 +200,22 @@ __global__ void __launch_bounds__(kCountThreads, 2)
 }
 
 // The CTA work of the listing pass: the block-bin sources of the range that close a triangle and the warp-bin
-// sources that close at least kListBlockMin, appended to heavy in no particular order (*nheavy: zeroed count).
+// sources that close at least the threshold, appended to heavy in no particular order (*nheavy: zeroed count).  The
+// threshold follows the range's triangles (*found) over the listing kernel's CTAs (grid); *list_min receives it.
 __global__ void k_list_heavy(CsrView g, int64_t first, int64_t count, const uint32_t* __restrict__ cnt,
-                             int32_t* __restrict__ heavy, uint32_t* __restrict__ nheavy) {
+                             const unsigned long long* __restrict__ found, int grid, int32_t* __restrict__ heavy,
+                             uint32_t* __restrict__ nheavy, uint32_t* __restrict__ list_min) {
+  const unsigned long long share = *found / ((unsigned long long)(grid > 0 ? grid : 1) * kListShare);
+  const uint32_t thr = share < kListBlockMinLo ? kListBlockMinLo
+                                               : (share > kListBlockMinHi ? kListBlockMinHi : (uint32_t)share);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *list_min = thr;
   const int64_t total = (int64_t)g.nb + g.nw;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const bool blk = i < g.nb;
     const int32_t u = __ldg(&g.list[blk ? i : g.n - g.nw + (i - g.nb)]);
     if (u < first || u >= first + count) continue;
     const uint32_t c = __ldg(&cnt[u - first]);
-    if (blk ? c > 0 : c >= kListBlockMin) heavy[atomicAdd(nheavy, 1u)] = u;
+    if (blk ? c > 0 : c >= thr) heavy[atomicAdd(nheavy, 1u)] = u;
   }
 }
 
@@ -248,7 +261,7 @@ tc_status launch_graph_counts(const tc_graph* g, const int64_t* d_voff, int32_t 
   TC_TRY((smem_attribute_once<k_list<dev::kModeCount>>(dev::kCountSmem)));
   dev::Sink none;
   k_list<dev::kModeCount><<<count_grid(g), kCountThreads, dev::kCountSmem, s>>>(
-      g->view(), 0, g->n, none, d_cursors, d_cnt, nullptr, g->list.as<int32_t>(), nullptr);
+      g->view(), 0, g->n, none, d_cursors, d_cnt, nullptr, g->list.as<int32_t>(), nullptr, nullptr);
   note_launch();
   TC_CUDA(cudaGetLastError());
   k_graph_sums<<<grid_for(g->n, 256), 256, 0, s>>>(d_cnt, g->perm.as<int32_t>(), g->n, d_voff, k,
@@ -278,7 +291,8 @@ tc_status launch_list(const tc_graph* g, int64_t first, int64_t count, int32_t* 
                           "k_list attribute")))
       break;
     k_list<dev::kModeCount><<<grid, kCountThreads, dev::kCountSmem, s>>>(
-        g->view(), first, count, none, d_cursors, cnt.as<uint32_t>(), nullptr, g->list.as<int32_t>(), nullptr);
+        g->view(), first, count, none, d_cursors, cnt.as<uint32_t>(), nullptr, g->list.as<int32_t>(), nullptr,
+        nullptr);
     note_launch();
     if ((st = cuda_status(cudaGetLastError(), "k_list count"))) break;
     // per-source output offsets; their total is the number found (per-source counts are below 2^31: C(d+, 2)
@@ -289,8 +303,9 @@ tc_status launch_list(const tc_graph* g, int64_t first, int64_t count, int32_t* 
       break;
     // the CTAs' sources for pass 2 (their number in d_cursors[3])
     if ((st = cuda_status(cudaMemsetAsync(d_cursors + 3, 0, sizeof(uint32_t), s), "memset heavy"))) break;
-    k_list_heavy<<<2 * num_sms(), 256, 0, s>>>(g->view(), first, count, cnt.as<uint32_t>(), heavy.as<int32_t>(),
-                                            d_cursors + 3);
+    k_list_heavy<<<2 * num_sms(), 256, 0, s>>>(g->view(), first, count, cnt.as<uint32_t>(),
+                                               reinterpret_cast<const unsigned long long*>(d_found), grid,
+                                               heavy.as<int32_t>(), d_cursors + 3, d_cursors + 4);
     note_launch();
     if ((st = cuda_status(cudaGetLastError(), "k_list_heavy"))) break;
     // pass 2: the triples, each source into its own range
@@ -305,7 +320,7 @@ tc_status launch_list(const tc_graph* g, int64_t first, int64_t count, int32_t* 
       break;
     k_list<dev::kModeList><<<grid, kCountThreads, dev::kCountSmem, s>>>(
         g->view(), first, count, sk, d_cursors, cnt.as<uint32_t>(), offs.as<int64_t>(), heavy.as<int32_t>(),
-        d_cursors + 3);
+        d_cursors + 3, d_cursors + 4);
     note_launch();
     st = cuda_status(cudaGetLastError(), "k_list");
   } while (0);
