@@ -479,8 +479,11 @@ def test_one_launch_build(tc, name, make):
     assert a[4] == b[4] == oracle.count(hs, hd, n)[0]
 
 
-def test_host_and_device_inputs_and_allocators_agree(tc):
-    spec = graphgen.rmat(14, 10, 31)
+@pytest.mark.parametrize("scale,ef", [(14, 10), (11, 8)], ids=["compact", "one_launch"])
+def test_host_and_device_inputs_and_allocators_agree(tc, scale, ef):
+    """Host and device inputs with the library's pool and with torch's allocator, on a graph built compactly and on
+    one small enough for the one-launch build."""
+    spec = graphgen.rmat(scale, ef, 31)
     hs, hd = spec.edges()
     ref = oracle.count(hs, hd, spec.n)[0]
     for device in (False, True):
