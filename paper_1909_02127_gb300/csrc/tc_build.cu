@@ -317,7 +317,70 @@ __global__ void k_rank_keys(const int32_t* __restrict__ deg, int64_t n, int B, u
     mx = max(mx, d);
   }
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
-  if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(maxdeg, mx);
+  if (maxdeg && (threadIdx.x & 31) == 0 && mx > 0) atomicMax(maxdeg, mx);
+}
+
+// The compact build's rank keys with the count clamped to kRankClamp, so that two 8-bit radix passes order them:
+// (min(count, kRankClamp) << B) | id.  The vertices at the clamp (counted in *tail) end up last, in id order, and
+// k_rank_tail orders them by their true counts.
+constexpr uint32_t kRankClamp = 65535;
+constexpr int kRankClampBits = 16;
+constexpr int kRankTailMax = 4096;  // the fix-up sort's capacity: 2M / kRankClamp + 1 <= 4096 for M <= 2^27
+
+__global__ void k_rank_keys_clamped(const int32_t* __restrict__ deg, int64_t n, int B, uint64_t* __restrict__ rkeys,
+                                    uint32_t* __restrict__ tail) {
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;  // warp-uniform trip count
+    uint32_t d = 0;
+    if (i < n) {
+      d = (uint32_t)deg[i];
+      rkeys[i] = ((uint64_t)(d < kRankClamp ? d : kRankClamp) << B) | (uint64_t)i;
+    }
+    const unsigned at = __ballot_sync(kFull, i < n && d >= kRankClamp);
+    if (at && (threadIdx.x & 31) == __ffs(at) - 1) atomicAdd(tail, (uint32_t)__popc(at));
+  }
+}
+
+// One CTA: the last *tail keys of the sorted array (the vertices at the clamp, in id order) sorted again on their
+// true counts, (count << B) | id, by a bitonic sort in shared memory.
+__global__ void __launch_bounds__(1024) k_rank_tail(uint64_t* __restrict__ sorted, int64_t n, int B,
+                                                    const int32_t* __restrict__ deg, const uint32_t* __restrict__ tail,
+                                                    uint32_t* __restrict__ err) {
+  __shared__ uint64_t v[kRankTailMax];
+  const int t = (int)*tail;
+  if (t <= 1) return;
+  if (t > kRankTailMax || t > n) {
+    if (threadIdx.x == 0) *err = 1u;
+    return;
+  }
+  int p = 1;
+  while (p < t) p <<= 1;
+  const uint64_t mask = (1ull << B) - 1ull;
+  for (int i = threadIdx.x; i < p; i += blockDim.x) {
+    uint64_t k = ~0ull;
+    if (i < t) {
+      const uint64_t id = sorted[n - t + i] & mask;
+      k = ((uint64_t)(uint32_t)deg[id] << B) | id;
+    }
+    v[i] = k;
+  }
+  __syncthreads();
+  for (int kk = 2; kk <= p; kk <<= 1) {
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < p; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const uint64_t a = v[i], b = v[ixj];
+          if ((a > b) == ((i & kk) == 0)) {
+            v[i] = b;
+            v[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < t; i += blockDim.x) sorted[n - t + i] = v[i];
 }
 
 // rank[id] = r and perm[r] = id; rcount (may be null) receives the input-pair count of rank r.
@@ -1469,10 +1532,20 @@ tc_status build_graph_compact(tc_graph* g, cudaStream_t s) {
     if ((st = cuda_status(cudaMemsetAsync(c.sizes, 0, sizeof(CompactSizes), s), "memset sizes"))) break;
     CompactSizes* ds = c.sizes;
     // ---- rank: stable sort of (count << B) | id on the count bits ----
-    k_rank_keys<<<grid_for(n, 256), 256, 0, s>>>(g->indeg.as<int32_t>(), n, B, c.rkeys, &ds->maxdeg);
-    if ((st = launched("k_rank_keys"))) break;
     uint64_t* rs = nullptr;
-    if ((st = radix_sort_u64(a, c.rkeys, c.rkeys_alt, n, B, B + bits_of(M), &rs, s, c.sort_tmp))) break;
+    const int count_bits = bits_of(M);
+    if (count_bits > kRankClampBits && (2 * M) / kRankClamp + 1 <= kRankTailMax) {
+      // two radix passes on the clamped counts, then the few vertices at the clamp ordered by their true counts
+      k_rank_keys_clamped<<<grid_for(n, 256), 256, 0, s>>>(g->indeg.as<int32_t>(), n, B, c.rkeys, &ds->rank_tail);
+      if ((st = launched("k_rank_keys_clamped"))) break;
+      if ((st = radix_sort_u64(a, c.rkeys, c.rkeys_alt, n, B, B + kRankClampBits, &rs, s, c.sort_tmp))) break;
+      k_rank_tail<<<1, 1024, 0, s>>>(rs, n, B, g->indeg.as<int32_t>(), &ds->rank_tail, &ds->rank_err);
+      if ((st = launched("k_rank_tail"))) break;
+    } else {
+      k_rank_keys<<<grid_for(n, 256), 256, 0, s>>>(g->indeg.as<int32_t>(), n, B, c.rkeys, nullptr);
+      if ((st = launched("k_rank_keys"))) break;
+      if ((st = radix_sort_u64(a, c.rkeys, c.rkeys_alt, n, B, B + count_bits, &rs, s, c.sort_tmp))) break;
+    }
     k_rank<<<grid_for(n, 256), 256, 0, s>>>(rs, n, B, c.rank, g->perm.as<int32_t>(), c.rcount);
     if ((st = launched("k_rank"))) break;
     // ---- buckets: group by the lower-ranked endpoint, sort and de-duplicate each ----
@@ -1525,6 +1598,11 @@ tc_status build_graph_compact(tc_graph* g, cudaStream_t s) {
     if ((st = cuda_status(cudaStreamSynchronize(s), "tc_build sync"))) break;
     if (hs->rc.err) {
       set_error("tc_build: a bucket's targets exceeded the range bound (inconsistent pair counts)");
+      st = TC_ERR_INTERNAL;
+      break;
+    }
+    if (hs->rank_err) {
+      set_error("tc_build: more vertices at the rank sort's count clamp than its fix-up sort holds");
       st = TC_ERR_INTERNAL;
       break;
     }

@@ -82,8 +82,8 @@ struct CompactSizes {
   int64_t entries;              // padded column entries: off[n]
   int64_t dquads;               // quads of the dense rows
   unsigned long long dense_rows;
-  int32_t maxdeg;               // (written by k_rank_keys; unused)
-  int32_t pad;
+  uint32_t rank_tail;           // vertices whose input-pair count reaches the rank sort's clamp
+  uint32_t rank_err;            // the clamped vertices outnumbered the fix-up sort (cannot happen within its bound)
 };
 static_assert(sizeof(CompactSizes) + 8 <= kHostErrOffset, "the compact build's sizes must fit the landing slot");
 

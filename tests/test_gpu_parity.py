@@ -279,7 +279,23 @@ def _repeat_heavy_pairs():
     return src[perm], dst[perm], n
 
 
+def _counts_past_the_clamp():
+    """Six vertices whose input-pair counts pass 65535, each a different amount (the rank sort clamps counts there
+    and orders those vertices afterwards), among random pairs."""
+    rng = np.random.default_rng(2200)
+    n = 20000
+    s, d = [], []
+    for k in range(6):
+        reps = 66000 + 997 * (5 - k)
+        s.append(np.full(reps, 100 + 7 * k))
+        d.append(rng.integers(0, n, reps))
+    s.append(rng.integers(0, n, 50000))
+    d.append(rng.integers(0, n, 50000))
+    return np.concatenate(s).astype(np.int32), np.concatenate(d).astype(np.int32), n
+
+
 CSR_CASES = [("rmat13", lambda: (*graphgen.rmat(13, 12, 21).edges(), 1 << 13)),
+             ("counts_past_clamp", _counts_past_the_clamp),
              ("rmat16p", lambda: (*graphgen.rmat(16, 8, 23, n=60000, permute=True).edges(), 60000)),
              ("repeat_heavy", _repeat_heavy_pairs),
              ("er_sparse", lambda: (*graphgen.er(30000, 20000, 22).edges(), 30000))]
