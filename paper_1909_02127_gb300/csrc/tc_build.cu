@@ -396,6 +396,36 @@ __global__ void k_rank(const uint64_t* __restrict__ sorted, int64_t n, int B, in
   }
 }
 
+// k_rank with the bucket starts claimed instead of scanned: each warp's 32 consecutive ranks get adjacent rooms
+// (a warp scan of their input-pair counts) at an offset claimed with one atomic add, so rooms follow the claims,
+// not the ranks, and no scan or cursor copy is needed.  pstart and cur receive each rank's room.
+__global__ void k_rank_buckets(const uint64_t* __restrict__ sorted, int64_t n, int B, int32_t* __restrict__ rank,
+                               int32_t* __restrict__ perm, int64_t* __restrict__ pstart, int64_t* __restrict__ cur,
+                               unsigned long long* __restrict__ alloc) {
+  const uint64_t mask = (1ull << B) - 1ull;
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = base + threadIdx.x;  // warp-uniform trip count
+    unsigned long long c = 0;
+    int32_t id = 0;
+    if (r < n) {
+      const uint64_t k = sorted[r];
+      id = (int32_t)(k & mask);
+      c = k >> B;
+      rank[id] = (int32_t)r;
+      perm[r] = id;
+    }
+    const unsigned long long incl = warp_inclusive_scan(c);
+    unsigned long long room = 0;
+    if (lane == 31 && incl) room = atomicAdd(alloc, incl);
+    room = __shfl_sync(kFull, room, 31) + incl - c;
+    if (r < n) {
+      pstart[r] = (int64_t)room;
+      cur[r] = (int64_t)room;
+    }
+  }
+}
+
 // Pair keys (lo << B) | hi (or the sentinel) -> (min rank << B) | max rank (the sentinel stays).
 __global__ void k_relabel(const uint64_t* __restrict__ keys, int64_t len, int B, const int32_t* __restrict__ rank,
                           uint64_t* __restrict__ okeys) {
@@ -1452,7 +1482,7 @@ namespace {
 struct CompactScratch {
   CompactSizes* sizes;
   uint64_t *rkeys, *rkeys_alt;
-  int32_t *rank, *rcount, *tgt, *odeg, *lists, *plen, *dnq;
+  int32_t *rank, *tgt, *odeg, *lists, *plen, *dnq;
   int64_t *pstart, *cur, *dqoff;
   int2* rowinfo;
   void *scan_tmp, *sort_tmp;
@@ -1464,7 +1494,6 @@ CompactScratch compact_scratch(Arena& ar, int64_t n, int64_t M, int64_t wn) {
   c.rkeys = ar.take<uint64_t>(n);
   c.rkeys_alt = ar.take<uint64_t>(n);
   c.rank = ar.take<int32_t>(n);
-  c.rcount = ar.take<int32_t>(n);
   c.pstart = ar.take<int64_t>(n + 1);
   c.cur = ar.take<int64_t>(n);
   c.tgt = ar.take<int32_t>(2 * M);
@@ -1546,13 +1575,11 @@ tc_status build_graph_compact(tc_graph* g, cudaStream_t s) {
       if ((st = launched("k_rank_keys"))) break;
       if ((st = radix_sort_u64(a, c.rkeys, c.rkeys_alt, n, B, B + count_bits, &rs, s, c.sort_tmp))) break;
     }
-    k_rank<<<grid_for(n, 256), 256, 0, s>>>(rs, n, B, c.rank, g->perm.as<int32_t>(), c.rcount);
-    if ((st = launched("k_rank"))) break;
+    // ranks, and each rank's bucket room (claimed, so no scan)
+    k_rank_buckets<<<grid_for(n, 256), 256, 0, s>>>(rs, n, B, c.rank, g->perm.as<int32_t>(), c.pstart, c.cur,
+                                                    &ds->bucket_alloc);
+    if ((st = launched("k_rank_buckets"))) break;
     // ---- buckets: group by the lower-ranked endpoint, sort and de-duplicate each ----
-    if ((st = exclusive_scan_i32_to_i64(a, c.rcount, c.pstart, n, s, c.scan_tmp))) break;
-    if ((st = cuda_status(cudaMemcpyAsync(c.cur, c.pstart, (size_t)n * 8, cudaMemcpyDeviceToDevice, s),
-                          "copy cursors")))
-      break;
     k_bucket<<<grid_for((M + kBucketItems - 1) / kBucketItems, 256), 256, 0, s>>>(
         g->keys.as<uint64_t>(), M, B, c.rank, reinterpret_cast<unsigned long long*>(c.cur), c.tgt);
     if ((st = launched("k_bucket"))) break;

@@ -82,6 +82,7 @@ struct CompactSizes {
   int64_t entries;              // padded column entries: off[n]
   int64_t dquads;               // quads of the dense rows
   unsigned long long dense_rows;
+  unsigned long long bucket_alloc;  // bucket room claimed so far (compact builds place buckets by claim)
   uint32_t rank_tail;           // vertices whose input-pair count reaches the rank sort's clamp
   uint32_t rank_err;            // the clamped vertices outnumbered the fix-up sort (cannot happen within its bound)
 };
