@@ -1022,6 +1022,110 @@ __global__ void k_dense_fill(const int64_t* __restrict__ off, const int32_t* __r
   }
 }
 
+// ---- the CSR's tail with one scan (compact builds) --------------------------------------------------------------
+// Per vertex from d+(v): sizes[v] = (padded length << 32) | dense quads, its row code (the rules of k_padded_len and
+// k_dense_select), and its dense quads by window position.  Summed over the vertices, the low half stays below 2^32
+// and never carries into the high one, so one scan gives both the offsets and the dense rows' first quads.
+__global__ void k_row_codes(const int32_t* __restrict__ dplus, int64_t n, int32_t base_w, int32_t wtopq,
+                            uint64_t* __restrict__ sizes, int32_t* __restrict__ nq, int2* __restrict__ rowinfo) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t d = dplus[v];
+    const int32_t pl = (d + 3) & ~3;
+    int32_t code = pl, q = 0;
+    if (v >= base_w) {
+      const int32_t wq = wtopq - (int32_t)((v + 1 - base_w) >> 7);
+      if (d >= kDenseMinDegree && 4 * (int64_t)wq <= d) q = wq;
+      nq[v - base_w] = q;
+      if (q) code = -q;
+    }
+    sizes[v] = ((uint64_t)(uint32_t)pl << 32) | (uint32_t)q;
+    rowinfo[v] = make_int2(d, code);
+  }
+}
+
+// k_rows_copy from the scanned sizes: each source's offset and dense-row start are unpacked (off, dq0) as its row is
+// copied; the first thread also writes off[n], the spare quad and the totals.
+__global__ void k_rows_copy_scanned(const int64_t* __restrict__ pstart, const int32_t* __restrict__ tgt,
+                                    const int32_t* __restrict__ d, const uint64_t* __restrict__ psz, int64_t n,
+                                    int32_t base_w, int64_t* __restrict__ off, int32_t* __restrict__ col,
+                                    int32_t* __restrict__ dq0, CompactSizes* __restrict__ sizes) {
+  const int lane = threadIdx.x & 31;
+  const int32_t pad = (int32_t)n;
+  if (blockIdx.x == 0 && threadIdx.x < 4) {
+    const uint64_t t = psz[n];
+    const int64_t e = (int64_t)(t >> 32);
+    col[e + threadIdx.x] = pad;
+    if (threadIdx.x == 0) {
+      off[n] = e;
+      sizes->entries = e;
+      sizes->dquads = (int64_t)(uint32_t)t;
+    }
+  }
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long drows = 0;
+  for (int64_t base = warp0 * 32; base < n; base += nwarps * 32) {
+    const int64_t sidx = base + lane;
+    int64_t ps = 0, o = 0;
+    int32_t dd = 0, pl = 0;
+    if (sidx < n) {
+      const uint64_t a = psz[sidx], b = psz[sidx + 1];
+      ps = pstart[sidx];
+      o = (int64_t)(a >> 32);
+      dd = d[sidx];
+      pl = (int32_t)((b >> 32) - (a >> 32));
+      off[sidx] = o;
+      if (sidx >= base_w) {
+        const bool dense = (uint32_t)b != (uint32_t)a;
+        dq0[sidx - base_w] = dense ? (int32_t)(uint32_t)a : -1;
+        drows += dense ? 1 : 0;
+      }
+    }
+    if (pl == 4) {
+      int4 q = make_int4(pad, pad, pad, pad);
+      q.x = tgt[ps];
+      if (dd > 1) q.y = tgt[ps + 1];
+      if (dd > 2) q.z = tgt[ps + 2];
+      if (dd > 3) q.w = tgt[ps + 3];
+      *reinterpret_cast<int4*>(col + o) = q;
+    }
+    // rows of two to eight quads, four at a time: their loads are issued together before any store waits on them
+    unsigned todo = __ballot_sync(kFull, pl > 4 && pl <= 32);
+    while (todo) {
+      int32_t v[4], rpl[4];
+      int64_t ro[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        rpl[r] = 0;
+        ro[r] = 0;
+        v[r] = pad;
+        if (todo) {
+          const int k = __ffs(todo) - 1;
+          todo &= todo - 1;
+          const int64_t rps = __shfl_sync(kFull, ps, k);
+          ro[r] = __shfl_sync(kFull, o, k);
+          const int32_t rd = __shfl_sync(kFull, dd, k);
+          rpl[r] = __shfl_sync(kFull, pl, k);
+          if (lane < rd) v[r] = tgt[rps + lane];
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (lane < rpl[r]) col[ro[r] + lane] = v[r];
+    }
+    todo = __ballot_sync(kFull, pl > 32);
+    while (todo) {
+      const int k = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int64_t rps = __shfl_sync(kFull, ps, k), ro = __shfl_sync(kFull, o, k);
+      const int32_t rd = __shfl_sync(kFull, dd, k), rpl = __shfl_sync(kFull, pl, k);
+      for (int32_t j = lane; j < rpl; j += 32) col[ro + j] = j < rd ? tgt[rps + j] : pad;
+    }
+  }
+  drows = warp_sum(drows);
+  if (lane == 0 && drows) atomicAdd(&sizes->dense_rows, drows);
+}
+
 // Scatter of counts from rank space back to original ids.
 __global__ void k_unpermute(const unsigned long long* __restrict__ by_rank, const int32_t* __restrict__ perm,
                             int64_t n, unsigned long long* __restrict__ by_id) {
@@ -1482,8 +1586,9 @@ namespace {
 struct CompactScratch {
   CompactSizes* sizes;
   uint64_t *rkeys, *rkeys_alt;
-  int32_t *rank, *tgt, *odeg, *lists, *plen, *dnq;
-  int64_t *pstart, *cur, *dqoff;
+  int32_t *rank, *tgt, *odeg, *lists, *dnq;
+  int64_t *pstart, *cur;
+  uint64_t* psz;  // [n + 1] (padded length << 32) | dense quads, scanned in place
   int2* rowinfo;
   void *scan_tmp, *sort_tmp;
 };
@@ -1499,10 +1604,9 @@ CompactScratch compact_scratch(Arena& ar, int64_t n, int64_t M, int64_t wn) {
   c.tgt = ar.take<int32_t>(2 * M);
   c.odeg = ar.take<int32_t>(n);
   c.lists = ar.take<int32_t>(n);
-  c.plen = ar.take<int32_t>(n);
+  c.psz = ar.take<uint64_t>(n + 1);
   c.rowinfo = ar.take<int2>(n);
   c.dnq = ar.take<int32_t>(wn > 0 ? wn : 1);
-  c.dqoff = ar.take<int64_t>(wn + 1);
   c.scan_tmp = ar.take<char>(scan_temp_bytes(n > wn ? n : wn));
   c.sort_tmp = ar.take<char>(radix_temp_bytes(n));
   return c;
@@ -1543,6 +1647,9 @@ tc_status build_graph_compact(tc_graph* g, cudaStream_t s) {
   while ((2 * M) / mid_max > (int64_t)kBigBits) mid_max <<= 1;
   const int64_t bound_entries = M + 3 * (n < M ? n : M);
   const int64_t bound_quads = M / 4 + 1;
+  // the offsets and dense quads are scanned as the two 32-bit halves of one word
+  if (bound_entries + 4 >= (int64_t(1) << 32) || bound_quads >= (int64_t(1) << 32))
+    return build_graph_pruned(g, -1, nullptr, s);
   const int64_t base_w = tc_graph::window_base(n, kWarpBitmapBits);
   const int64_t wn = n - base_w;
   Buf scratch;
@@ -1592,21 +1699,15 @@ tc_status build_graph_compact(tc_graph* g, cudaStream_t s) {
     if ((st = smem_attribute_once<k_rows_block>((int)blk_smem))) break;
     k_rows_block<<<num_sms(), kBigThreads, blk_smem, s>>>(c.pstart, c.cur, n, mid_max, c.tgt, c.odeg, c.lists, rc);
     if ((st = launched("k_rows_block"))) break;
-    // ---- CSR: padded offsets, then the rows ----
-    k_padded_len<<<grid_for(n, 256), 256, 0, s>>>(c.odeg, n, c.plen);
-    if ((st = launched("k_padded_len"))) break;
-    if ((st = exclusive_scan_i32_to_i64(a, c.plen, g->off.as<int64_t>(), n, s, c.scan_tmp))) break;
-    k_rows_copy<<<grid_for(n, 256), 256, 0, s>>>(c.pstart, c.tgt, c.odeg, g->off.as<int64_t>(), n,
-                                                 g->col.as<int32_t>(), (int32_t)n, &ds->entries);
-    if ((st = launched("k_rows_copy"))) break;
-    // ---- dense rows: selection and quad offsets ----
+    // ---- row codes, then one scan of (padded length << 32) | dense quads, then the rows with their offsets ----
     const int32_t wtopq = n > base_w ? (int32_t)(((n - 1 - base_w) >> 7) + 1) : 0;
-    k_dense_select<<<grid_for(n, 256), 256, 0, s>>>(c.odeg, n, (int32_t)base_w, wtopq, c.dnq, c.rowinfo);
-    if ((st = launched("k_dense_select"))) break;
-    if ((st = exclusive_scan_i32_to_i64(a, c.dnq, c.dqoff, wn, s, c.scan_tmp))) break;
-    k_dense_index<<<grid_for(wn, 256), 256, 0, s>>>(c.dnq, c.dqoff, wn, g->dq0.as<int32_t>(), &ds->dense_rows,
-                                                    &ds->dquads);
-    if ((st = launched("k_dense_index"))) break;
+    k_row_codes<<<grid_for(n, 256), 256, 0, s>>>(c.odeg, n, (int32_t)base_w, wtopq, c.psz, c.dnq, c.rowinfo);
+    if ((st = launched("k_row_codes"))) break;
+    if ((st = exclusive_scan_u64(a, c.psz, c.psz, n, s, c.scan_tmp))) break;
+    k_rows_copy_scanned<<<grid_for(n, 256), 256, 0, s>>>(c.pstart, c.tgt, c.odeg, c.psz, n, (int32_t)base_w,
+                                                         g->off.as<int64_t>(), g->col.as<int32_t>(),
+                                                         g->dq0.as<int32_t>(), ds);
+    if ((st = launched("k_rows_copy_scanned"))) break;
     // ---- bins ----
     k_bins<<<grid_for(n, 256), 256, 0, s>>>(g->off.as<int64_t>(), g->col.as<int32_t>(), c.rowinfo, n,
                                             block_min_work_for(M), g->list.as<int32_t>(), g->tlist.as<int32_t>(),

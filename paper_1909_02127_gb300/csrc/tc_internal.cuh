@@ -143,6 +143,9 @@ tc_status exclusive_scan_i32_to_i64(const Allocator& a, const int32_t* in, int64
                                     void* tmp = nullptr);
 // Exclusive scan of n uint32 values in place; *total (device, may be null) receives the sum.
 tc_status exclusive_scan_u32(const Allocator& a, uint32_t* data, int64_t n, cudaStream_t s, void* tmp = nullptr);
+// out[0..n] = exclusive scan of in[0..n), out[n] = the total.
+tc_status exclusive_scan_u64(const Allocator& a, const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t s,
+                             void* tmp = nullptr);
 // Scratch bytes of a scan of n elements (partial sums of every level; 8-byte elements, enough for both scans).
 size_t scan_temp_bytes(int64_t n);
 // Scratch bytes of radix_sort_u64 over n keys (tile histograms and their scan).

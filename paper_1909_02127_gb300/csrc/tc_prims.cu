@@ -216,6 +216,11 @@ tc_status exclusive_scan_i32_to_i64(const Allocator& a, const int32_t* in, int64
   return scan_rec<int32_t, int64_t>(a, in, out, n, out + n, s, tmp);
 }
 
+tc_status exclusive_scan_u64(const Allocator& a, const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t s,
+                             void* tmp) {
+  return scan_rec<uint64_t, uint64_t>(a, in, out, n, out + n, s, tmp);
+}
+
 tc_status exclusive_scan_u32(const Allocator& a, uint32_t* data, int64_t n, cudaStream_t s, void* tmp) {
   return scan_rec<uint32_t, uint32_t>(a, data, data, n, nullptr, s, tmp);
 }
