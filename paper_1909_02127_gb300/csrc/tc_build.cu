@@ -563,26 +563,47 @@ __global__ void k_rows_small(const int64_t* __restrict__ pstart, const int64_t* 
     if (to_warp) lists[pw + __popc(mw & lt)] = (int32_t)sidx;
     if (to_block) lists[n - 1 - (pb + __popc(mb & lt))] = (int32_t)sidx;
     int32_t dd = L <= 1 ? L : 0;  // a bucket of one pair is sorted and distinct
+    // buckets of 2..32 pairs, four at a time: their loads issued together, their sorting networks interleaved
     unsigned todo = __ballot_sync(kFull, L >= 2 && L <= kSmallRow);
     while (todo) {
-      const int k = __ffs(todo) - 1;
-      todo &= todo - 1;
-      const int64_t rps = __shfl_sync(kFull, ps, k);
-      const int32_t rl = __shfl_sync(kFull, L, k);
-      int32_t x = lane < rl ? tgt[rps + lane] : INT_MAX;
+      int32_t x[4], rl[4], rk[4];
+      int64_t rps[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        rl[r] = 0;
+        rk[r] = -1;
+        rps[r] = 0;
+        x[r] = INT_MAX;
+        if (todo) {
+          rk[r] = __ffs(todo) - 1;
+          todo &= todo - 1;
+          rps[r] = __shfl_sync(kFull, ps, rk[r]);
+          rl[r] = __shfl_sync(kFull, L, rk[r]);
+          if (lane < rl[r]) x[r] = tgt[rps[r] + lane];
+        }
+      }
 #pragma unroll
       for (int kk = 2; kk <= 32; kk <<= 1) {
 #pragma unroll
         for (int j = kk >> 1; j > 0; j >>= 1) {
-          const int32_t y = __shfl_xor_sync(kFull, x, j);
-          x = (((lane & j) == 0) == ((lane & kk) == 0)) ? min(x, y) : max(x, y);
+          const bool lower = ((lane & j) == 0) == ((lane & kk) == 0);
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int32_t y = __shfl_xor_sync(kFull, x[r], j);
+            x[r] = lower ? min(x[r], y) : max(x[r], y);
+          }
         }
       }
-      const int32_t prev = __shfl_up_sync(kFull, x, 1);
-      const bool keep = x != INT_MAX && (lane == 0 || x != prev);
-      const unsigned km = __ballot_sync(kFull, keep);
-      if (keep) tgt[rps + __popc(km & lt)] = x;
-      if (lane == k) dd = __popc(km);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int32_t prev = __shfl_up_sync(kFull, x[r], 1);
+        const bool keep = x[r] != INT_MAX && (lane == 0 || x[r] != prev);
+        const unsigned km = __ballot_sync(kFull, keep);
+        if (rl[r] > 0) {
+          if (keep) tgt[rps[r] + __popc(km & lt)] = x[r];
+          if (lane == rk[r]) dd = __popc(km);
+        }
+      }
     }
     if (sidx < n && L <= kSmallRow) {
       d[sidx] = dd;
