@@ -402,6 +402,12 @@ typedef struct tc_tuning {
                                                           path runs as one cooperative kernel launch, its steps
                                                           separated by grid-wide barriers, instead of about 25
                                                           launches.  0: never.  >= 0 */
+  int64_t vertex_plain_max_edges;                      /* tc_count_per_vertex adds to its per-block counters of the
+                                                          top ranks without reading them back for graphs of at most
+                                                          this many edges: a source u adds at most d+(u) to one
+                                                          counter as the middle vertex and d+(u) as the last, 2m in
+                                                          all, so below 2^31 edges no counter reaches 2^32.  Above
+                                                          it every add checks its counter.  0 <= this < 2^31 */
 } tc_tuning;
 
 /* tc_set_tuning — replace the table (TC_ERR_INVALID_ARG if malformed).  Applies to graphs built afterwards. */

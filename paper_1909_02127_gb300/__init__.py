@@ -47,6 +47,7 @@ class tc_graph_info(ctypes.Structure):
 TC_TUNING_MAX_CLASSES = 16
 TINY_MAX_VERTICES = 1 << 14          # the one-launch build: at most this many vertices
 TINY_MAX_PAIRS = (1 << 18) - 1       # and fewer than 2^18 input pairs
+VERTEX_PLAIN_MAX_EDGES = (1 << 31) - 1  # per-vertex counters without read-back up to this many edges
 
 
 class tc_tuning(ctypes.Structure):
@@ -56,7 +57,7 @@ class tc_tuning(ctypes.Structure):
                 ("block_min_work", ctypes.c_int64 * TC_TUNING_MAX_CLASSES),
                 ("isect_max_wedges_milli", ctypes.c_int64), ("bucket_max_pairs", ctypes.c_int64),
                 ("compact_max_pairs", ctypes.c_int64), ("stage_min_csr_bytes", ctypes.c_int64),
-                ("tiny_max_pairs", ctypes.c_int64)]
+                ("tiny_max_pairs", ctypes.c_int64), ("vertex_plain_max_edges", ctypes.c_int64)]
 
 
 class tc_server_config(ctypes.Structure):
@@ -192,7 +193,7 @@ def _apply_tuning_file(lib, path: str = TUNING_FILE) -> bool:
                            data.get("bucket_max_pairs", cur.bucket_max_pairs),
                            data.get("compact_max_pairs", cur.compact_max_pairs),
                            data.get("stage_min_csr_bytes", cur.stage_min_csr_bytes),
-                           data.get("tiny_max_pairs", cur.tiny_max_pairs))
+                           data.get("tiny_max_pairs", cur.tiny_max_pairs), cur.vertex_plain_max_edges)
         return lib.tc_set_tuning(ctypes.byref(t)) == TC_OK
     except Exception:
         return False
@@ -200,7 +201,8 @@ def _apply_tuning_file(lib, path: str = TUNING_FILE) -> bool:
 
 def _tuning_struct(classes, batch_warp_max_edges: int = 1 << 25, isect_max_wedges_milli: int = 0,
                    bucket_max_pairs: int = 1 << 29, compact_max_pairs: int = 1 << 25,
-                   stage_min_csr_bytes: int = 4 << 30, tiny_max_pairs: int = TINY_MAX_PAIRS) -> "tc_tuning":
+                   stage_min_csr_bytes: int = 4 << 30, tiny_max_pairs: int = TINY_MAX_PAIRS,
+                   vertex_plain_max_edges: int = VERTEX_PLAIN_MAX_EDGES) -> "tc_tuning":
     t = tc_tuning()
     t.num_classes = len(classes)
     t.batch_warp_max_edges = int(batch_warp_max_edges)
@@ -209,6 +211,7 @@ def _tuning_struct(classes, batch_warp_max_edges: int = 1 << 25, isect_max_wedge
     t.compact_max_pairs = int(compact_max_pairs)
     t.stage_min_csr_bytes = int(stage_min_csr_bytes)
     t.tiny_max_pairs = int(tiny_max_pairs)
+    t.vertex_plain_max_edges = int(vertex_plain_max_edges)
     for i, (max_edges, work) in enumerate(classes):
         t.class_max_edges[i] = int(max_edges)
         t.block_min_work[i] = int(work)
@@ -218,10 +221,10 @@ def _tuning_struct(classes, batch_warp_max_edges: int = 1 << 25, isect_max_wedge
 def tc_set_tuning(classes, batch_warp_max_edges: Optional[int] = None,
                   isect_max_wedges_milli: Optional[int] = None, bucket_max_pairs: Optional[int] = None,
                   compact_max_pairs: Optional[int] = None, stage_min_csr_bytes: Optional[int] = None,
-                  tiny_max_pairs: Optional[int] = None) -> None:
+                  tiny_max_pairs: Optional[int] = None, vertex_plain_max_edges: Optional[int] = None) -> None:
     """classes: [(max_edges, block_min_work), ...] with ascending max_edges; batch_warp_max_edges,
-    isect_max_wedges_milli, bucket_max_pairs, compact_max_pairs, stage_min_csr_bytes and tiny_max_pairs: keep the
-    current values if None."""
+    isect_max_wedges_milli, bucket_max_pairs, compact_max_pairs, stage_min_csr_bytes, tiny_max_pairs and
+    vertex_plain_max_edges: keep the current values if None."""
     if not 1 <= len(classes) <= TC_TUNING_MAX_CLASSES:
         raise ValueError("1..16 classes")
     cur = tc_tuning()
@@ -238,8 +241,10 @@ def tc_set_tuning(classes, batch_warp_max_edges: Optional[int] = None,
         stage_min_csr_bytes = cur.stage_min_csr_bytes
     if tiny_max_pairs is None:
         tiny_max_pairs = cur.tiny_max_pairs
+    if vertex_plain_max_edges is None:
+        vertex_plain_max_edges = cur.vertex_plain_max_edges
     t = _tuning_struct(classes, batch_warp_max_edges, isect_max_wedges_milli, bucket_max_pairs, compact_max_pairs,
-                       stage_min_csr_bytes, tiny_max_pairs)
+                       stage_min_csr_bytes, tiny_max_pairs, vertex_plain_max_edges)
     _check(load_library().tc_set_tuning(ctypes.byref(t)))
 
 
@@ -259,6 +264,12 @@ def tc_get_tiny_max_pairs() -> int:
     t = tc_tuning()
     _check(load_library().tc_get_tuning(ctypes.byref(t)))
     return int(t.tiny_max_pairs)
+
+
+def tc_get_vertex_plain_max_edges() -> int:
+    t = tc_tuning()
+    _check(load_library().tc_get_tuning(ctypes.byref(t)))
+    return int(t.vertex_plain_max_edges)
 
 
 def tc_get_compact_max_pairs() -> int:

@@ -63,6 +63,7 @@ tc_tuning g_tuning = [] {
   // measured: staged long rows 1.5% faster at R-MAT 26 (5 GB CSR), 2-7% slower at R-MAT 20-24 (up to 1.2 GB)
   t.stage_min_csr_bytes = int64_t(4) << 30;
   t.tiny_max_pairs = kTinyMaxPairs;
+  t.vertex_plain_max_edges = kVertexPlainMaxEdges;
   return t;
 }();
 }  // namespace
@@ -96,6 +97,11 @@ int64_t compact_max_pairs() {
 int64_t tiny_max_pairs() {
   std::lock_guard<std::mutex> lk(g_tuning_mutex);
   return g_tuning.tiny_max_pairs;
+}
+
+int64_t vertex_plain_max_edges() {
+  std::lock_guard<std::mutex> lk(g_tuning_mutex);
+  return g_tuning.vertex_plain_max_edges;
 }
 
 bool use_buckets(int64_t pairs) {
@@ -325,6 +331,10 @@ TC_API tc_status tc_set_tuning(const tc_tuning* t) {
       t->stage_min_csr_bytes < 0 || t->tiny_max_pairs < 0) {
     set_error("tc_set_tuning: isect_max_wedges_milli, bucket_max_pairs, compact_max_pairs, stage_min_csr_bytes and "
               "tiny_max_pairs must be >= 0");
+    return TC_ERR_INVALID_ARG;
+  }
+  if (t->vertex_plain_max_edges < 0 || t->vertex_plain_max_edges > kVertexPlainMaxEdges) {
+    set_error("tc_set_tuning: vertex_plain_max_edges must be in [0, 2^31 - 1]");
     return TC_ERR_INVALID_ARG;
   }
   for (int i = 0; i < t->num_classes; ++i) {

@@ -17,7 +17,7 @@ __global__ void __launch_bounds__(kCountThreads, 2)
   __shared__ unsigned long long red[kWarpsPerCTA];
   __shared__ int s_idx;
   int nhub = 0;
-  if (MODE == dev::kModeVertex) {  // zeroed hub counters after the counting layout
+  if (dev::is_vertex(MODE)) {  // zeroed hub counters after the counting layout
     sk.hub = smem + dev::kCountSmem / 4;
     sk.hub0 = g.n > dev::kHubRanks ? (int32_t)(g.n - dev::kHubRanks) : 0;
     nhub = (int)(g.n - sk.hub0);
@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(kCountThreads, 2)
     for (int w = 0; w < kWarpsPerCTA; ++w) s += red[w];
     if (s) atomicAdd(total, s);
   }
-  if (MODE == dev::kModeVertex) {  // every add of this CTA is in (the barrier above)
+  if (dev::is_vertex(MODE)) {  // every add of this CTA is in (the barrier above)
     for (int i = threadIdx.x; i < nhub; i += kCountThreads) {
       const uint32_t c = sk.hub[i];
       if (c) atomicAdd(&sk.pv[sk.hub0 + i], (unsigned long long)c);
@@ -62,10 +62,15 @@ tc_status launch_count(const tc_graph* g, uint64_t* d_total, uint64_t* d_per_ver
   if (!adjacent) TC_CUDA(cudaMemsetAsync(d_cursors, 0, 3 * sizeof(uint32_t), s));
   const int grid = count_grid(g);
   dev::Sink sk;
-  if (d_per_vertex) {
+  if (d_per_vertex && g->m <= vertex_plain_max_edges()) {  // no counter can reach 2^32: plain adds
     sk.pv = (unsigned long long*)d_per_vertex;
     TC_TRY((smem_attribute_once<k_count<dev::kModeVertex, false>>(dev::kVertexSmem)));
     k_count<dev::kModeVertex, false><<<grid, kCountThreads, dev::kVertexSmem, s>>>(
+        g->view(), (unsigned long long*)d_total, sk, d_cursors);
+  } else if (d_per_vertex) {
+    sk.pv = (unsigned long long*)d_per_vertex;
+    TC_TRY((smem_attribute_once<k_count<dev::kModeVertexChecked, false>>(dev::kVertexSmem)));
+    k_count<dev::kModeVertexChecked, false><<<grid, kCountThreads, dev::kVertexSmem, s>>>(
         g->view(), (unsigned long long*)d_total, sk, d_cursors);
   } else if (use_staged_rows(g)) {  // CSR beyond L2: long hop-2 rows staged through shared memory
     TC_TRY((smem_attribute_once<k_count<dev::kModeCount, true>>(dev::kCountStagedSmem)));

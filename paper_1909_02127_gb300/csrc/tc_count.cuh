@@ -87,11 +87,13 @@ __device__ __forceinline__ void low_insert(const int32_t* __restrict__ row, int 
   }
 }
 
-// What a closed 2-path produces besides the count.
-enum Mode { kModeCount = 0, kModeVertex = 1, kModeList = 2 };
+// What a closed 2-path produces besides the count.  The two per-vertex modes differ only in how they add to the
+// per-CTA counters of the top ranks (vertex_add).
+enum Mode { kModeCount = 0, kModeVertex = 1, kModeList = 2, kModeVertexChecked = 3 };
+__host__ __device__ constexpr bool is_vertex(int mode) { return mode == kModeVertex || mode == kModeVertexChecked; }
 
 struct Sink {
-  unsigned long long* pv = nullptr;      // kModeVertex: t(x) in rank space
+  unsigned long long* pv = nullptr;      // per-vertex modes: t(x) in rank space
   int32_t* tri = nullptr;                // kModeList: triples of original ids, 3 per triangle
   unsigned long long* slot = nullptr;    // kModeList: the next output position of this source (shared memory;
                                          // one per warp, or one per CTA in block mode), advanced atomically
@@ -99,30 +101,42 @@ struct Sink {
   const int32_t* perm = nullptr;         // kModeList: rank -> original id
   int32_t u = 0;                         // kModeList: the current source
   int32_t pu = 0;                        // kModeList: its original id
-  uint32_t* hub = nullptr;               // kModeVertex: this CTA's counters of t(x), x in [hub0, n) (shared memory)
-  int32_t hub0 = 0;
+  uint32_t* hub = nullptr;               // per-vertex modes: this CTA's counters of t(x), x in [hub0, n) (shared
+  int32_t hub0 = 0;                      // memory)
 };
 
-// kModeVertex: per-CTA shared-memory counters for the top kHubRanks ranks.  Ranks follow the input-pair count, so
-// these are the vertices in the most triangles, whose global counters would otherwise take most of the atomics
+// Per-vertex modes: per-CTA shared-memory counters for the top kHubRanks ranks.  Ranks follow the input-pair count,
+// so these are the vertices in the most triangles, whose global counters would otherwise take most of the atomics
 // (on R-MAT 20 the top 5120 ranks take 81% of all t(x) increments).  20 KB per CTA keeps two CTAs on an SM.
 constexpr int kHubRanks = 5120;
 constexpr uint32_t kHubSpill = 1u << 31;
 
-// t(x) += k.  A top rank counts in the CTA's shared counter, which the kernel adds to pv when it ends; the add that
-// takes a counter to 2^31 moves 2^31 of it to pv at once, so no counter wraps.  Any other x adds to pv directly.
+// t(x) += k for x = v or w of closed 2-paths u->v->w (t(u) goes to pv directly, source_add).  A top rank counts in
+// the CTA's shared counter, which the kernel adds to pv when it ends; any other x adds to pv directly.
+//
+// A source u adds at most d+(u) to any one counter as v (the hits of row v are N+(u) ∩ N+(v)) and at most d+(u) as w
+// (the v in N+(u) whose row holds w), so over all sources no counter of any CTA takes more than 2m.  For m < 2^31
+// (kModeVertex) a counter therefore never reaches 2^32, and the add needs no read-back: a shared-memory add whose
+// old value is not returned is the cheaper instruction (R-MAT 20: per-vertex counting 7.1 -> 5.5 ms).  Otherwise
+// (kModeVertexChecked) the add that takes a counter to 2^31 moves 2^31 of it to pv at once, so no counter wraps.
+template <int MODE>
 __device__ __forceinline__ void vertex_add(const Sink& sk, int32_t x, uint32_t k) {
   const int32_t h = x - sk.hub0;
-  if (h >= 0) {
+  if (h < 0) {
+    atomicAdd(&sk.pv[x], (unsigned long long)k);
+  } else if (MODE == kModeVertex) {
+    atomicAdd(&sk.hub[h], k);
+  } else {
     const uint32_t old = atomicAdd(&sk.hub[h], k);
     if (old < kHubSpill && old + k >= kHubSpill) {
       atomicSub(&sk.hub[h], kHubSpill);
       atomicAdd(&sk.pv[x], (unsigned long long)kHubSpill);
     }
-  } else {
-    atomicAdd(&sk.pv[x], (unsigned long long)k);
   }
 }
+
+// t(u) += k for a source u (once per source, or once per warp of a CTA's source).
+__device__ __forceinline__ void source_add(const Sink& sk, int32_t u, unsigned long long k) { atomicAdd(&sk.pv[u], k); }
 
 // kModeList: triangle (u, v, w) as its sorted original ids at output position pos (nothing past the capacity).
 __device__ __forceinline__ void write_triple(const Sink& sk, unsigned long long pos, int32_t a, int32_t b,
@@ -222,11 +236,11 @@ __device__ __forceinline__ uint32_t list_bits(uint32_t m0, uint32_t m1, uint32_t
 template <int MODE, class C>
 __device__ __forceinline__ uint32_t test_quad(const int4 q, const C& c, const Sink& sk, int32_t v) {
   const uint32_t h0 = c(q.x), h1 = c(q.y), h2 = c(q.z), h3 = c(q.w);
-  if (MODE == kModeVertex) {  // t(w) here; the caller adds the row's hits to t(v)
-    if (h0) vertex_add(sk, q.x, 1u);
-    if (h1) vertex_add(sk, q.y, 1u);
-    if (h2) vertex_add(sk, q.z, 1u);
-    if (h3) vertex_add(sk, q.w, 1u);
+  if (is_vertex(MODE)) {  // t(w) here; the caller adds the row's hits to t(v)
+    if (h0) vertex_add<MODE>(sk, q.x, 1u);
+    if (h1) vertex_add<MODE>(sk, q.y, 1u);
+    if (h2) vertex_add<MODE>(sk, q.z, 1u);
+    if (h3) vertex_add<MODE>(sk, q.w, 1u);
     return (h0 + h1) + (h2 + h3);
   }
   if (MODE == kModeList) list_hits(q, h0, h1, h2, h3, sk, v);
@@ -258,9 +272,9 @@ __device__ __forceinline__ uint32_t long_row(const int4* __restrict__ col4, uint
       hits += test_quad<MODE>(a, c, sk, v);
     }
   }
-  if (MODE == kModeVertex) {
+  if (is_vertex(MODE)) {
     const uint32_t s = warp_sum(hits);
-    if (lane == 0 && s) vertex_add(sk, v, s);
+    if (lane == 0 && s) vertex_add<MODE>(sk, v, s);
   }
   return hits;
 }
@@ -306,9 +320,9 @@ __device__ __forceinline__ uint32_t long_row_staged(const int4* __restrict__ col
     hits += test_quad<MODE>(q, c, sk, v);
   }
   // every copy group left pending is empty (its step lies past the row)
-  if (MODE == kModeVertex) {
+  if (is_vertex(MODE)) {
     const uint32_t s = warp_sum(hits);
-    if (lane == 0 && s) vertex_add(sk, v, s);
+    if (lane == 0 && s) vertex_add<MODE>(sk, v, s);
   }
   return hits;
 }
@@ -355,7 +369,7 @@ __device__ __forceinline__ uint32_t walk(const Rows& r, int R, uint32_t x0, uint
       const int own = cur + __popc(starts & lt);
       const int4 q = __ldg(&col4[r.q0[own] + (x - r.P[own])]);
       const uint32_t h = test_quad<MODE>(q, c, sk, MODE != kModeCount ? r.v[own] : 0);
-      if (MODE == kModeVertex && h) vertex_add(sk, r.v[own], h);
+      if (is_vertex(MODE) && h) vertex_add<MODE>(sk, r.v[own], h);
       hits += h;
     }
     cur += __popc(starts);
@@ -452,12 +466,12 @@ __device__ __forceinline__ uint32_t dense_list_walk(const Rows& r, int R, uint32
   return hits;
 }
 
-// Is v's row also stored as a dense bitmap?  Returns its first quad or -1 (always -1 in per-vertex mode, which
-// walks the id rows: expanding the set bits of each AND into per-vertex adds measured twice as slow, 15.8 vs 7 ms at
-// R-MAT 20).
+// Is v's row also stored as a dense bitmap?  Returns its first quad or -1 (always -1 in the per-vertex modes, which
+// walk the id rows: expanding the set bits of each AND into per-vertex adds measured twice as slow, 15.8 vs 7 ms at
+// R-MAT 20, and 12.9 vs 5.5 ms with adds that return nothing).
 template <int MODE>
 __device__ __forceinline__ int32_t dense_row(const CsrView& g, int32_t v) {
-  if (MODE == kModeVertex || g.dq0 == nullptr || v < g.base_w || v >= g.n) return -1;
+  if (is_vertex(MODE) || g.dq0 == nullptr || v < g.base_w || v >= g.n) return -1;
   return __ldg(&g.dq0[v - g.base_w]);
 }
 
@@ -613,9 +627,9 @@ __device__ __forceinline__ uint32_t warp_source(int32_t u, const CsrView& g, uin
   __syncwarp();
   mark_row(row, len, g.n, g.base_w, bm, false, lane, 32);
   __syncwarp();
-  if (MODE == kModeVertex) {
+  if (is_vertex(MODE)) {
     const uint32_t s = warp_sum(hits);
-    if (lane == 0 && s) vertex_add(sk, u, s);
+    if (lane == 0 && s) source_add(sk, u, s);
   }
   return hits;
 }
@@ -651,7 +665,7 @@ __device__ __forceinline__ uint32_t block_hops(const CsrView& g, int64_t beg, in
     const uint32_t lrank = block_exclusive_scan<uint32_t>(is_long ? 1u : 0u, ws, &NL);
     const uint32_t srank = block_exclusive_scan<uint32_t>(is_short ? 1u : 0u, ws, &R);
     const uint32_t pre = block_exclusive_scan<uint32_t>(is_short ? ro.nq : 0u, ws, &Q);
-    if (MODE != kModeVertex) {
+    if (!is_vertex(MODE)) {
       const int32_t sq = dense ? (v + 1 - g.base_w) >> 7 : 0;
       const uint32_t nqd = dense ? (uint32_t)(g.wtopq - sq) : 0u;
       const uint32_t drank = block_exclusive_scan<uint32_t>(dense ? 1u : 0u, ws, &ND);
@@ -691,7 +705,7 @@ __device__ __forceinline__ uint32_t block_hops(const CsrView& g, int64_t beg, in
     const uint32_t per = (Q + kWarpsPerCTA - 1) / kWarpsPerCTA;
     const uint32_t x0 = min(Q, (uint32_t)warp * per), x1 = min(Q, x0 + per);
     hits += walk<MODE>(br.sr, (int)R, x0, x1, col4, c, sk, (int32_t)g.n);
-    if (MODE != kModeVertex && QD > 0) {  // dense rows: equal shares of their quads
+    if (!is_vertex(MODE) && QD > 0) {  // dense rows: equal shares of their quads
       const uint32_t dper = (QD + kWarpsPerCTA - 1) / kWarpsPerCTA;
       const uint32_t d0 = min(QD, (uint32_t)warp * dper), d1 = min(QD, d0 + dper);
       if (MODE == kModeCount)
@@ -735,9 +749,9 @@ __device__ __forceinline__ uint32_t block_source(int32_t u, const CsrView& g, ui
                             br, ws, sk, ring);
   }
   mark_row(row, len, g.n, g.base_b, bm, false, tid, kCountThreads);
-  if (MODE == kModeVertex) {
+  if (is_vertex(MODE)) {
     const uint32_t s = warp_sum(hits);
-    if (lane == 0 && s) vertex_add(sk, u, s);
+    if (lane == 0 && s) source_add(sk, u, s);
   }
   __syncthreads();
   return hits;
@@ -800,15 +814,15 @@ __device__ __forceinline__ uint32_t tiny_source(int32_t u, const CsrView& g, con
       }
       if (hit) {
         ++hits;
-        if (MODE == kModeVertex) {
-          vertex_add(sk, a, 1u);
-          vertex_add(sk, b, 1u);
+        if (is_vertex(MODE)) {
+          vertex_add<MODE>(sk, a, 1u);
+          vertex_add<MODE>(sk, b, 1u);
         }
         if (MODE == kModeList) write_triple(sk, pos++, pu, pa, b);
       }
     }
   }
-  if (MODE == kModeVertex && hits) vertex_add(sk, u, hits);
+  if (is_vertex(MODE) && hits) source_add(sk, u, hits);
   return hits;
 }
 
@@ -832,7 +846,7 @@ constexpr int kBlockStagedSmem = kBlockRingOffset + kWarpsPerCTA * kBlockRingByt
 constexpr int kCountStagedSmem = kBlockStagedSmem > kWarpStagedSmem ? kBlockStagedSmem : kWarpStagedSmem;
 // two CTAs per SM: dynamic + static (272 bytes in k_count) + the 1 KB the runtime reserves per CTA, within 228 KB
 static_assert(2 * (kCountStagedSmem + 512 + 1024) <= 228 * 1024, "staged counting must keep two CTAs per SM");
-constexpr int kVertexSmem = kCountSmem + kHubRanks * 4;  // kModeVertex: the hub counters follow
+constexpr int kVertexSmem = kCountSmem + kHubRanks * 4;  // per-vertex modes: the hub counters follow
 // two CTAs per SM: dynamic + static (< 1 KB) + the 1 KB the runtime reserves per CTA, within 228 KB
 static_assert(2 * (kVertexSmem + 2048) <= 228 * 1024, "vertex-mode counting must keep two CTAs per SM");
 

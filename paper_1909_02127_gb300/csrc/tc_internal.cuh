@@ -101,6 +101,10 @@ constexpr int kLongQuads = 16;                     // rows of >= 16 quads (64 id
 int64_t block_min_work_for(int64_t m);
 int64_t batch_warp_max_edges();
 int64_t stage_min_csr_bytes();
+// Per-vertex counting adds to its per-CTA counters without read-back for graphs of at most this many edges (the
+// tuning table; at most kVertexPlainMaxEdges, below which no counter can reach 2^32).
+constexpr int64_t kVertexPlainMaxEdges = (int64_t(1) << 31) - 1;
+int64_t vertex_plain_max_edges();
 
 // Per-graph view used by the counting kernels.  Vertices are relabelled by rank in the (input-pair count, id)
 // order, so every oriented edge goes from a lower to a higher id and rows hold ascending ids.  Rows start on

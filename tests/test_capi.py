@@ -134,8 +134,17 @@ def test_tuning_table_round_trip_without_gpu(lib):
         with pytest.raises(tc.TCError):
             tc.tc_set_tuning([(1 << 40, 1 << 15)], isect_max_wedges_milli=-1)
         tc.tc_set_tuning([(1 << 40, 1 << 15)], isect_max_wedges_milli=ratio)
+        # per-vertex counters without read-back: only below 2^31 edges, where no counter can reach 2^32
+        assert tc.tc_get_vertex_plain_max_edges() == tc.VERTEX_PLAIN_MAX_EDGES == (1 << 31) - 1
+        tc.tc_set_tuning(tc.tc_get_tuning(), vertex_plain_max_edges=0)
+        assert tc.tc_get_vertex_plain_max_edges() == 0
+        for bad in (-1, 1 << 31):
+            with pytest.raises(tc.TCError):
+                tc.tc_set_tuning(tc.tc_get_tuning(), vertex_plain_max_edges=bad)
+        assert tc.tc_get_vertex_plain_max_edges() == 0
+        tc.tc_set_tuning(tc.tc_get_tuning(), vertex_plain_max_edges=tc.VERTEX_PLAIN_MAX_EDGES)
     finally:
-        tc.tc_set_tuning(saved)
+        tc.tc_set_tuning(saved, vertex_plain_max_edges=tc.VERTEX_PLAIN_MAX_EDGES)
 
 
 class _FakeDeviceTensor:

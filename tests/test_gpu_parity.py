@@ -212,6 +212,24 @@ def test_medium_graphs(tc, spec):
     np.testing.assert_array_equal(gt, t)
 
 
+@pytest.mark.parametrize("spec", [graphgen.rmat(16, 16, 11), graphgen.rmat(17, 8, 12, n=100000, permute=True)],
+                         ids=["rmat16", "rmat17p"])
+def test_per_vertex_add_modes(tc, spec):
+    """Per-vertex counts with the per-block counters of the top ranks added to without read-back (graphs below 2^31
+    edges) and with every add checking its counter (forced here by a bound of 0 edges): both equal the oracle."""
+    hs, hd = spec.edges()
+    T, _, t = oracle.count(hs, hd, spec.n, per_vertex=True)
+    saved = tc.tc_get_tuning()
+    try:
+        for bound in (tc.VERTEX_PLAIN_MAX_EDGES, 0):
+            tc.tc_set_tuning(saved, vertex_plain_max_edges=bound)
+            got, gt, _ = gpu_counts(tc, hs, hd, spec.n)
+            assert got == T, bound
+            np.testing.assert_array_equal(gt, t)
+    finally:
+        tc.tc_set_tuning(saved, vertex_plain_max_edges=tc.VERTEX_PLAIN_MAX_EDGES)
+
+
 def test_rmat20_full(tc):
     """R-MAT scale 20, edge factor 16: the benchmark workload, counted in the benchmark's launch configuration
     (device-resident edges, one tc_count), every per-vertex count compared."""
@@ -249,10 +267,14 @@ def test_rmat20_full(tc):
             assert T2 == T
             np.testing.assert_array_equal(gt, t)
             assert int(tc.tc_count_batch([g])[0]) == T
+            tc.tc_set_tuning([(1 << 62, 1 << 13)], vertex_plain_max_edges=0)  # every counter add checked
+            T2, gt = tc.tc_count_per_vertex(g)
+            assert T2 == T
+            np.testing.assert_array_equal(gt, t)
         finally:
             tc.tc_free(g)
     finally:
-        tc.tc_set_tuning(saved)
+        tc.tc_set_tuning(saved, vertex_plain_max_edges=tc.VERTEX_PLAIN_MAX_EDGES)
 
 
 def _repeat_heavy_pairs():
