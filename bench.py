@@ -565,11 +565,12 @@ def sub_serve(args, dist: Dist) -> dict:
 
 
 def run_extras(args, dist: Dist, dev, stream, flush) -> dict:
-    """The sub-records of the default line: R-MAT 26, the 4096-graph batch, serving.  A failure is reported in its
-    record (and raised again when it is a count mismatch)."""
+    """The sub-records of the default line: R-MAT 26, per-vertex counts and listing on R-MAT 20, the 4096-graph batch,
+    serving.  A failure is reported in its record (and raised again when it is a count mismatch)."""
     import torch
     out = {}
     for name, fn in (("rmat26", lambda: sub_rmat26(args, dev, stream, flush)),
+                     ("modes", lambda: sub_modes(args, dev, stream, flush)),
                      ("batch", lambda: batch_measure(args, dist, 10, 3)),
                      ("serve", lambda: sub_serve(args, dist))):
         t0 = time.perf_counter()
@@ -723,6 +724,96 @@ def run_unfused(args, dist: Dist):
     }
 
 
+def check_listed(out, T: int, ds, dd, n: int, samples: int = 4096) -> None:
+    """Spot check of a listing: a sample of the listed triples are triangles of the input (ascending, distinct,
+    every pair an input edge)."""
+    import numpy as np
+    import torch
+    if T == 0:
+        return
+    sample = out[torch.randint(0, T, (samples,), device=out.device)].cpu().numpy()
+    hs, hd = ds.cpu().numpy().astype(np.int64), dd.cpu().numpy().astype(np.int64)
+    edges = np.unique(np.minimum(hs, hd) * n + np.maximum(hs, hd))
+    t = sample.astype(np.int64)
+
+    def present(x):
+        i = np.minimum(np.searchsorted(edges, x), edges.size - 1)
+        return edges[i] == x
+
+    ok = (t[:, 0] < t[:, 1]) & (t[:, 1] < t[:, 2])
+    ok &= present(t[:, 0] * n + t[:, 1]) & present(t[:, 1] * n + t[:, 2])
+    ok &= present(t[:, 0] * n + t[:, 2])
+    if not ok.all():
+        raise RuntimeError(f"listing differs: {int((~ok).sum())} sampled triples are not triangles")
+
+
+def sub_modes(args, dev, stream, flush, reps: int = 10) -> dict:
+    """The two other outputs of the traversal on the headline graph (R-MAT 20), built once: per-vertex counts t(x)
+    (tc_count_per_vertex into device memory; the sum of t must be 3T) and the listing of every triangle
+    (tc_list_triangles into device memory; the number found must be T, and sampled triples must be triangles),
+    each timed with CUDA events over `reps` calls after one untimed call, the L2 flushed before each."""
+    import ctypes
+
+    import torch
+
+    import graphgen
+    import paper_1909_02127_gb300 as tc
+
+    spec = graphgen.config("rmat20")
+    ds, dd = spec.edges(device=dev)
+    g = tc.tc_load_edges(ds, dd, spec.n, stream=stream)
+    try:
+        tc.tc_build(g, stream)
+        T = tc.tc_count(g, stream)
+        pv = torch.empty(spec.n, dtype=torch.int64, device=dev)
+
+        def timed(fn):
+            fn()
+            ms = []
+            for k in range(reps):
+                flush.fill_(k)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            return statistics.median(ms)
+
+        def per_vertex():
+            T2, _ = tc.tc_count_per_vertex(g, pv, stream)
+            if T2 != T:
+                raise RuntimeError(f"per-vertex total {T2} differs from the count {T}")
+
+        pv_ms = timed(per_vertex)
+        if int(pv.sum().item()) != 3 * T:
+            raise RuntimeError("per-vertex counts differ: their sum is not 3T")
+        del pv
+        out = torch.empty((max(T, 1), 3), dtype=torch.int32, device=dev)
+        lib = tc.load_library()
+        found = ctypes.c_uint64()
+        sp = ctypes.c_void_p(stream.cuda_stream)
+
+        def list_all():
+            st = lib.tc_list_triangles(g, 0, spec.n, out.data_ptr(), T, ctypes.byref(found), tc.TC_PTR_DEVICE, sp)
+            if st != tc.TC_OK:
+                raise RuntimeError(f"listing: status {st}")
+            if found.value != T:
+                raise RuntimeError(f"listing differs: found {found.value} of {T}")
+
+        list_ms = timed(list_all)
+        check_listed(out, T, ds, dd, spec.n)
+        del out
+    finally:
+        tc.tc_free(g)
+    return {"workload": spec.name, "triangles": T, "reps": reps, "per_vertex_ms": round(pv_ms, 4),
+            "list_ms": round(list_ms, 4), "list_triangles_per_s": round(T / (list_ms / 1e3), 1),
+            "list_output_bytes": 12 * T,
+            "note": "per-vertex: tc_count_per_vertex into device memory; listing: both passes of tc_list_triangles "
+                    "(ascending original-id triples into device memory); CUDA events, median, L2 flushed before "
+                    "each call"}
+
+
 def run_list(args, dist: Dist):
     """Triangle listing: every triangle of the graph written as ascending original-id triples into device memory
     (tc_list_triangles), timed with CUDA events; the count kernel on the same graph beside it."""
@@ -771,23 +862,7 @@ def run_list(args, dist: Dist):
     clock_info = clocks.stop()
     dist.barrier()
     launches = tc.tc_kernel_launches() - launches0
-    # spot check: a sample of the listed triples are triangles of the input (sorted, distinct, adjacent)
-    sample = out[torch.randint(0, max(T, 1), (4096,), device=dev)].cpu().numpy() if T else None
-    if sample is not None:
-        import numpy as np
-        hs, hd = ds.cpu().numpy().astype(np.int64), dd.cpu().numpy().astype(np.int64)
-        edges = np.unique(np.minimum(hs, hd) * spec.n + np.maximum(hs, hd))
-        t = sample.astype(np.int64)
-
-        def present(x):
-            i = np.minimum(np.searchsorted(edges, x), edges.size - 1)
-            return edges[i] == x
-
-        ok = (t[:, 0] < t[:, 1]) & (t[:, 1] < t[:, 2])
-        ok &= present(t[:, 0] * spec.n + t[:, 1]) & present(t[:, 1] * spec.n + t[:, 2])
-        ok &= present(t[:, 0] * spec.n + t[:, 2])
-        if not ok.all():
-            raise RuntimeError(f"listing: {int((~ok).sum())} sampled triples are not triangles")
+    check_listed(out, T, ds, dd, spec.n)
     count_ms = []
     d_total = torch.zeros(1, dtype=torch.int64, device=dev)
     for k in range(args.steps):

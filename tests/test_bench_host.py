@@ -62,3 +62,17 @@ def test_profiled_traffic_only_for_the_current_source(tmp_path, monkeypatch):
     assert bench.profiled_traffic("y") is None  # no summary
     (csrc / "tc_prims.cuh").write_text("// changed\n")
     assert bench.profiled_traffic("x") is None  # taken on another source
+
+
+def test_listing_spot_check():
+    """check_listed accepts the triangles of K4 and rejects a listed triple that is not a triangle of the input."""
+    import pytest
+    import torch
+    src = torch.tensor([0, 0, 0, 1, 1, 2], dtype=torch.int32)
+    dst = torch.tensor([1, 2, 3, 2, 3, 3], dtype=torch.int32)
+    tri = torch.tensor([[0, 1, 2], [0, 1, 3], [0, 2, 3], [1, 2, 3]], dtype=torch.int32)
+    bench.check_listed(tri, 4, src, dst, 4, samples=64)
+    bench.check_listed(tri[:0], 0, src, dst, 4)
+    keep = src != 0
+    with pytest.raises(RuntimeError, match="differs"):  # K4 without vertex 0's edges: only (1, 2, 3) remains
+        bench.check_listed(tri, 4, src[keep], dst[keep], 4, samples=64)
