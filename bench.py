@@ -51,11 +51,11 @@ def parse():
     p.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     p.add_argument("--serve-pool", type=int, default=1024, help="serve: distinct request graphs")
     p.add_argument("--build-workers", type=int, default=6, help="serve: concurrent CSR builders")
-    p.add_argument("--serve-rates", default="2000,5000,10000,20000,40000",
+    p.add_argument("--serve-rates", default="2000,5000,6000,7000,8000,10000",
                    help="serve: offered rates (req/s) of the capacity sweep, comma-separated ('' for none)")
     p.add_argument("--sweep-duration", type=float, default=2.0, help="serve: seconds of arrivals per swept rate")
     p.add_argument("--no-extras", action="store_true",
-                   help="rmat20: leave out the R-MAT 26, batch and serving sub-records")
+                   help="rmat20: leave out the R-MAT 26, per-vertex/listing, batch and serving sub-records")
     p.add_argument("--rmat26-launches", type=int, default=5, help="R-MAT 26 sub-record: timed count launches")
     p.add_argument("--extra-serve-duration", type=float, default=10.0,
                    help="serving sub-record: seconds of arrivals at --rate")
