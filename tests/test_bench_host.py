@@ -76,3 +76,28 @@ def test_listing_spot_check():
     keep = src != 0
     with pytest.raises(RuntimeError, match="differs"):  # K4 without vertex 0's edges: only (1, 2, 3) remains
         bench.check_listed(tri, 4, src[keep], dst[keep], 4, samples=64)
+
+
+def test_serving_keep_up_rule(monkeypatch):
+    """The capacity sweep's rule: a mode keeps up with a rate when it serves at least 95% of it with p99 at most
+    50 ms; its capacity is the highest such rate (None if none).  Replays are faked on the host."""
+    import types
+    served = {  # (mode's batching, rate) -> (graphs/s, p99 ms)
+        ("pipeline", 1000.0): (1000.0, 3.0), ("pipeline", 2000.0): (1990.0, 49.0), ("pipeline", 4000.0): (3000.0, 900.0),
+        (True, 1000.0): (999.0, 2.0), (True, 2000.0): (1800.0, 10.0), (True, 4000.0): (2000.0, 10.0),
+        (False, 1000.0): (1000.0, 51.0), (False, 2000.0): (2000.0, 60.0), (False, 4000.0): (2100.0, 80.0)}
+
+    class Pool:
+        def trace(self, rate, duration, seed_offset=0):
+            return [rate], None
+
+    def replay(args, pool, arrivals, pick, batching, timeout):
+        gps, p99 = served[(batching, arrivals[0])]
+        return {"graphs_per_s": gps, "p50_ms": 1.0, "p99_ms": p99, "mean_batch": 1.0}
+
+    monkeypatch.setattr(bench, "serve_replay", replay)
+    out = bench.serve_capacity(types.SimpleNamespace(), Pool(), [1000.0, 2000.0, 4000.0], 2.0)
+    assert out["batched_max_rate"] == 2000.0        # 1990/2000 >= 0.95 and p99 49 <= 50; 4000 fails both
+    assert out["count_batched_max_rate"] == 1000.0  # 1800/2000 < 0.95
+    assert out["one_by_one_max_rate"] is None       # p99 above 50 ms at every rate
+    assert [x["rate"] for x in out["batched"]] == [1000.0, 2000.0, 4000.0]
