@@ -101,3 +101,17 @@ def test_serving_keep_up_rule(monkeypatch):
     assert out["count_batched_max_rate"] == 1000.0  # 1800/2000 < 0.95
     assert out["one_by_one_max_rate"] is None       # p99 above 50 ms at every rate
     assert [x["rate"] for x in out["batched"]] == [1000.0, 2000.0, 4000.0]
+
+
+def test_profiled_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
+    """The DRAM traffic of a committed count-kernel profile is used only while its recorded source hash is the
+    current kernel source's; otherwise the bench reports none."""
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "k_count_demo.md").write_text(
+        "# demo\n\nsource_sha: 0123456789abcdef\n\ndram_bytes_per_launch: 7.5e+07\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "count_kernel_source_hash", lambda: "0123456789abcdef")
+    assert bench.profiled_traffic("demo") == 7.5e7
+    monkeypatch.setattr(bench, "count_kernel_source_hash", lambda: "fedcba9876543210")
+    assert bench.profiled_traffic("demo") is None
+    assert bench.profiled_traffic("absent") is None
