@@ -198,3 +198,37 @@ def test_noalloc_binding_rejects_bad_outputs_before_any_launch(monkeypatch):
     tc.tc_count_per_vertex_noalloc(1, ok_pv, ok_tot)
     tc.tc_count_per_vertex_noalloc(1, 0x2000, 0x3000)  # raw device addresses: the caller vouches for them
     assert len(calls) == 2
+
+
+def test_tuning_file_applies_only_on_its_device(lib, tmp_path, monkeypatch):
+    """tuning.json is installed only when its device name and SM count match the current GPU (faked here: no GPU),
+    keeps the fields it does not name, and leaves the table alone otherwise."""
+    import json
+    import types
+
+    import torch
+
+    import paper_1909_02127_gb300 as tc
+    saved = tc.tc_get_tuning()
+    saved_tiny = tc.tc_get_tiny_max_pairs()
+    whole = tc.tc_tuning()
+    assert lib.tc_get_tuning(ctypes.byref(whole)) == tc.TC_OK
+    path = tmp_path / "tuning.json"
+    path.write_text(json.dumps({"device": "Fake GPU", "sms": 7, "classes": [[1000, 11], [1 << 40, 22]],
+                                "compact_max_pairs": 12345}))
+    monkeypatch.setattr(torch.cuda, "is_available", lambda: True)
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    try:
+        monkeypatch.setattr(torch.cuda, "get_device_properties",
+                            lambda i: types.SimpleNamespace(name="Other GPU", multi_processor_count=7))
+        assert not tc._apply_tuning_file(lib, str(path))
+        assert tc.tc_get_tuning() == saved
+        monkeypatch.setattr(torch.cuda, "get_device_properties",
+                            lambda i: types.SimpleNamespace(name="Fake GPU", multi_processor_count=7))
+        assert tc._apply_tuning_file(lib, str(path))
+        assert tc.tc_get_tuning() == [(1000, 11), (1 << 40, 22)]
+        assert tc.tc_get_compact_max_pairs() == 12345
+        assert tc.tc_get_tiny_max_pairs() == saved_tiny                     # not in the file: kept
+        assert tc.tc_get_vertex_plain_max_edges() == tc.VERTEX_PLAIN_MAX_EDGES
+    finally:
+        assert lib.tc_set_tuning(ctypes.byref(whole)) == tc.TC_OK
