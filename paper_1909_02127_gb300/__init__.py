@@ -173,7 +173,8 @@ TUNING_FILE = os.path.join(_HERE, "tuning.json")
 
 
 def _apply_tuning_file(lib, path: str = TUNING_FILE) -> bool:
-    """Install the autotuner's table when it was measured on this kind of device (name and SM count match)."""
+    """Install the autotuner's table when it was measured on this kind of device (name and SM count match); a field
+    the file does not name keeps its current value."""
     if not os.path.exists(path):
         return False
     try:
@@ -188,8 +189,8 @@ def _apply_tuning_file(lib, path: str = TUNING_FILE) -> bool:
             return False
         cur = tc_tuning()
         lib.tc_get_tuning(ctypes.byref(cur))
-        t = _tuning_struct(data["classes"], data.get("batch_warp_max_edges", 1 << 25),
-                           data.get("isect_max_wedges_milli", 0),
+        t = _tuning_struct(data["classes"], data.get("batch_warp_max_edges", cur.batch_warp_max_edges),
+                           data.get("isect_max_wedges_milli", cur.isect_max_wedges_milli),
                            data.get("bucket_max_pairs", cur.bucket_max_pairs),
                            data.get("compact_max_pairs", cur.compact_max_pairs),
                            data.get("stage_min_csr_bytes", cur.stage_min_csr_bytes),

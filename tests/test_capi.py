@@ -229,6 +229,7 @@ def test_tuning_file_applies_only_on_its_device(lib, tmp_path, monkeypatch):
         assert tc.tc_get_tuning() == [(1000, 11), (1 << 40, 22)]
         assert tc.tc_get_compact_max_pairs() == 12345
         assert tc.tc_get_tiny_max_pairs() == saved_tiny                     # not in the file: kept
+        assert tc.tc_get_isect_max_wedges_milli() == whole.isect_max_wedges_milli
         assert tc.tc_get_vertex_plain_max_edges() == tc.VERTEX_PLAIN_MAX_EDGES
     finally:
         assert lib.tc_set_tuning(ctypes.byref(whole)) == tc.TC_OK
